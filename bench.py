@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark: DOF*timesteps/s to MGRIT relative residual 1e-10.
+
+Workload (multilevel MGRIT on the unit square): heat equation u_t = Laplace u + f,
+manufactured solution u = sin(pi x) sin(pi y) cos t, B-splines of order
+p in {2,3,4,5} on 64 x 64 elements (N = (62+p)^2 interior unknowns), backward
+Euler with N_t = 256 steps on [0,1], MGRIT with m = 4 down to <= 4 coarse steps
+(256 -> 64 -> 16 -> 4), FCF relaxation, p-multigrid V(1,1) spatial solves to
+relative residual 1e-10.  One "step" of the benchmark = one MGRIT solve for
+each of the four orders (a unit of work = N_p * N_t DOF*timesteps, summed).
+
+Forms: "chosen" = FP32 smoothing / SpMM / transfers / Gauss--Seidel with FP64
+residual refinement (precision 1); "plain" = everything FP64 (precision 0).
+The value is the chosen form's throughput; the plain form is reported beside it.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF*timesteps/s to MGRIT rel. residual 1e-10, chosen vs plain FP64 form"
+UNIT = "DOF*timesteps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--orders", default="2,3,4,5")
+    ap.add_argument("--nel", type=int, default=64)
+    ap.add_argument("--Nt", type=int, default=256)
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-check", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--profile-only", action="store_true",
+                    help="one chosen-form solve per order and exit (for ncu launch lists)")
+    return ap.parse_args()
+
+
+def manufactured():
+    import numpy as np
+    S = lambda xi, eta, x, y: np.sin(np.pi * x) * np.sin(np.pi * y)
+    C = lambda t: 2 * np.pi ** 2 * np.cos(t) - np.sin(t)
+    return S, C
+
+
+def bytes_per_vcycle_dof(p, B):
+    """Algorithmic bytes of one V(1,1) per DOF per right-hand side (8-byte
+    values; matrices amortised over the B right-hand sides of a launch):
+    3 residual products + 2 ILUT sweeps (L and U) + 2 order transfers plus the
+    p = 1 W-cycle and vector traffic."""
+    q = (2 * p + 1) ** 2
+    return (3 * 8 * q + 2 * 12 * q + 2 * 8 * (p + 2) ** 2) / max(B, 1) + 300.0
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.f.name).read().strip().splitlines() if l.strip()]
+        except OSError:
+            rows = []
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def oracle_sample(reps=1, p=2, nel=64, Nt=64):
+    """The oracle (CPU, FP64, as it stands) on a bounded sample of the workload:
+    order p, nel x nel elements, N_t steps (levels N_t -> ... <= 4), MGRIT with
+    p-multigrid spatial solves to the workload's tolerances.  Setup (assembly,
+    Python ILUT) is excluded from the timing.  Returns (DOF*ts/s, seconds, desc)."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import numpy as np
+    from oracle import assembly, geometry, mgrit
+    S, C = manufactured()
+    hi, lo = assembly.problem(p, nel, geometry.UnitSquare())
+    u0, fhat = hi.project(S), hi.load_vector(S)
+    fac = mgrit.pmg_factory(hi, lo, tol=1e-10)
+    cache = {}
+    mk = lambda l, c: cache.setdefault(l, fac(l, c))
+    times = []
+    for _ in range(reps):
+        mg = mgrit.MGRIT(hi.M, hi.K, 1.0, 1.0, Nt, 4, mk, u0, fhat, C)
+        t0 = time.perf_counter()
+        mg.run(tol=1e-10)
+        times.append(time.perf_counter() - t0)
+    desc = (f"oracle MGRIT (NumPy/SciPy FP64, p-multigrid spatial solves) on p={p}, "
+            f"{nel}x{nel} elements, N_t={Nt} (levels {mgrit.level_sizes(Nt, 4)}), tol 1e-10; "
+            f"setup excluded; 1 thread")
+    return hi.N * Nt, times, desc
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # each step = one oracle MGRIT solve of the bounded sample
+    n_units, times, desc = oracle_sample(reps=args.warmup + args.steps, Nt=32)
+    t = sum(times[args.warmup:])
+    v = n_units * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "heat_c2 bounded sample (p=2, N_t=32)", "nel": 64},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2107_05337_gb300 import binding as B
+    S, C = manufactured()
+    orders = [int(x) for x in args.orders.split(",")]
+    T, Nt, nel = 1.0, args.Nt, args.nel
+    fcoef = np.array([C(n * T / Nt) for n in range(Nt + 1)])
+    probs, u0s, fhats, Us = {}, {}, {}, {}
+    for p in orders:
+        probs[p] = B.Problem(p, nel)
+        u0s[p] = probs[p].project(S)
+        fhats[p] = probs[p].load_vector(S)
+        Us[p] = torch.empty((Nt + 1, probs[p].N), dtype=torch.float64, device="cuda")
+    opts = dict(T=T, Nt=Nt, m=4, max_levels=30, min_coarse=4, relax=1, tol=1e-10, max_iter=100)
+    t_setup = time.perf_counter()
+    chosen = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=1, tol=1e-10)) for p in orders}
+    setup_s = time.perf_counter() - t_setup
+    units = sum(probs[p].N * Nt for p in orders)
+    stream = torch.cuda.current_stream()
+
+    def step(handles, stats=None):
+        for p in orders:
+            _, st, _ = handles[p].run(u0s[p], fhats[p], fcoef, Us[p])
+            if stats is not None:
+                stats[p] = st
+
+    if args.profile_only:
+        step(chosen)
+        torch.cuda.synchronize()
+        return
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def timed(handles, K, W):
+        for _ in range(W):
+            step(handles)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        ms = []
+        stats = {}
+        l0 = B.kernel_launches()
+        with Clocks(local) as ck:
+            for _ in range(K):
+                flush.fill_(1.0)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step(handles, stats)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+        launches = B.kernel_launches() - l0
+        total = sum(ms)
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            total = float(t.item())
+        return total, ms, stats, ck.summary(), launches
+
+    total, ms, stats, clocks, launches = timed(chosen, args.steps, args.warmup)
+    value = world * units * args.steps / (total * 1e-3)
+
+    # plain FP64 form, same workload
+    plain = None
+    if not args.skip_plain:
+        plain_h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=0, tol=1e-10)) for p in orders}
+        ptot, pms, pstats, _, _ = timed(plain_h, max(1, min(args.steps, 2)), 1)
+        pk = max(1, min(args.steps, 2))
+        plain = {"value": world * units * pk / (ptot * 1e-3), "ms_per_step": ptot / pk,
+                 "iters": {p: pstats[p]["iters"] for p in orders},
+                 "vcyc_mean": {p: round(pstats[p]["vcyc_mean"], 3) for p in orders}}
+        del plain_h
+
+    # end to end through the C ABI with host buffers: H2D of u0, fhat (pinned),
+    # solve, D2H of the final time level, every step
+    hu0 = {p: u0s[p].cpu().pin_memory() for p in orders}
+    hfh = {p: fhats[p].cpu().pin_memory() for p in orders}
+    hout = {p: torch.empty(probs[p].N, dtype=torch.float64).pin_memory() for p in orders}
+    du0 = {p: torch.empty_like(u0s[p]) for p in orders}
+    dfh = {p: torch.empty_like(fhats[p]) for p in orders}
+    e2e_ms = []
+    for k in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for p in orders:
+            du0[p].copy_(hu0[p], non_blocking=True)
+            dfh[p].copy_(hfh[p], non_blocking=True)
+            chosen[p].run(du0[p], dfh[p], fcoef, Us[p])
+            hout[p].copy_(Us[p][Nt], non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    h2d = sum(2 * probs[p].N * 8 + (Nt + 1) * 8 for p in orders)
+    d2h = sum(probs[p].N * 8 for p in orders)
+    e2e = {"value": world * units * len(e2e_ms) / (sum(e2e_ms) * 1e-3), "unit": UNIT,
+           "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # roofline of the dominant kernel (k_mgrit_sweep), one profiled solve per order
+    roof = None
+    prof_tot_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
+    for p in orders:
+        hp = B.MGRIT(probs[p], **opts, pmg=dict(precision=1, tol=1e-10), profile=1, graphs=0)
+        hp.run(u0s[p], fhats[p], fcoef, Us[p])
+        pr = hp.profile()
+        for g, c, t in zip(pr["grid"], pr["cycles"], pr["ms"]):
+            prof_bytes += c * probs[p].N * bytes_per_vcycle_dof(p, g)
+            prof_tot_ms += t
+            prof_launches += 1
+        del hp
+    peaks = measured_peaks()
+    if prof_launches:
+        achieved = prof_bytes / (prof_tot_ms * 1e-3) / 1e9
+        peak = peaks["hbm_gbs"] if peaks else 6800.0
+        roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 5), "traffic": None,
+                "kernel": "k_mgrit_sweep", "launches_profiled": prof_launches,
+                "mean_launch_ms": round(prof_tot_ms / prof_launches, 4),
+                "peak_source": "measured" if peaks else "fallback"}
+
+    # error against the oracle's sequential backward Euler (FP64, direct solves)
+    errors = None
+    if not args.skip_check and rank == 0:
+        from oracle import assembly, geometry, timestep
+        errors = {}
+        for p in orders:
+            d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+            seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C)
+            chosen[p].run(u0s[p], fhats[p], fcoef, Us[p])
+            U = Us[p].cpu().numpy()
+            errors[p] = float(np.linalg.norm(U - seq) / np.linalg.norm(seq))
+
+    cpu = None
+    if not args.skip_cpu and rank == 0:
+        n_units, times, desc = oracle_sample(reps=1)
+        cpu = {"value": n_units / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": desc}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": f"heat_c2: unit square, nel={nel}, p={orders}, N_t={Nt}, T=1, "
+                                       "m=4 multilevel FCF MGRIT, p-MG V(1,1) to 1e-10",
+                           "parallelism": f"replicas{world}" if world > 1 else "single GPU",
+                           "l2": "flushed (256 MiB write) before every timed step"},
+                "plain_fp64": plain,
+                "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "iters": {p: stats[p]["iters"] for p in orders},
+                "vcyc_mean": {p: round(stats[p]["vcyc_mean"], 3) for p in orders},
+                "error_vs_oracle": errors, "setup_s": round(setup_s, 3),
+                "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+                "clocks": clocks}
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

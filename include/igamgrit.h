@@ -1,0 +1,220 @@
+/*
+ * igamgrit.h -- C ABI of the GB300 (sm_103a) solver for the IgA-discretised
+ * heat equation with MGRIT in time and p-multigrid in space
+ * (Tielen, Moeller, Vuik, arXiv 2107.05337).
+ *
+ * Problem (Sec. 2, Eq. (heat)): d_t u - kappa Laplace(u) = f on
+ * Omega = F((0,1)^2), u = 0 on the boundary, u(.,0) = u0.  B-splines of order
+ * p on a uniform open knot vector with nel elements per direction (Sec. 2);
+ * backward Euler, theta = 1 (Sec. 2, Eq. (los)):
+ *     (M + kappa dt K) u^{k+1} = M u^k + dt f^{k+1}.
+ * Each such spatial solve is done by the p-multigrid cycle of Sec. 4 (ILUT
+ * smoother, L2-projection transfers to p = 1, one h-multigrid W-cycle with
+ * Gauss--Seidel at p = 1, direct coarsest solve).  The time stepping is
+ * solved parallel-in-time by MGRIT (Sec. 3: FCF relaxation, injection, ideal
+ * interpolation, V-cycle over rediscretised levels dt_l = m^l dt).
+ *
+ * Conventions shared by every entry point:
+ *  - Unknowns: the (Dirichlet-eliminated) interior coefficients, n = nel+p-2
+ *    per direction, N = n*n, numbered i = ix + n*iy (xi fastest).
+ *  - Vectors passed as pointers are DEVICE memory owned by the caller unless
+ *    the argument says "host".  Handles are owned by the library and freed by
+ *    the matching *_destroy call.
+ *  - Every call returns an igm_status and never throws; on failure the
+ *    thread-local message igm_last_error() says why.  Work is enqueued on the
+ *    CUDA stream passed in (0 = legacy default stream); calls that need a
+ *    device result on the host (mgrit_solve, cycles_out) synchronise it.
+ *  - There is no CPU fallback: without a usable sm_103a device every call
+ *    that touches the GPU returns IGM_ERR_CUDA.
+ */
+#ifndef IGAMGRIT_H
+#define IGAMGRIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  IGM_OK = 0,
+  IGM_ERR_ARG = -1,           /* invalid argument or unsupported size */
+  IGM_ERR_CUDA = -2,          /* CUDA runtime error (message has the CUDA text) */
+  IGM_ERR_OOM = -3,           /* device or host allocation failed */
+  IGM_ERR_NOT_CONVERGED = -4, /* a spatial solve or MGRIT hit its cycle limit */
+  IGM_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+  IGM_ERR_NUMERIC = -6        /* zero pivot in ILUT, NaN/Inf in a residual */
+} igm_status;
+
+typedef void* igm_stream; /* a cudaStream_t */
+
+/* ---------------------------------------------------------------------------
+ * Discretisation (Sec. 2).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int p;          /* B-spline order p >= 1 (Sec. 2, Cox--de Boor) */
+  int nel;        /* elements per direction (uniform open knot vector, span 1/nel) */
+  int nquad;      /* Gauss points per direction per element; 0 -> p+1 */
+  int geom;       /* 0: unit square (affine, F = identity);
+                     1: B-spline geometry map given by gdeg, gn, gctrl */
+  int gdeg[2];    /* geometry degrees (xi, eta) when geom == 1 */
+  int gn[2];      /* control points per direction when geom == 1 */
+  const double* gctrl; /* HOST, [gn[1]][gn[0]][2], xi fastest; uniform open knots */
+  double kappa;   /* diffusion coefficient (Sec. 2, Eq. (heat)) */
+} iga_desc;
+
+typedef struct iga_ops iga_ops;
+
+/* Assemble M, K (Sec. 2), the order-1 matrices on the same knots, the
+ * transfer matrix P_1^p and the row-sum lumped masses (Sec. 4, Eq. (PM)) on
+ * the host with Gauss quadrature, and upload them.  *out receives a handle.
+ * Errors: IGM_ERR_ARG for p < 1, nel < 2, a geometry with a non-positive
+ * Jacobian determinant sign change, or an invalid control net. */
+igm_status iga_assemble(const iga_desc* desc, iga_ops** out);
+void iga_destroy(iga_ops* ops);
+
+/* Sizes: n per direction, N = n*n unknowns, number of quadrature points of
+ * the whole mesh (nel^2 * nquad^2) used by the two calls below. */
+igm_status iga_sizes(const iga_ops* ops, int* n, int* N, int* nquad_points);
+
+/* HOST [nqp][4] array of (xi, eta, x, y) at every quadrature point, in the
+ * order the two calls below expect their function values. */
+igm_status iga_quadrature_points(const iga_ops* ops, double* pts);
+
+/* b_i = int_Omega f Phi_i (interior i) from HOST values fq[nqp] of f at the
+ * quadrature points; writes DEVICE out[N]. */
+igm_status iga_load_vector(const iga_ops* ops, const double* fq, double* out, igm_stream s);
+
+/* Consistent L2 projection onto the spline space (Sec. 3: g^0 is u^0
+ * projected onto V_{h,p}): solves M u = b(fq); writes DEVICE out[N]. */
+igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_stream s);
+
+/* y = M x, y = K x (FP64) on a block of nrhs DEVICE columns with leading
+ * dimension ld (column j at x + j*ld).  which: 0 = M, 1 = K. */
+igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, double* y,
+                     long ld, igm_stream s);
+
+/* ---------------------------------------------------------------------------
+ * p-multigrid (Sec. 4) for A = M + c K, c = kappa*dt.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  int nu1, nu2;           /* pre/post ILUT smoothing steps (Sec. 4, steps 1 and 5) */
+  double ilut_droptol;    /* ILUT drop tolerance relative to ||a_i||_2 (default 1e-12) */
+  double ilut_fill;       /* ILUT fill factor: keep ceil(fill*nnz) per row part (default 1) */
+  int hmg_coarsest_nel;   /* h-multigrid coarsening stops at this element count (default 8) */
+  int precision;          /* 0: FP64 throughout; 1: FP32 smoothing, SpMM, transfers and
+                             Gauss--Seidel, FP64 outer residual b - A x with iterative
+                             refinement and FP64 coarsest p=1 direct solve */
+  int inner_cycles;       /* precision 1: FP32 V-cycles per FP64 refinement step (default 1) */
+  double tol;             /* spatial stop: ||b - A x||_2 <= tol ||b||_2 (default 1e-10) */
+  int max_cycles;         /* cycle limit of one spatial solve (default 50) */
+} pmg_opts;
+
+typedef struct pmg_handle pmg_handle;
+
+/* Fill *o with the defaults listed above. */
+void pmg_default_opts(pmg_opts* o);
+
+/* Build the p-multigrid hierarchy for A = M + kappa_dt K: ILUT factors in
+ * natural order with their block-row (grid-row) schedule and dense
+ * diagonal-block inverses, the p=1 operator and its Galerkin h-hierarchy
+ * with Gauss--Seidel block data, and the coarsest dense factor.  Host setup
+ * plus one upload.  Errors: IGM_ERR_NUMERIC on a zero ILUT pivot. */
+igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_opts* opts, pmg_handle** out);
+void pmg_destroy(pmg_handle* h);
+
+/* Spatial solves on nrhs independent right-hand sides b (DEVICE, column j at
+ * b + j*ld), updating the initial guesses x in place.  ncycles > 0: exactly
+ * that many cycles (p-multigrid V-cycles in the FP64 form; FP64 refinement
+ * steps of inner_cycles FP32 V-cycles in the mixed form); ncycles == 0: cycle
+ * until the stop test holds or max_cycles.  cycles_out: HOST [nrhs] or NULL.
+ * Returns IGM_ERR_NOT_CONVERGED if some column hit max_cycles. */
+igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long ld, int ncycles,
+                      int* cycles_out, igm_stream s);
+
+/* Block-row triangular sweeps with the ILUT factors (diagnostics and tests):
+ * z = (L U)^{-1} r on nrhs DEVICE columns, in the handle's precision. */
+igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, double* z, long ld,
+                          igm_stream s);
+
+/* Host copies of the ILUT factors in CSR (L strictly lower, U upper with the
+ * diagonal), for pattern comparisons.  Pass NULL arrays to query sizes
+ * (*nnz_l, *nnz_u).  Values are FP64. */
+igm_status pmg_ilut_factors(const pmg_handle* h, int* nnz_l, int* nnz_u, int* l_ptr, int* l_col,
+                            double* l_val, int* u_ptr, int* u_col, double* u_val);
+
+/* ---------------------------------------------------------------------------
+ * MGRIT (Sec. 3).
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double T;        /* final time */
+  int Nt;          /* fine time steps */
+  int m;           /* coarsening factor (Sec. 3: dt_C = m dt_F) */
+  int max_levels;  /* time levels including the fine one (2 = two-level) */
+  int min_coarse;  /* stop coarsening once a level has <= min_coarse steps */
+  int relax;       /* 0: F-relaxation, 1: FCF-relaxation (Sec. 3) */
+  double tol;      /* stop when rho_k <= tol * rho_0 (C-point residual 2-norm) */
+  int max_iter;    /* iteration limit */
+  pmg_opts pmg;    /* spatial solver options used on every level */
+  int initial_guess; /* 0: u_n = 0 for n >= 1; 1: start from the U passed in */
+  int graphs;      /* 1: replay each iteration's launches as CUDA graphs (default 1) */
+  int profile;     /* 1: record CUDA events around every sweep launch (mgrit_profile) */
+} mgrit_opts;
+
+typedef struct {
+  int iters;             /* MGRIT iterations (coarse corrections) done */
+  int levels;            /* time levels used */
+  double res_hist[256];  /* rho_k, k = 0..iters (fine-level C-point residual norms) */
+  double vcyc_mean;      /* mean cycles per spatial solve */
+  long solves;           /* spatial solves done (all levels, all columns) */
+  long vcycles;          /* cycles done (all solves) */
+  double seconds;        /* wall time of the iteration loop (setup excluded) */
+  double setup_seconds;  /* p-multigrid setup of all levels */
+  long launches;         /* kernel launches of the run */
+} mgrit_stats;
+
+typedef struct mgrit_handle mgrit_handle;
+
+void mgrit_default_opts(mgrit_opts* o);
+
+/* Set up MGRIT (Sec. 3) for the time grid in opts: the level hierarchy
+ * dt_l = m^l dt, one p-multigrid hierarchy per level (rediscretised operator
+ * M + kappa dt_l K), and the device work buffers.  Host setup plus uploads;
+ * no solve.  The handle keeps a pointer to ops, which must outlive it. */
+igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, mgrit_handle** out);
+void mgrit_destroy(mgrit_handle* mg);
+
+/* Solve the space-time system of Sec. 3 by MGRIT with the handle's options.
+ * u0: DEVICE [N] initial coefficients (g^0); fhat: DEVICE [N] load vector of
+ * the spatial source profile or NULL; fcoef: HOST [Nt+1] time factors c(t_n)
+ * of a separable source f(x,t) = c(t) fhat(x) or NULL; U: DEVICE [Nt+1][N],
+ * caller-owned, receives all time levels (U[0] = u0).  Reads one FP64 vector
+ * of C-point residual norms back per iteration for the stopping test.
+ * Returns IGM_ERR_NOT_CONVERGED when max_iter is reached first. */
+igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double* fhat, const double* fcoef,
+                     double* U, mgrit_stats* stats, igm_stream s);
+
+/* One-shot convenience: mgrit_create + mgrit_run + mgrit_destroy. */
+igm_status mgrit_solve(const iga_ops* ops, const mgrit_opts* opts, const double* u0,
+                       const double* fhat, const double* fcoef, double* U, mgrit_stats* stats,
+                       igm_stream s);
+
+/* Per-launch record of the last mgrit_run with opts.profile = 1:
+ * HOST arrays of capacity cap: level, grid (CTAs), mode, duration in ms and
+ * spatial cycles done by the launch.  Returns the number of launches recorded
+ * in *count (at most cap). */
+igm_status mgrit_profile(const mgrit_handle* mg, int cap, int* count, int* level, int* grid,
+                         int* mode, float* ms, long* cycles);
+
+/* Thread-local text of the last error (empty string if none). */
+const char* igm_last_error(void);
+
+/* Number of device kernel launches issued by this library since load
+ * (all entry points, all threads). */
+long igm_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IGAMGRIT_H */

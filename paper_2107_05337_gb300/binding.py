@@ -1,0 +1,340 @@
+"""ctypes binding of ``libigamgrit.so`` (C ABI in include/igamgrit.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  PyTorch provides device memory and the current stream.  If the
+library is missing the calls raise -- there is no CPU fallback.
+"""
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_long, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+
+class IgmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"igamgrit status {status}: {msg}")
+        self.status = status
+
+
+class IgaDesc(ctypes.Structure):
+    _fields_ = [("p", c_int), ("nel", c_int), ("nquad", c_int), ("geom", c_int),
+                ("gdeg", c_int * 2), ("gn", c_int * 2), ("gctrl", POINTER(c_double)),
+                ("kappa", c_double)]
+
+
+class PmgOpts(ctypes.Structure):
+    _fields_ = [("nu1", c_int), ("nu2", c_int), ("ilut_droptol", c_double),
+                ("ilut_fill", c_double), ("hmg_coarsest_nel", c_int), ("precision", c_int),
+                ("inner_cycles", c_int), ("tol", c_double), ("max_cycles", c_int)]
+
+
+class MgritOpts(ctypes.Structure):
+    _fields_ = [("T", c_double), ("Nt", c_int), ("m", c_int), ("max_levels", c_int),
+                ("min_coarse", c_int), ("relax", c_int), ("tol", c_double), ("max_iter", c_int),
+                ("pmg", PmgOpts), ("initial_guess", c_int), ("graphs", c_int),
+                ("profile", c_int)]
+
+
+class MgritStats(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("levels", c_int), ("res_hist", c_double * 256),
+                ("vcyc_mean", c_double), ("solves", c_long), ("vcycles", c_long),
+                ("seconds", c_double), ("setup_seconds", c_double), ("launches", c_long)]
+
+
+EXPORTS = {
+    "iga_assemble": (c_int, [POINTER(IgaDesc), POINTER(c_void_p)]),
+    "iga_destroy": (None, [c_void_p]),
+    "iga_sizes": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int)]),
+    "iga_quadrature_points": (c_int, [c_void_p, POINTER(c_double)]),
+    "iga_load_vector": (c_int, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
+    "iga_project": (c_int, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
+    "iga_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p]),
+    "pmg_default_opts": (None, [POINTER(PmgOpts)]),
+    "pmg_setup": (c_int, [c_void_p, c_double, POINTER(PmgOpts), POINTER(c_void_p)]),
+    "pmg_destroy": (None, [c_void_p]),
+    "pmg_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int, POINTER(c_int),
+                           c_void_p]),
+    "pmg_ilut_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_void_p]),
+    "pmg_ilut_factors": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                 POINTER(c_int), POINTER(c_double), POINTER(c_int),
+                                 POINTER(c_int), POINTER(c_double)]),
+    "mgrit_default_opts": (None, [POINTER(MgritOpts)]),
+    "mgrit_create": (c_int, [c_void_p, POINTER(MgritOpts), POINTER(c_void_p)]),
+    "mgrit_destroy": (None, [c_void_p]),
+    "mgrit_run": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p,
+                          POINTER(MgritStats), c_void_p]),
+    "mgrit_solve": (c_int, [c_void_p, POINTER(MgritOpts), c_void_p, c_void_p, POINTER(c_double),
+                            c_void_p, POINTER(MgritStats), c_void_p]),
+    "mgrit_profile": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                              POINTER(c_int), POINTER(ctypes.c_float), POINTER(c_long)]),
+    "igm_last_error": (ctypes.c_char_p, []),
+    "igm_kernel_launches": (c_long, []),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load the library (raises if it has not been built)."""
+    global _LIB
+    if _LIB is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: run paper_2107_05337_gb300.build.build() "
+                               "(there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in EXPORTS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status):
+    if status != 0:
+        raise IgmError(status, lib().igm_last_error().decode())
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("igamgrit needs a CUDA device (no CPU fallback)")
+    return torch
+
+
+def _stream():
+    return c_void_p(_torch().cuda.current_stream().cuda_stream)
+
+
+def _dptr(t):
+    return c_void_p(t.data_ptr())
+
+
+def quarter_annulus_net():
+    """B-spline control net (degrees (3,1), 4 x 2 points) of the map
+    F(xi, eta) = (1 + eta) C(xi), C the cubic Bezier quarter arc with control
+    points (1,0), (1,k), (k,1), (0,1), k = 4(sqrt 2 - 1)/3."""
+    k = 4.0 * (np.sqrt(2.0) - 1.0) / 3.0
+    arc = np.array([[1.0, 0.0], [1.0, k], [k, 1.0], [0.0, 1.0]])
+    ctrl = np.stack([arc * 1.0, arc * 2.0])  # [eta index][xi index][2]
+    return (3, 1), (4, 2), np.ascontiguousarray(ctrl)
+
+
+class Problem:
+    """IgA discretisation (iga_assemble): order p, nel x nel elements."""
+
+    def __init__(self, p, nel, geom="unit_square", kappa=1.0, nquad=0):
+        L = lib()
+        d = IgaDesc()
+        d.p, d.nel, d.nquad, d.kappa = p, nel, nquad, kappa
+        self._ctrl = None
+        if geom == "unit_square":
+            d.geom = 0
+        elif geom == "quarter_annulus":
+            deg, gn, ctrl = quarter_annulus_net()
+            d.geom = 1
+            d.gdeg[0], d.gdeg[1] = deg
+            d.gn[0], d.gn[1] = gn
+            self._ctrl = np.ascontiguousarray(ctrl.ravel())
+            d.gctrl = self._ctrl.ctypes.data_as(POINTER(c_double))
+        else:
+            raise ValueError(geom)
+        h = c_void_p()
+        _check(L.iga_assemble(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self.p, self.nel, self.geom, self.kappa = p, nel, geom, kappa
+        n, N, nqp = c_int(), c_int(), c_int()
+        _check(L.iga_sizes(h, ctypes.byref(n), ctypes.byref(N), ctypes.byref(nqp)))
+        self.n, self.N, self.nqp = n.value, N.value, nqp.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and _LIB is not None:
+            _LIB.iga_destroy(self.h)
+            self.h = None
+
+    def quadrature_points(self):
+        pts = np.zeros((self.nqp, 4))
+        _check(lib().iga_quadrature_points(self.h, pts.ctypes.data_as(POINTER(c_double))))
+        return pts
+
+    def _fq(self, fn):
+        q = self.quadrature_points()
+        return np.ascontiguousarray(fn(q[:, 0], q[:, 1], q[:, 2], q[:, 3]), dtype=np.float64)
+
+    def load_vector(self, fn):
+        """b_i = int f Phi_i for fn(xi, eta, x, y); returns a CUDA float64 tensor."""
+        torch = _torch()
+        fq = self._fq(fn)
+        out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        _check(lib().iga_load_vector(self.h, fq.ctypes.data_as(POINTER(c_double)), _dptr(out),
+                                     _stream()))
+        return out
+
+    def project(self, fn):
+        """L2 projection of fn(xi, eta, x, y) onto the spline space."""
+        torch = _torch()
+        fq = self._fq(fn)
+        out = torch.empty(self.N, dtype=torch.float64, device="cuda")
+        _check(lib().iga_project(self.h, fq.ctypes.data_as(POINTER(c_double)), _dptr(out),
+                                 _stream()))
+        return out
+
+    def apply(self, which, X):
+        """Y = M X (which='M') or K X (which='K') on columns X [nrhs, N] (CUDA float64)."""
+        torch = _torch()
+        X = X.contiguous()
+        Y = torch.empty_like(X)
+        nrhs = X.shape[0] if X.dim() == 2 else 1
+        _check(lib().iga_apply(self.h, 0 if which == "M" else 1, nrhs, _dptr(X), _dptr(Y),
+                               self.N, _stream()))
+        return Y
+
+
+def pmg_opts(**kw):
+    o = PmgOpts()
+    lib().pmg_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class PMG:
+    """p-multigrid hierarchy for A = M + kappa_dt K (pmg_setup)."""
+
+    def __init__(self, problem, kappa_dt, **opts):
+        self.problem = problem
+        self.opts = pmg_opts(**opts)
+        h = c_void_p()
+        _check(lib().pmg_setup(problem.h, kappa_dt, ctypes.byref(self.opts), ctypes.byref(h)))
+        self.h = h
+        self.N = problem.N
+
+    def __del__(self):
+        if getattr(self, "h", None) and _LIB is not None:
+            _LIB.pmg_destroy(self.h)
+            self.h = None
+
+    def solve(self, B, X, ncycles=0, check=True):
+        """In-place solves on columns: B, X CUDA float64 [nrhs, N]; returns cycles per column."""
+        assert B.dtype == X.dtype and B.is_contiguous() and X.is_contiguous()
+        nrhs = B.shape[0]
+        cyc = (c_int * nrhs)()
+        st = lib().pmg_vcycle(self.h, nrhs, _dptr(B), _dptr(X), self.N, ncycles, cyc, _stream())
+        if check:
+            _check(st)
+        return np.array(cyc[:], dtype=np.int64), st
+
+    def ilut_apply(self, R):
+        torch = _torch()
+        Z = torch.empty_like(R)
+        _check(lib().pmg_ilut_apply(self.h, R.shape[0], _dptr(R), _dptr(Z), self.N, _stream()))
+        return Z
+
+    def factors(self):
+        """(L, U) as scipy CSR matrices (host copies of the ILUT factors)."""
+        import scipy.sparse as sp
+        L = lib()
+        nl, nu = c_int(), c_int()
+        null_i, null_d = POINTER(c_int)(), POINTER(c_double)()
+        _check(L.pmg_ilut_factors(self.h, ctypes.byref(nl), ctypes.byref(nu), null_i, null_i,
+                                  null_d, null_i, null_i, null_d))
+        N = self.N
+        lp = np.zeros(N + 1, np.int32); lc = np.zeros(nl.value, np.int32); lv = np.zeros(nl.value)
+        up_ = np.zeros(N + 1, np.int32); uc = np.zeros(nu.value, np.int32); uv = np.zeros(nu.value)
+        P_i = lambda a: a.ctypes.data_as(POINTER(c_int))
+        P_d = lambda a: a.ctypes.data_as(POINTER(c_double))
+        _check(L.pmg_ilut_factors(self.h, None, None, P_i(lp), P_i(lc), P_d(lv), P_i(up_), P_i(uc),
+                                  P_d(uv)))
+        return (sp.csr_matrix((lv, lc, lp), shape=(N, N)),
+                sp.csr_matrix((uv, uc, up_), shape=(N, N)))
+
+
+def mgrit_opts(**kw):
+    o = MgritOpts()
+    lib().mgrit_default_opts(ctypes.byref(o))
+    pmg_kw = kw.pop("pmg", {})
+    for k, v in kw.items():
+        setattr(o, k, v)
+    for k, v in pmg_kw.items():
+        setattr(o.pmg, k, v)
+    return o
+
+
+def _stats(st):
+    return dict(iters=st.iters, levels=st.levels,
+                res_hist=list(st.res_hist[:st.iters + 1]), vcyc_mean=st.vcyc_mean,
+                solves=st.solves, vcycles=st.vcycles, seconds=st.seconds,
+                setup_seconds=st.setup_seconds, launches=st.launches)
+
+
+class MGRIT:
+    """MGRIT handle (mgrit_create / mgrit_run): setup once, solve many times."""
+
+    def __init__(self, problem, **opts):
+        self.problem = problem
+        self.opts = mgrit_opts(**opts)
+        h = c_void_p()
+        _check(lib().mgrit_create(problem.h, ctypes.byref(self.opts), ctypes.byref(h)))
+        self.h = h
+        self.Nt = self.opts.Nt
+
+    def __del__(self):
+        if getattr(self, "h", None) and _LIB is not None:
+            _LIB.mgrit_destroy(self.h)
+            self.h = None
+
+    def run(self, u0, fhat=None, fcoef=None, U=None, check=True):
+        """u0, fhat: CUDA float64 [N]; fcoef: host [Nt+1].  Returns (U, stats, status)."""
+        torch = _torch()
+        if U is None:
+            U = torch.empty((self.Nt + 1, self.problem.N), dtype=torch.float64, device="cuda")
+        fc = None if fcoef is None else np.ascontiguousarray(fcoef, dtype=np.float64)
+        st = MgritStats()
+        status = lib().mgrit_run(self.h, _dptr(u0), _dptr(fhat) if fhat is not None else None,
+                                 fc.ctypes.data_as(POINTER(c_double)) if fc is not None else None,
+                                 _dptr(U), ctypes.byref(st), _stream())
+        if check:
+            _check(status)
+        return U, _stats(st), status
+
+    def profile(self, cap=100000):
+        """Per-launch records of the last run made with profile=1."""
+        cnt = c_int()
+        lv = (c_int * cap)(); gr = (c_int * cap)(); md = (c_int * cap)()
+        ms = (ctypes.c_float * cap)(); cy = (c_long * cap)()
+        _check(lib().mgrit_profile(self.h, cap, ctypes.byref(cnt), lv, gr, md, ms, cy))
+        k = cnt.value
+        return dict(level=np.array(lv[:k]), grid=np.array(gr[:k]), mode=np.array(md[:k]),
+                    ms=np.array(ms[:k], dtype=np.float64), cycles=np.array(cy[:k]))
+
+
+def mgrit_solve(problem, u0, fhat=None, fcoef=None, U=None, check=True, **opts):
+    """One-shot MGRIT solve (mgrit_solve).  u0, fhat: CUDA float64 [N]; fcoef:
+    host array [Nt+1] of c(t_n).  Returns (U [Nt+1, N] CUDA float64, stats, status)."""
+    torch = _torch()
+    o = mgrit_opts(**opts)
+    if U is None:
+        U = torch.empty((o.Nt + 1, problem.N), dtype=torch.float64, device="cuda")
+    fc = None
+    if fcoef is not None:
+        fc = np.ascontiguousarray(fcoef, dtype=np.float64)
+    st = MgritStats()
+    status = lib().mgrit_solve(problem.h, ctypes.byref(o), _dptr(u0),
+                               _dptr(fhat) if fhat is not None else None,
+                               fc.ctypes.data_as(POINTER(c_double)) if fc is not None else None,
+                               _dptr(U), ctypes.byref(st), _stream())
+    if check:
+        _check(status)
+    return U, _stats(st), status
+
+
+def kernel_launches():
+    return lib().igm_kernel_launches()

@@ -1,0 +1,1069 @@
+// C ABI of the library (include/igamgrit.h): host orchestration, device
+// uploads and the kernels that run the p-multigrid solves (Sec. 4) and the
+// MGRIT sweeps (Sec. 3).
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/igamgrit.h"
+#include "host_setup.h"
+#include "solver.cuh"
+
+using namespace igm;
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+static std::atomic<long> g_launches{0};
+
+static igm_status fail(igm_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CU(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t _e = (call);                                                              \
+    if (_e != cudaSuccess)                                                                \
+      return fail(_e == cudaErrorMemoryAllocation ? IGM_ERR_OOM : IGM_ERR_CUDA,           \
+                  std::string(#call) + ": " + cudaGetErrorString(_e));                    \
+  } while (0)
+
+extern "C" const char* igm_last_error(void) { return g_err.c_str(); }
+extern "C" long igm_kernel_launches(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------------------
+// device buffers
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+struct Uploader {
+  std::vector<std::unique_ptr<DevBuf>> bufs;
+  cudaError_t err = cudaSuccess;
+  template <typename T>
+  T* put(const std::vector<T>& v) {
+    if (err != cudaSuccess) return nullptr;
+    if (v.empty()) return nullptr;
+    auto b = std::make_unique<DevBuf>();
+    b->bytes = v.size() * sizeof(T);
+    err = cudaMalloc(&b->p, b->bytes);
+    if (err != cudaSuccess) return nullptr;
+    err = cudaMemcpy(b->p, v.data(), b->bytes, cudaMemcpyHostToDevice);
+    T* out = (T*)b->p;
+    bufs.push_back(std::move(b));
+    return out;
+  }
+  template <typename T>
+  float* put32(const std::vector<T>& v) {
+    std::vector<float> f(v.begin(), v.end());
+    return put(f);
+  }
+  void* raw(size_t bytes) {
+    if (err != cudaSuccess) return nullptr;
+    auto b = std::make_unique<DevBuf>();
+    b->bytes = bytes;
+    err = cudaMalloc(&b->p, bytes);
+    if (err != cudaSuccess) return nullptr;
+    err = cudaMemset(b->p, 0, bytes);
+    void* out = b->p;
+    bufs.push_back(std::move(b));
+    return out;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// handles
+// ---------------------------------------------------------------------------
+struct iga_ops {
+  Geometry geom;
+  Discretisation hi, lo;   // order p and order 1 on the same knots / rule
+  Csr P, PT;               // transfer interior x interior and its transpose
+  double kappa = 1.0;
+  Uploader up;
+  // device copies
+  double *bM64 = nullptr, *bK64 = nullptr, *sM64 = nullptr, *sK64 = nullptr;
+  float *bM32 = nullptr, *bK32 = nullptr;
+  std::vector<double> qpts, qwdet;
+};
+
+struct pmg_handle {
+  const iga_ops* ops = nullptr;
+  pmg_opts opts;
+  double c = 0.0;
+  Csr L, U;
+  PmgD d;
+  Uploader up;
+  bool arena_smem = true;
+  long arena_bytes = 0;
+  char* garena = nullptr;   // global arena for grid_capacity CTAs when not in shared memory
+  int grid_capacity = 0;
+};
+
+static Csr transpose(const Csr& A) {
+  Csr T;
+  T.rows = A.cols;
+  T.cols = A.rows;
+  T.ptr.assign(T.rows + 1, 0);
+  for (int c : A.col) T.ptr[c + 1]++;
+  for (int i = 0; i < T.rows; ++i) T.ptr[i + 1] += T.ptr[i];
+  T.col.resize(A.col.size());
+  T.val.resize(A.val.size());
+  std::vector<int> pos(T.ptr.begin(), T.ptr.end() - 1);
+  for (int i = 0; i < A.rows; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      int c = A.col[k];
+      T.col[pos[c]] = i;
+      T.val[pos[c]] = A.val[k];
+      pos[c]++;
+    }
+  return T;
+}
+
+static int dev_smem_optin() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// iga_assemble and friends
+// ---------------------------------------------------------------------------
+extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
+  if (!desc || !out) return fail(IGM_ERR_ARG, "null argument");
+  if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");
+  if (desc->nel < 4 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [4, 1024]");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+    return fail(IGM_ERR_CUDA, "no CUDA device");
+  auto ops = std::make_unique<iga_ops>();
+  ops->kappa = desc->kappa;
+  Geometry& g = ops->geom;
+  if (desc->geom == 0) {
+    g.affine = true;
+  } else if (desc->geom == 1) {
+    g.affine = false;
+    for (int d = 0; d < 2; ++d) {
+      g.deg[d] = desc->gdeg[d];
+      g.nctrl[d] = desc->gn[d];
+      if (g.deg[d] < 1 || g.nctrl[d] <= g.deg[d]) return fail(IGM_ERR_ARG, "invalid geometry net");
+      g.knots[d] = open_uniform_knots(g.deg[d], g.nctrl[d] - g.deg[d]);
+    }
+    if (!desc->gctrl) return fail(IGM_ERR_ARG, "geometry control net missing");
+    g.ctrl.assign(desc->gctrl, desc->gctrl + 2 * g.nctrl[0] * g.nctrl[1]);
+  } else {
+    return fail(IGM_ERR_ARG, "geom must be 0 or 1");
+  }
+  const int nq = desc->nquad > 0 ? desc->nquad : desc->p + 1;
+  std::string e = assemble(g, desc->p, desc->nel, nq, ops->hi);
+  if (!e.empty()) return fail(IGM_ERR_ARG, e);
+  e = assemble(g, 1, desc->nel, nq, ops->lo);
+  if (!e.empty()) return fail(IGM_ERR_ARG, e);
+  ops->P = transfer(g, ops->hi, ops->lo);
+  ops->PT = transpose(ops->P);
+  quadrature_points(g, ops->hi, ops->qpts, ops->qwdet);
+  Uploader& up = ops->up;
+  if (g.affine) {
+    ops->bM64 = up.put(ops->hi.M1);
+    ops->bK64 = up.put(ops->hi.K1);
+    ops->bM32 = up.put32(ops->hi.M1);
+    ops->bK32 = up.put32(ops->hi.K1);
+  }
+  ops->sM64 = up.put(ops->hi.M.val);
+  ops->sK64 = up.put(ops->hi.K.val);
+  if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
+  *out = ops.release();
+  return IGM_OK;
+}
+
+extern "C" void iga_destroy(iga_ops* ops) { delete ops; }
+
+extern "C" igm_status iga_sizes(const iga_ops* ops, int* n, int* N, int* nqp) {
+  if (!ops) return fail(IGM_ERR_ARG, "null handle");
+  if (n) *n = ops->hi.n;
+  if (N) *N = ops->hi.N;
+  if (nqp) *nqp = (int)ops->qwdet.size();
+  return IGM_OK;
+}
+
+extern "C" igm_status iga_quadrature_points(const iga_ops* ops, double* pts) {
+  if (!ops || !pts) return fail(IGM_ERR_ARG, "null argument");
+  std::memcpy(pts, ops->qpts.data(), ops->qpts.size() * sizeof(double));
+  return IGM_OK;
+}
+
+extern "C" igm_status iga_load_vector(const iga_ops* ops, const double* fq, double* out,
+                                      igm_stream s) {
+  if (!ops || !fq || !out) return fail(IGM_ERR_ARG, "null argument");
+  std::vector<double> b;
+  load_vector(ops->geom, ops->hi, fq, b);
+  CU(cudaMemcpyAsync(out, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  return IGM_OK;
+}
+
+// Banded Cholesky solve of the interior mass matrix (host, FP64).
+static std::string mass_solve(const Discretisation& d, std::vector<double>& x) {
+  const int N = d.N, n = d.n, p = d.p;
+  const int bw = p * n + p;  // half bandwidth in the natural ordering
+  std::vector<double> B((size_t)N * (bw + 1), 0.0);  // B[i][k] = A(i, i-k)
+  Csr A = d.M.to_csr(false);
+  for (int i = 0; i < N; ++i)
+    for (int k = A.ptr[i]; k < A.ptr[i + 1]; ++k) {
+      int j = A.col[k];
+      if (j <= i) B[(size_t)i * (bw + 1) + (i - j)] = A.val[k];
+    }
+  for (int i = 0; i < N; ++i) {
+    for (int k = std::min(i, bw); k >= 1; --k) {
+      int j = i - k;
+      double s = B[(size_t)i * (bw + 1) + k];
+      for (int l = k + 1; l <= std::min(i, bw); ++l) {
+        int m = i - l;          // column index
+        int kj = j - m;         // offset in row j
+        if (kj > bw || kj < 0) continue;
+        s -= B[(size_t)i * (bw + 1) + l] * B[(size_t)j * (bw + 1) + kj];
+      }
+      B[(size_t)i * (bw + 1) + k] = s / B[(size_t)j * (bw + 1)];
+    }
+    double s = B[(size_t)i * (bw + 1)];
+    for (int l = 1; l <= std::min(i, bw); ++l) s -= B[(size_t)i * (bw + 1) + l] * B[(size_t)i * (bw + 1) + l];
+    if (s <= 0.0) return "mass matrix not positive definite";
+    B[(size_t)i * (bw + 1)] = std::sqrt(s);
+  }
+  for (int i = 0; i < N; ++i) {
+    double s = x[i];
+    for (int l = 1; l <= std::min(i, bw); ++l) s -= B[(size_t)i * (bw + 1) + l] * x[i - l];
+    x[i] = s / B[(size_t)i * (bw + 1)];
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    double s = x[i];
+    for (int l = 1; l <= std::min(N - 1 - i, bw); ++l) s -= B[(size_t)(i + l) * (bw + 1) + l] * x[i + l];
+    x[i] = s / B[(size_t)i * (bw + 1)];
+  }
+  return "";
+}
+
+extern "C" igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_stream s) {
+  if (!ops || !fq || !out) return fail(IGM_ERR_ARG, "null argument");
+  std::vector<double> b;
+  load_vector(ops->geom, ops->hi, fq, b);
+  std::string e = mass_solve(ops->hi, b);
+  if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+  CU(cudaMemcpyAsync(out, b.data(), b.size() * sizeof(double), cudaMemcpyHostToDevice,
+                     (cudaStream_t)s));
+  CU(cudaStreamSynchronize((cudaStream_t)s));
+  return IGM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ char* cta_arena(char* garena, long bytes, bool smem) {
+  extern __shared__ __align__(16) char dyn_smem[];
+  return smem ? dyn_smem : garena + (size_t)blockIdx.x * bytes;
+}
+
+__global__ void __launch_bounds__(kBlock) k_apply_op(PmgD P, int which, const double* x,
+                                                     double* y, long ld, double* scratch) {
+  const double* xc = x + (size_t)blockIdx.x * ld;
+  double* yc = y + (size_t)blockIdx.x * ld;
+  double* tm = scratch + (size_t)blockIdx.x * 2 * P.N;
+  double* tk = tm + P.N;
+  if (P.affine) {
+    if (which == 0)
+      apply_A_affine<double>(P.n, P.p, P.bM64, (const double*)nullptr, P.bM64,
+                             (const double*)nullptr, xc, (const double*)nullptr,
+                             (const double*)nullptr, yc, tm, (double*)nullptr, (double*)nullptr);
+    else
+      apply_A_affine<double>(P.n, P.p, P.bM64, P.bK64, P.bK64, P.bM64, xc, (const double*)nullptr,
+                             (const double*)nullptr, yc, tm, tk, (double*)nullptr);
+  } else {
+    apply_stencil<double>(P.n, P.w, which == 0 ? P.sM64 : P.sA64, xc, (const double*)nullptr,
+                          (const double*)nullptr, yc, (double*)nullptr);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_pmg_solve(PmgD P, const double* b, double* x, long ld,
+                                                      int ncycles, int* cycles_out, int* status,
+                                                      char* garena, int smem) {
+  __shared__ double red[32];
+  char* arena = cta_arena(garena, P.arena_bytes, smem);
+  const double* bc = b + (size_t)blockIdx.x * ld;
+  double* xc = x + (size_t)blockIdx.x * ld;
+  int c = pmg_solve(P, bc, xc, arena, red, ncycles, status);
+  if (threadIdx.x == 0 && cycles_out) cycles_out[blockIdx.x] = c;
+}
+
+__global__ void __launch_bounds__(kBlock) k_ilut_apply(PmgD P, const double* r, double* z, long ld,
+                                                       char* garena, int smem) {
+  char* arena = cta_arena(garena, P.arena_bytes, smem);
+  const double* rc = r + (size_t)blockIdx.x * ld;
+  double* zc = z + (size_t)blockIdx.x * ld;
+  if (P.precision == 0) {
+    double* A = (double*)arena;
+    double* t = A + P.o_t;
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) t[i] = rc[i];
+    __syncthreads();
+    ilut_apply<double>(P, t, A + P.o_row);
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) zc[i] = t[i];
+  } else {
+    float* A = (float*)arena;
+    float* t = A + P.o_t;
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) t[i] = (float)rc[i];
+    __syncthreads();
+    ilut_apply<float>(P, t, A + P.o_row);
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) zc[i] = (double)t[i];
+  }
+}
+
+// MGRIT sweep modes (Sec. 3): F-relaxation, C-relaxation, F-relaxation plus
+// C-point residual and injection, coarse correction plus F-relaxation (ideal
+// interpolation), and sequential stepping on the coarsest level.
+enum : int { MODE_F = 0, MODE_C = 1, MODE_FR = 2, MODE_CF = 3, MODE_SEQ = 4, MODE_R = 5 };
+
+struct SweepArgs {
+  PmgD P;
+  int mode, m, Nl, nint;
+  double* W;              // [Nl+1][N]: the part of u each step's solve produces
+  const double* g;        // [Nl+1][N] right-hand side g^(l) (nullptr on the fine level)
+  const double* Wc;       // next level's W and g (correction)
+  const double* gc;
+  double* gnext;          // next level's g, written by the residual
+  double* norms;          // [nint] ||r_j||^2 (fine level) or nullptr
+  const double* fhat;     // fine level source profile or nullptr
+  const double* fcoef;    // device [Nt+1] time factors
+  double dt0;
+  double* scratch;        // per CTA: 2 N doubles (rhs, residual iterate)
+  char* garena;
+  int smem;
+  int ncycles;
+  unsigned long long* counters;  // [0] solves, [1] cycles
+  int* status;
+};
+
+__device__ void mgrit_step(const SweepArgs& a, char* arena, double* red, int n, bool residual,
+                           int j) {
+  const PmgD& P = a.P;
+  const int N = P.N;
+  double* rhs = a.scratch + (size_t)blockIdx.x * 2 * N;
+  double* xr = rhs + N;
+  double* tm = (P.precision == 0) ? (double*)arena + P.o_u : (double*)((float*)arena + P.o_d);
+  const double* u = a.W + (size_t)(n - 1) * N;
+  const double* ug = a.g ? a.g + (size_t)(n - 1) * N : nullptr;
+  const double scale = a.fhat ? a.dt0 * a.fcoef[n] : 0.0;
+  build_rhs(P, u, ug, scale, a.fhat, rhs, tm);
+  double* Wn = a.W + (size_t)n * N;
+  double* x = Wn;
+  if (residual) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) xr[i] = Wn[i];
+    __syncthreads();
+    x = xr;
+  }
+  int cyc = pmg_solve(P, rhs, x, arena, red, a.ncycles, a.status);
+  if (threadIdx.x == 0 && a.counters) {
+    atomicAdd(&a.counters[0], 1ull);
+    atomicAdd(&a.counters[1], (unsigned long long)cyc);
+  }
+  if (residual) {
+    double* gout = a.gnext + (size_t)(j + 1) * N;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double r = xr[i] - Wn[i];
+      gout[i] = r;
+      s += r * r;
+    }
+    s = block_sum(s, red);
+    if (a.norms && threadIdx.x == 0) a.norms[j] = s;
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
+  __shared__ double red[32];
+  char* arena = cta_arena(a.garena, a.P.arena_bytes, a.smem);
+  const int j = blockIdx.x, m = a.m, N = a.P.N;
+  switch (a.mode) {
+    case MODE_C:
+      mgrit_step(a, arena, red, (j + 1) * m, false, j);
+      break;
+    case MODE_CF: {
+      // u_{jm} += u^(l+1)_j (coarse correction at the C-point owned by this CTA)
+      if (j >= 1) {
+        double* w = a.W + (size_t)(j * m) * N;
+        const double* wc = a.Wc + (size_t)j * N;
+        const double* gc = a.gc + (size_t)j * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
+      }
+      if (j == a.nint - 1) {
+        double* w = a.W + (size_t)a.Nl * N;
+        const double* wc = a.Wc + (size_t)a.nint * N;
+        const double* gc = a.gc + (size_t)a.nint * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
+      }
+      __syncthreads();
+    }  // fall through: F-relaxation from the corrected C-point
+    case MODE_F:
+    case MODE_FR:
+      for (int k = 1; k < m; ++k) mgrit_step(a, arena, red, j * m + k, false, j);
+      if (a.mode == MODE_FR) mgrit_step(a, arena, red, (j + 1) * m, true, j);
+      break;
+    case MODE_R:
+      mgrit_step(a, arena, red, (j + 1) * m, true, j);
+      break;
+    case MODE_SEQ:
+      for (int n = 1; n <= a.Nl; ++n) mgrit_step(a, arena, red, n, false, 0);
+      break;
+  }
+}
+
+static cudaError_t set_smem(const void* fn, long bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ---------------------------------------------------------------------------
+// pmg_setup
+// ---------------------------------------------------------------------------
+extern "C" void pmg_default_opts(pmg_opts* o) {
+  if (!o) return;
+  o->nu1 = 1;
+  o->nu2 = 1;
+  o->ilut_droptol = 1e-12;
+  o->ilut_fill = 1.0;
+  o->hmg_coarsest_nel = 8;
+  o->precision = 1;
+  o->inner_cycles = 1;
+  o->tol = 1e-10;
+  o->max_cycles = 50;
+}
+
+static void gen_wcycle(int k, int last, std::vector<int>& ops) {
+  if (k == last) {
+    ops.push_back(W_COARSE | (k << 8));
+    return;
+  }
+  ops.push_back(W_GS | (k << 8));
+  ops.push_back(W_RESTRICT | (k << 8));
+  gen_wcycle(k + 1, last, ops);
+  // the second visit of an exact coarsest solve reproduces the first: skip it
+  if (k + 1 != last) gen_wcycle(k + 1, last, ops);
+  ops.push_back(W_PROLONG | (k << 8));
+  ops.push_back(W_GS | (k << 8));
+}
+
+static int align4(int x) { return (x + 3) & ~3; }
+
+extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_opts* opts,
+                                pmg_handle** out) {
+  if (!ops || !out) return fail(IGM_ERR_ARG, "null argument");
+  auto h = std::make_unique<pmg_handle>();
+  h->ops = ops;
+  if (opts) h->opts = *opts; else pmg_default_opts(&h->opts);
+  const pmg_opts& o = h->opts;
+  if (o.nu1 < 0 || o.nu2 < 0 || o.nu1 + o.nu2 < 1) return fail(IGM_ERR_ARG, "need nu1 + nu2 >= 1");
+  if (o.precision != 0 && o.precision != 1) return fail(IGM_ERR_ARG, "precision must be 0 or 1");
+  if (o.inner_cycles < 1) return fail(IGM_ERR_ARG, "inner_cycles must be >= 1");
+  if (o.max_cycles < 1) return fail(IGM_ERR_ARG, "max_cycles must be >= 1");
+  h->c = kappa_dt;
+  const Discretisation& hi = ops->hi;
+  const Discretisation& lo = ops->lo;
+  const int n = hi.n, N = hi.N, p = hi.p, W = 2 * p + 1;
+  // A = M + c K (Sec. 4: the backward-Euler step matrix)
+  Stencil A = hi.M;
+  for (size_t i = 0; i < A.val.size(); ++i) A.val[i] = hi.M.val[i] + kappa_dt * hi.K.val[i];
+  Csr Acsr = A.to_csr(true);
+  std::string e = ilut(Acsr, o.ilut_droptol, o.ilut_fill, h->L, h->U);
+  if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+  BlockTri BL, BU;
+  e = block_lower(h->L, n, BL);
+  if (e.empty()) e = block_upper(h->U, n, BU);
+  if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+  // p = 1 operator and its h-hierarchy (Sec. 4, Fig. 5)
+  std::vector<Stencil> H;
+  Stencil A1 = lo.M;
+  for (size_t i = 0; i < A1.val.size(); ++i) A1.val[i] = lo.M.val[i] + kappa_dt * lo.K.val[i];
+  H.push_back(A1);
+  int nel_k = hi.nel;
+  while (nel_k > o.hmg_coarsest_nel && nel_k % 2 == 0 && (int)H.size() < kMaxH) {
+    H.push_back(galerkin_coarse(H.back()));
+    nel_k /= 2;
+  }
+  std::vector<double> Cinv;
+  e = spd_inverse(H.back(), Cinv);
+  if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+
+  PmgD& d = h->d;
+  std::memset(&d, 0, sizeof(d));
+  Uploader& up = h->up;
+  d.p = p; d.n = n; d.N = N; d.w = p; d.affine = ops->geom.affine ? 1 : 0;
+  d.c = kappa_dt;
+  if (d.affine) {
+    std::vector<double> bA((size_t)n * W), bcM((size_t)n * W);
+    for (size_t i = 0; i < bA.size(); ++i) {
+      bA[i] = hi.M1[i] + kappa_dt * hi.K1[i];
+      bcM[i] = kappa_dt * hi.M1[i];
+    }
+    d.bM64 = ops->bM64; d.bK64 = ops->bK64; d.bM32 = ops->bM32; d.bK32 = ops->bK32;
+    d.bA64 = up.put(bA); d.bcM64 = up.put(bcM);
+    d.bA32 = up.put32(bA); d.bcM32 = up.put32(bcM);
+  }
+  d.sA64 = up.put(A.val);
+  d.sA32 = up.put32(A.val);
+  d.sM64 = ops->sM64;
+  d.Lptr = up.put(BL.off.ptr); d.Lcol = up.put(BL.off.col);
+  d.Lval64 = up.put(BL.off.val); d.Lval32 = up.put32(BL.off.val);
+  d.Linv64 = up.put(BL.inv); d.Linv32 = up.put32(BL.inv);
+  d.Uptr = up.put(BU.off.ptr); d.Ucol = up.put(BU.off.col);
+  d.Uval64 = up.put(BU.off.val); d.Uval32 = up.put32(BU.off.val);
+  d.Uinv64 = up.put(BU.inv); d.Uinv32 = up.put32(BU.inv);
+  // a row with no off-block entries still needs a valid pointer array
+  d.N1 = lo.N;
+  d.Pptr = up.put(ops->P.ptr); d.Pcol = up.put(ops->P.col);
+  d.Pval64 = up.put(ops->P.val); d.Pval32 = up.put32(ops->P.val);
+  d.PTptr = up.put(ops->PT.ptr); d.PTcol = up.put(ops->PT.col);
+  d.PTval64 = up.put(ops->PT.val); d.PTval32 = up.put32(ops->PT.val);
+  d.MpL64 = up.put(hi.lumped); d.MpL32 = up.put32(hi.lumped);
+  d.M1L64 = up.put(lo.lumped); d.M1L32 = up.put32(lo.lumped);
+  d.nh = (int)H.size();
+  for (int k = 0; k < d.nh; ++k) {
+    std::vector<double> G;
+    e = gs_blocks(H[k], G);
+    if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+    d.h[k].n = H[k].n;
+    d.h[k].A64 = up.put(H[k].val);
+    d.h[k].A32 = up.put32(H[k].val);
+    d.h[k].G64 = up.put(G);
+    d.h[k].G32 = up.put32(G);
+  }
+  d.Cinv = up.put(Cinv);
+  std::vector<int> wops;
+  gen_wcycle(0, d.nh - 1, wops);
+  if ((int)wops.size() > (int)(sizeof(d.ops) / sizeof(int)))
+    return fail(IGM_ERR_ARG, "h-multigrid hierarchy too deep for the W-cycle program");
+  d.nops = (int)wops.size();
+  for (int i = 0; i < d.nops; ++i) d.ops[i] = wops[i];
+  d.precision = o.precision;
+  d.inner = o.inner_cycles;
+  d.nu1 = o.nu1;
+  d.nu2 = o.nu2;
+  d.max_cycles = o.max_cycles;
+  d.tol = o.tol;
+  // arena layout, in elements of the smoothing precision
+  const int es = o.precision == 0 ? 8 : 4;
+  int off = 0;
+  if (o.precision == 1) {
+    d.o_r = off; off = align4(off + N);
+    d.o_d = off; off = align4(off + N);
+  }
+  d.o_t = off; off = align4(off + N);
+  d.o_u = off;
+  int hsum = 0;
+  for (int k = 0; k < d.nh; ++k) {
+    d.h[k].ox = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
+    d.h[k].ob = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
+    d.h[k].ot = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
+  }
+  off += std::max(align4(2 * N) + align4(N), hsum);
+  d.o_row = off;
+  off = align4(off + std::max(n, lo.n) + 4);
+  h->arena_bytes = (long)off * es;
+  d.arena_bytes = h->arena_bytes;
+  if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
+  const int optin = dev_smem_optin() - 1024;
+  h->arena_smem = h->arena_bytes <= optin;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t ce = set_smem((const void*)k_pmg_solve, optin);
+    if (ce == cudaSuccess) ce = set_smem((const void*)k_mgrit_sweep, optin);
+    if (ce == cudaSuccess) ce = set_smem((const void*)k_ilut_apply, optin);
+    if (ce != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(ce));
+    attr_done = true;
+  }
+  *out = h.release();
+  return IGM_OK;
+}
+
+extern "C" void pmg_destroy(pmg_handle* h) {
+  if (!h) return;
+  if (h->garena) cudaFree(h->garena);
+  delete h;
+}
+
+static igm_status ensure_arena(pmg_handle* h, int grid) {
+  if (h->arena_smem) return IGM_OK;
+  if (h->grid_capacity >= grid) return IGM_OK;
+  if (h->garena) cudaFree(h->garena);
+  h->garena = nullptr;
+  h->grid_capacity = 0;
+  CU(cudaMalloc(&h->garena, (size_t)h->arena_bytes * grid));
+  h->grid_capacity = grid;
+  return IGM_OK;
+}
+
+static long smem_of(const pmg_handle* h) { return h->arena_smem ? h->arena_bytes : 0; }
+
+extern "C" igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long ld,
+                                 int ncycles, int* cycles_out, igm_stream s) {
+  if (!h || !b || !x) return fail(IGM_ERR_ARG, "null argument");
+  if (nrhs < 0 || ncycles < 0 || ld < h->d.N) return fail(IGM_ERR_ARG, "bad nrhs/ld/ncycles");
+  if (nrhs == 0) return IGM_OK;
+  cudaStream_t st = (cudaStream_t)s;
+  igm_status rs = ensure_arena(h, nrhs);
+  if (rs != IGM_OK) return rs;
+  int* dcyc = nullptr;
+  int* dstat = nullptr;
+  CU(cudaMallocAsync(&dcyc, sizeof(int) * (nrhs + 1), st));
+  dstat = dcyc + nrhs;
+  CU(cudaMemsetAsync(dcyc, 0, sizeof(int) * (nrhs + 1), st));
+  k_pmg_solve<<<nrhs, kBlock, smem_of(h), st>>>(h->d, b, x, ld, ncycles, dcyc, dstat, h->garena,
+                                                 h->arena_smem ? 1 : 0);
+  g_launches++;
+  CU(cudaGetLastError());
+  std::vector<int> hc(nrhs + 1);
+  CU(cudaMemcpyAsync(hc.data(), dcyc, sizeof(int) * (nrhs + 1), cudaMemcpyDeviceToHost, st));
+  CU(cudaFreeAsync(dcyc, st));
+  CU(cudaStreamSynchronize(st));
+  if (cycles_out) std::memcpy(cycles_out, hc.data(), sizeof(int) * nrhs);
+  if (hc[nrhs] == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
+  if (hc[nrhs] == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "spatial solve hit max_cycles");
+  return IGM_OK;
+}
+
+extern "C" igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, double* z, long ld,
+                                     igm_stream s) {
+  if (!h || !r || !z) return fail(IGM_ERR_ARG, "null argument");
+  if (nrhs < 0 || ld < h->d.N) return fail(IGM_ERR_ARG, "bad nrhs/ld");
+  if (nrhs == 0) return IGM_OK;
+  igm_status rs = ensure_arena(h, nrhs);
+  if (rs != IGM_OK) return rs;
+  k_ilut_apply<<<nrhs, kBlock, smem_of(h), (cudaStream_t)s>>>(h->d, r, z, ld, h->garena,
+                                                                h->arena_smem ? 1 : 0);
+  g_launches++;
+  CU(cudaGetLastError());
+  return IGM_OK;
+}
+
+extern "C" igm_status pmg_ilut_factors(const pmg_handle* h, int* nnz_l, int* nnz_u, int* l_ptr,
+                                       int* l_col, double* l_val, int* u_ptr, int* u_col,
+                                       double* u_val) {
+  if (!h) return fail(IGM_ERR_ARG, "null handle");
+  if (nnz_l) *nnz_l = h->L.nnz();
+  if (nnz_u) *nnz_u = h->U.nnz();
+  if (l_ptr) std::memcpy(l_ptr, h->L.ptr.data(), h->L.ptr.size() * sizeof(int));
+  if (l_col) std::memcpy(l_col, h->L.col.data(), h->L.col.size() * sizeof(int));
+  if (l_val) std::memcpy(l_val, h->L.val.data(), h->L.val.size() * sizeof(double));
+  if (u_ptr) std::memcpy(u_ptr, h->U.ptr.data(), h->U.ptr.size() * sizeof(int));
+  if (u_col) std::memcpy(u_col, h->U.col.data(), h->U.col.size() * sizeof(int));
+  if (u_val) std::memcpy(u_val, h->U.val.data(), h->U.val.size() * sizeof(double));
+  return IGM_OK;
+}
+
+extern "C" igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, double* y,
+                                long ld, igm_stream s) {
+  if (!ops || !x || !y) return fail(IGM_ERR_ARG, "null argument");
+  if ((which != 0 && which != 1) || nrhs < 0 || ld < ops->hi.N)
+    return fail(IGM_ERR_ARG, "bad which/nrhs/ld");
+  if (nrhs == 0) return IGM_OK;
+  PmgD d;
+  std::memset(&d, 0, sizeof(d));
+  d.p = ops->hi.p; d.n = ops->hi.n; d.N = ops->hi.N; d.w = d.p;
+  d.affine = ops->geom.affine ? 1 : 0;
+  d.bM64 = ops->bM64; d.bK64 = ops->bK64;
+  d.sM64 = ops->sM64; d.sA64 = ops->sK64;
+  cudaStream_t st = (cudaStream_t)s;
+  double* scratch = nullptr;
+  CU(cudaMallocAsync(&scratch, sizeof(double) * 2 * (size_t)d.N * nrhs, st));
+  k_apply_op<<<nrhs, kBlock, 0, st>>>(d, which, x, y, ld, scratch);
+  g_launches++;
+  CU(cudaGetLastError());
+  CU(cudaFreeAsync(scratch, st));
+  return IGM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// MGRIT (Sec. 3)
+// ---------------------------------------------------------------------------
+extern "C" void mgrit_default_opts(mgrit_opts* o) {
+  if (!o) return;
+  o->T = 1.0;
+  o->Nt = 256;
+  o->m = 4;
+  o->max_levels = 30;
+  o->min_coarse = 4;
+  o->relax = 1;
+  o->tol = 1e-10;
+  o->max_iter = 100;
+  pmg_default_opts(&o->pmg);
+  o->initial_guess = 0;
+  o->graphs = 1;
+  o->profile = 0;
+}
+
+struct Level {
+  int Nl = 0;
+  double dt = 0.0;
+  pmg_handle* h = nullptr;
+  double* W = nullptr;
+  double* g = nullptr;
+};
+
+struct ProfRec {
+  int level, grid, mode;
+  cudaEvent_t e0, e1;
+};
+
+struct mgrit_handle {
+  const iga_ops* ops = nullptr;
+  mgrit_opts o;
+  std::vector<Level> L;
+  std::vector<pmg_handle*> owned;
+  Uploader up;
+  int max_grid = 1;
+  double* scratch = nullptr;
+  double* norms = nullptr;
+  unsigned long long* counters = nullptr;   // [0] solves, [1] cycles
+  int* status = nullptr;
+  double* dfcoef = nullptr;
+  double* hnorms = nullptr;                 // pinned host copy of the norms
+  double setup_seconds = 0.0;
+  // graphs of one iteration: A = fine relaxation + residual + norm copy,
+  // B = coarse levels + corrections; captured for one (U, fhat) pair
+  cudaGraphExec_t gA = nullptr, gB = nullptr;
+  const double* g_U = nullptr;
+  const double* g_fhat = nullptr;
+  cudaStream_t g_stream = nullptr;
+  // per-launch profile of the last run
+  std::vector<ProfRec> prof;
+  std::vector<unsigned long long> prof_cyc;  // counter snapshots after each launch
+  unsigned long long* dlog = nullptr;
+  int dlog_cap = 0;
+  ~mgrit_handle() {
+    if (gA) cudaGraphExecDestroy(gA);
+    if (gB) cudaGraphExecDestroy(gB);
+    for (auto& r : prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+    for (auto* h : owned) pmg_destroy(h);
+    if (hnorms) cudaFreeHost(hnorms);
+  }
+};
+
+extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, mgrit_handle** out) {
+  if (!ops || !opts || !out) return fail(IGM_ERR_ARG, "null argument");
+  const mgrit_opts& o = *opts;
+  if (o.Nt < 1 || o.m < 2 || !(o.T > 0.0) || o.max_iter < 0 || o.max_levels < 1 ||
+      o.max_iter > 255)
+    return fail(IGM_ERR_ARG, "bad MGRIT options (Nt >= 1, m >= 2, T > 0, 0 <= max_iter <= 255)");
+  if (o.relax != 0 && o.relax != 1) return fail(IGM_ERR_ARG, "relax must be 0 or 1");
+  auto t0 = std::chrono::steady_clock::now();
+  auto mg = std::make_unique<mgrit_handle>();
+  mg->ops = ops;
+  mg->o = o;
+  const int N = ops->hi.N;
+  std::vector<Level>& L = mg->L;
+  Level l0;
+  l0.Nl = o.Nt;
+  l0.dt = o.T / o.Nt;
+  L.push_back(l0);
+  while ((int)L.size() < o.max_levels && L.back().Nl > o.min_coarse && L.back().Nl % o.m == 0 &&
+         L.back().Nl / o.m >= 1) {
+    Level nx;
+    nx.Nl = L.back().Nl / o.m;
+    nx.dt = L.back().dt * o.m;
+    L.push_back(nx);
+  }
+  const int nlev = (int)L.size();
+  Uploader& up = mg->up;
+  for (int l = 0; l < nlev; ++l) {
+    pmg_handle* h = nullptr;
+    igm_status r = pmg_setup(ops, ops->kappa * L[l].dt, &o.pmg, &h);
+    if (r != IGM_OK) return r;
+    mg->owned.push_back(h);
+    L[l].h = h;
+    if (l > 0) {
+      L[l].W = (double*)up.raw(sizeof(double) * (size_t)(L[l].Nl + 1) * N);
+      L[l].g = (double*)up.raw(sizeof(double) * (size_t)(L[l].Nl + 1) * N);
+    }
+  }
+  for (int l = 0; l < nlev; ++l) mg->max_grid = std::max(mg->max_grid, L[l].Nl / o.m);
+  mg->scratch = (double*)up.raw(sizeof(double) * 2 * (size_t)N * mg->max_grid);
+  mg->norms = (double*)up.raw(sizeof(double) * (size_t)mg->max_grid);
+  mg->counters = (unsigned long long*)up.raw(sizeof(unsigned long long) * 2);
+  mg->status = (int*)up.raw(sizeof(int));
+  mg->dfcoef = (double*)up.raw(sizeof(double) * (size_t)(o.Nt + 1));
+  if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
+  CU(cudaMallocHost(&mg->hnorms, sizeof(double) * mg->max_grid));
+  for (int l = 0; l < nlev; ++l) {
+    igm_status r = ensure_arena(L[l].h, mg->max_grid);
+    if (r != IGM_OK) return r;
+  }
+  mg->setup_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  *out = mg.release();
+  return IGM_OK;
+}
+
+extern "C" void mgrit_destroy(mgrit_handle* mg) { delete mg; }
+
+// Launch one sweep kernel on level l.
+static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm, double* U,
+                        const double* fhat, cudaStream_t st, bool profile) {
+  const int nlev = (int)mg->L.size();
+  std::vector<Level>& L = mg->L;
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = L[l].h->d;
+  a.mode = mode;
+  a.m = mg->o.m;
+  a.Nl = L[l].Nl;
+  a.nint = L[l].Nl / mg->o.m;
+  a.W = l == 0 ? U : L[l].W;
+  a.g = l > 0 ? L[l].g : nullptr;
+  if (l + 1 < nlev) {
+    a.Wc = L[l + 1].W;
+    a.gc = L[l + 1].g;
+    a.gnext = L[l + 1].g;
+  }
+  a.norms = nrm;
+  a.fhat = (l == 0) ? fhat : nullptr;
+  a.fcoef = mg->dfcoef;
+  a.dt0 = L[0].dt;
+  a.scratch = mg->scratch;
+  a.garena = L[l].h->garena;
+  a.smem = L[l].h->arena_smem ? 1 : 0;
+  a.ncycles = 0;
+  a.counters = mg->counters;
+  a.status = mg->status;
+  ProfRec rec{l, grid, mode, nullptr, nullptr};
+  if (profile) {
+    CU(cudaEventCreate(&rec.e0));
+    CU(cudaEventCreate(&rec.e1));
+    CU(cudaEventRecord(rec.e0, st));
+  }
+  k_mgrit_sweep<<<grid, kBlock, smem_of(L[l].h), st>>>(a);
+  g_launches++;
+  CU(cudaGetLastError());
+  if (profile) {
+    CU(cudaEventRecord(rec.e1, st));
+    const int k = (int)mg->prof.size();
+    if (k < mg->dlog_cap)
+      CU(cudaMemcpyAsync(mg->dlog + 2 * k, mg->counters, 2 * sizeof(unsigned long long),
+                         cudaMemcpyDeviceToDevice, st));
+    mg->prof.push_back(rec);
+  }
+  return IGM_OK;
+}
+
+#define SWEEP(l, mode, grid, nrm)                                                \
+  do {                                                                           \
+    igm_status _r = sweep(mg, l, mode, grid, nrm, U, fhat, st, profile);         \
+    if (_r != IGM_OK) return _r;                                                 \
+  } while (0)
+
+// Part A of an iteration: fine-level relaxation (Sec. 3, FCF or F) and the
+// C-point residual, injected into g^(1); copies the per-interval norms.
+static igm_status part_A(mgrit_handle* mg, bool first, double* U, const double* fhat,
+                         cudaStream_t st, bool profile) {
+  const int nint0 = mg->L[0].Nl / mg->o.m;
+  if (mg->o.relax == 1) {
+    // the leading F-relaxation is skipped after the first iteration: the
+    // interpolation has just made the F-points Phi-consistent
+    if (first) SWEEP(0, MODE_F, nint0, nullptr);
+    SWEEP(0, MODE_C, nint0, nullptr);
+    SWEEP(0, MODE_FR, nint0, mg->norms);
+  } else {
+    SWEEP(0, first ? MODE_FR : MODE_R, nint0, mg->norms);
+  }
+  CU(cudaMemcpyAsync(mg->hnorms, mg->norms, sizeof(double) * nint0, cudaMemcpyDeviceToHost, st));
+  return IGM_OK;
+}
+
+// Part B: the coarse levels (recursive V-cycle, Sec. 3 algorithm box) and the
+// corrections with F-relaxation (ideal interpolation) back to the fine level.
+static igm_status part_B(mgrit_handle* mg, double* U, const double* fhat, cudaStream_t st,
+                         bool profile) {
+  const int nlev = (int)mg->L.size(), N = mg->ops->hi.N;
+  std::vector<Level>& L = mg->L;
+  for (int l = 1; l < nlev; ++l) {
+    CU(cudaMemsetAsync(L[l].W, 0, sizeof(double) * (size_t)(L[l].Nl + 1) * N, st));
+    if (l == nlev - 1) {
+      SWEEP(l, MODE_SEQ, 1, nullptr);
+    } else {
+      const int ni = L[l].Nl / mg->o.m;
+      if (mg->o.relax == 1) {
+        SWEEP(l, MODE_F, ni, nullptr);
+        SWEEP(l, MODE_C, ni, nullptr);
+      }
+      SWEEP(l, MODE_FR, ni, nullptr);
+    }
+  }
+  for (int l = nlev - 2; l >= 0; --l) SWEEP(l, MODE_CF, L[l].Nl / mg->o.m, nullptr);
+  return IGM_OK;
+}
+
+static igm_status capture(mgrit_handle* mg, bool partA, double* U, const double* fhat,
+                          cudaStream_t st, cudaGraphExec_t* out) {
+  CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  igm_status r = partA ? part_A(mg, false, U, fhat, st, false) : part_B(mg, U, fhat, st, false);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(st, &g);
+  if (r != IGM_OK) { if (g) cudaGraphDestroy(g); return r; }
+  if (e != cudaSuccess) return fail(IGM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(IGM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return IGM_OK;
+}
+
+extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double* fhat,
+                                const double* fcoef, double* U, mgrit_stats* stats, igm_stream s) {
+  if (!mg || !u0 || !U) return fail(IGM_ERR_ARG, "null argument");
+  const mgrit_opts& o = mg->o;
+  cudaStream_t st = (cudaStream_t)s;
+  const int N = mg->ops->hi.N;
+  const int nlev = (int)mg->L.size();
+  const bool profile = o.profile != 0;
+  const bool use_graphs = o.graphs != 0 && !profile && nlev > 1;
+  if (fhat && !fcoef) return fail(IGM_ERR_ARG, "fhat given without fcoef");
+  if (!fcoef) fhat = nullptr;
+  const long launches0 = g_launches.load();
+  if (fhat)
+    CU(cudaMemcpyAsync(mg->dfcoef, fcoef, sizeof(double) * (o.Nt + 1), cudaMemcpyHostToDevice, st));
+  CU(cudaMemsetAsync(mg->counters, 0, 2 * sizeof(unsigned long long), st));
+  CU(cudaMemsetAsync(mg->status, 0, sizeof(int), st));
+  for (auto& r : mg->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
+  mg->prof.clear();
+  if (profile && !mg->dlog) {
+    mg->dlog_cap = 4096;
+    mg->dlog = (unsigned long long*)mg->up.raw(sizeof(unsigned long long) * 2 * mg->dlog_cap);
+    if (mg->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(mg->up.err));
+  }
+  if (use_graphs && (mg->g_U != U || mg->g_fhat != fhat || mg->g_stream != st)) {
+    if (mg->gA) cudaGraphExecDestroy(mg->gA);
+    if (mg->gB) cudaGraphExecDestroy(mg->gB);
+    mg->gA = mg->gB = nullptr;
+  }
+  // initial guess: U[0] = u0, U[n>=1] = 0 unless the caller's U is to be kept
+  CU(cudaMemcpyAsync(U, u0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+  if (!o.initial_guess) CU(cudaMemsetAsync(U + N, 0, sizeof(double) * (size_t)o.Nt * N, st));
+  auto t0 = std::chrono::steady_clock::now();
+  std::vector<double> hist;
+  int it = 0;
+  if (nlev == 1) {
+    SWEEP(0, MODE_SEQ, 1, nullptr);
+  } else {
+    const int nint0 = mg->L[0].Nl / o.m;
+    while (true) {
+      if (use_graphs && it > 0) {
+        if (!mg->gA) {
+          igm_status r = capture(mg, true, U, fhat, st, &mg->gA);
+          if (r != IGM_OK) return r;
+        }
+        CU(cudaGraphLaunch(mg->gA, st));
+        g_launches += (o.relax == 1) ? 2 : 1;
+      } else {
+        igm_status r = part_A(mg, it == 0, U, fhat, st, profile);
+        if (r != IGM_OK) return r;
+      }
+      CU(cudaStreamSynchronize(st));
+      double rr = 0.0;
+      for (int j = 0; j < nint0; ++j) rr += mg->hnorms[j];
+      const double rho = std::sqrt(rr);
+      hist.push_back(rho);
+      if (!(rho == rho)) return fail(IGM_ERR_NUMERIC, "NaN in the MGRIT residual");
+      if (rho == 0.0 || rho <= o.tol * hist[0] || it >= o.max_iter) break;
+      if (use_graphs) {
+        if (!mg->gB) {
+          igm_status r = capture(mg, false, U, fhat, st, &mg->gB);
+          if (r != IGM_OK) return r;
+        }
+        CU(cudaGraphLaunch(mg->gB, st));
+        int nb = 0;
+        for (int l = 1; l < nlev; ++l)
+          nb += (l == nlev - 1) ? 1 : (o.relax == 1 ? 3 : 1);
+        g_launches += nb + (nlev - 1);
+      } else {
+        igm_status r = part_B(mg, U, fhat, st, profile);
+        if (r != IGM_OK) return r;
+      }
+      ++it;
+    }
+    if (use_graphs) {
+      mg->g_U = U;
+      mg->g_fhat = fhat;
+      mg->g_stream = st;
+    }
+  }
+  CU(cudaStreamSynchronize(st));
+  auto t1 = std::chrono::steady_clock::now();
+  unsigned long long hc[2] = {0, 0};
+  int hstat = 0;
+  CU(cudaMemcpy(hc, mg->counters, sizeof(hc), cudaMemcpyDeviceToHost));
+  CU(cudaMemcpy(&hstat, mg->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (profile) {
+    const int k = std::min((int)mg->prof.size(), mg->dlog_cap);
+    mg->prof_cyc.assign(2 * (size_t)k, 0);
+    if (k) CU(cudaMemcpy(mg->prof_cyc.data(), mg->dlog, sizeof(unsigned long long) * 2 * k,
+                         cudaMemcpyDeviceToHost));
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iters = it;
+    stats->levels = nlev;
+    for (size_t k = 0; k < hist.size() && k < 256; ++k) stats->res_hist[k] = hist[k];
+    stats->solves = (long)hc[0];
+    stats->vcycles = (long)hc[1];
+    stats->vcyc_mean = hc[0] ? (double)hc[1] / (double)hc[0] : 0.0;
+    stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+    stats->setup_seconds = mg->setup_seconds;
+    stats->launches = g_launches.load() - launches0;
+  }
+  if (hstat == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
+  if (hstat == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "a spatial solve hit max_cycles");
+  if (nlev > 1 && !hist.empty() && !(hist.back() <= o.tol * hist[0]) && hist.back() != 0.0)
+    return fail(IGM_ERR_NOT_CONVERGED, "MGRIT hit max_iter");
+  return IGM_OK;
+}
+
+extern "C" igm_status mgrit_profile(const mgrit_handle* mg, int cap, int* count, int* level,
+                                    int* grid, int* mode, float* ms, long* cycles) {
+  if (!mg || !count) return fail(IGM_ERR_ARG, "null argument");
+  const int k = std::min(cap, (int)std::min(mg->prof.size(), (size_t)mg->dlog_cap));
+  for (int i = 0; i < k; ++i) {
+    const ProfRec& r = mg->prof[i];
+    if (level) level[i] = r.level;
+    if (grid) grid[i] = r.grid;
+    if (mode) mode[i] = r.mode;
+    if (ms) {
+      float t = 0.f;
+      CU(cudaEventElapsedTime(&t, r.e0, r.e1));
+      ms[i] = t;
+    }
+    if (cycles) {
+      const unsigned long long prev = i ? mg->prof_cyc[2 * (i - 1) + 1] : 0ull;
+      cycles[i] = (long)(mg->prof_cyc[2 * i + 1] - prev);
+    }
+  }
+  *count = k;
+  return IGM_OK;
+}
+
+extern "C" igm_status mgrit_solve(const iga_ops* ops, const mgrit_opts* opts, const double* u0,
+                                  const double* fhat, const double* fcoef, double* U,
+                                  mgrit_stats* stats, igm_stream s) {
+  mgrit_handle* mg = nullptr;
+  igm_status r = mgrit_create(ops, opts, &mg);
+  if (r != IGM_OK) return r;
+  r = mgrit_run(mg, u0, fhat, fcoef, U, stats, s);
+  mgrit_destroy(mg);
+  return r;
+}

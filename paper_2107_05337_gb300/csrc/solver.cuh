@@ -1,0 +1,245 @@
+// The spatial solve (Sec. 4 p-multigrid cycle, repeated to a tolerance) and
+// the MGRIT time step (Sec. 3) as CTA-wide device functions.
+#pragma once
+#include "device.cuh"
+
+namespace igm {
+
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = -4, ST_NUMERIC = -6 };
+
+__device__ __forceinline__ void record_status(int* status, int code) {
+  if (status && threadIdx.x == 0) atomicMin(status, code);
+}
+
+// FP64 residual out = b - A x (out may be float: the mixed form's r32);
+// returns ||b - A x||_2^2 computed in FP64.
+template <typename O>
+__device__ double residual64(const PmgD& P, const double* b, const double* x, O* out, double* tm,
+                             double* tk, double* red) {
+  if (P.affine)
+    return apply_A_affine<double>(P.n, P.p, P.bM64, P.bK64, P.bA64, P.bcM64, x,
+                                  (const double*)nullptr, b, out, tm, tk, red);
+  return apply_stencil<double>(P.n, P.w, P.sA64, x, (const double*)nullptr, b, out, red);
+}
+
+// t = b - A x in the smoothing precision (no norm).
+template <typename T>
+__device__ void residualT(const PmgD& P, const T* b, const T* x, T* t, T* tm, T* tk);
+
+template <>
+__device__ void residualT<float>(const PmgD& P, const float* b, const float* x, float* t, float* tm,
+                                 float* tk) {
+  if (P.affine)
+    apply_A_affine<float>(P.n, P.p, P.bM32, P.bK32, P.bA32, P.bcM32, x, (const float*)nullptr, b, t,
+                          tm, tk, (double*)nullptr);
+  else
+    apply_stencil<float>(P.n, P.w, P.sA32, x, (const float*)nullptr, b, t, (double*)nullptr);
+}
+
+template <>
+__device__ void residualT<double>(const PmgD& P, const double* b, const double* x, double* t,
+                                  double* tm, double* tk) {
+  residual64<double>(P, b, x, t, tm, tk, (double*)nullptr);
+}
+
+template <typename T> struct Prec;
+template <> struct Prec<float> {
+  __device__ static const int* Lp(const PmgD& P) { return P.Lptr; }
+  __device__ static const float* Lv(const PmgD& P) { return P.Lval32; }
+  __device__ static const float* Li(const PmgD& P) { return P.Linv32; }
+  __device__ static const float* Uv(const PmgD& P) { return P.Uval32; }
+  __device__ static const float* Ui(const PmgD& P) { return P.Uinv32; }
+  __device__ static const float* Pv(const PmgD& P) { return P.Pval32; }
+  __device__ static const float* PTv(const PmgD& P) { return P.PTval32; }
+  __device__ static const float* MpL(const PmgD& P) { return P.MpL32; }
+  __device__ static const float* M1L(const PmgD& P) { return P.M1L32; }
+  __device__ static const float* HA(const HLevelD& H) { return H.A32; }
+  __device__ static const float* HG(const HLevelD& H) { return H.G32; }
+};
+template <> struct Prec<double> {
+  __device__ static const double* Lv(const PmgD& P) { return P.Lval64; }
+  __device__ static const double* Li(const PmgD& P) { return P.Linv64; }
+  __device__ static const double* Uv(const PmgD& P) { return P.Uval64; }
+  __device__ static const double* Ui(const PmgD& P) { return P.Uinv64; }
+  __device__ static const double* Pv(const PmgD& P) { return P.Pval64; }
+  __device__ static const double* PTv(const PmgD& P) { return P.PTval64; }
+  __device__ static const double* MpL(const PmgD& P) { return P.MpL64; }
+  __device__ static const double* M1L(const PmgD& P) { return P.M1L64; }
+  __device__ static const double* HA(const HLevelD& H) { return H.A64; }
+  __device__ static const double* HG(const HLevelD& H) { return H.G64; }
+};
+
+// v <- U^{-1} L^{-1} v (the ILUT smoother S = (LU)^{-1} applied to v).
+template <typename T>
+__device__ void ilut_apply(const PmgD& P, T* v, T* row) {
+  block_lower_solve<T>(P.n, P.Lptr, P.Lcol, Prec<T>::Lv(P), Prec<T>::Li(P), v, row);
+  block_upper_solve<T>(P.n, P.Uptr, P.Ucol, Prec<T>::Uv(P), Prec<T>::Ui(P), v, row);
+}
+
+// x_k = A_k^{-1} b_k on the coarsest h-level with the FP64 inverse.
+template <typename T>
+__device__ void coarse_solve(int Nc, const double* Cinv, const T* b, T* x) {
+  for_group_rows(Nc, [&](int r, bool act, int gl) {
+    double s = 0.0;
+    if (act)
+      for (int j = gl; j < Nc; j += kGroup) s += Cinv[(size_t)r * Nc + j] * (double)b[j];
+    s = group_sum(s);
+    if (act && gl == 0) x[r] = (T)s;
+  });
+  __syncthreads();
+}
+
+// One W-cycle of h-multigrid at p = 1 (Sec. 4, Fig. 5), interpreting the
+// host-generated op list.  h-level 0 holds b_0 = restricted residual and
+// x_0 = 0 on entry and the coarse correction on exit.
+template <typename T>
+__device__ void wcycle(const PmgD& P, T* A, T* row) {
+  for (int o = 0; o < P.nops; ++o) {
+    const int op = P.ops[o] & 0xff, k = P.ops[o] >> 8;
+    const HLevelD& H = P.h[k];
+    T* xk = A + H.ox;
+    T* bk = A + H.ob;
+    T* tk = A + H.ot;
+    switch (op) {
+      case W_GS:
+        gs_sweep<T>(H.n, Prec<T>::HA(H), Prec<T>::HG(H), bk, xk, row);
+        break;
+      case W_RESTRICT:
+        residual9<T>(H.n, Prec<T>::HA(H), bk, xk, tk);
+        restrict_bilinear<T>(H.n, tk, A + P.h[k + 1].ob, A + P.h[k + 1].ox);
+        break;
+      case W_COARSE:
+        coarse_solve<T>(H.n * H.n, P.Cinv, bk, xk);
+        break;
+      case W_PROLONG:
+        prolong_bilinear<T>(H.n, A + P.h[k + 1].ox, xk);
+        break;
+    }
+  }
+}
+
+// One p-multigrid cycle (Sec. 4, steps 1-5) on A x = b in precision T.
+// t: scratch of N; on entry t may already hold b - A x (t_is_residual).
+// x_is_zero: x = 0 on entry (the first pre-smoothing then needs no product).
+template <typename T>
+__device__ void pmg_cycle(const PmgD& P, const T* b, T* x, T* A, bool t_is_residual, bool x_is_zero) {
+  const int N = P.N;
+  T* t = A + P.o_t;
+  T* tm = A + P.o_u;
+  T* tk = tm + N;
+  T* row = A + P.o_row;
+  for (int s = 0; s < P.nu1; ++s) {
+    const bool zero = x_is_zero && s == 0;
+    if (zero) {
+      for (int i = threadIdx.x; i < N; i += blockDim.x) t[i] = b[i];
+      __syncthreads();
+    } else if (!(s == 0 && t_is_residual)) {
+      residualT<T>(P, b, x, t, tm, tk);
+    }
+    ilut_apply<T>(P, t, row);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = zero ? t[i] : x[i] + t[i];
+    __syncthreads();
+  }
+  if (P.nu1 == 0 && x_is_zero) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = 0;
+    __syncthreads();
+  }
+  // step 2: r_1 = (M_1^L)^{-1} P^T (b - A x)
+  residualT<T>(P, b, x, t, tm, tk);
+  const HLevelD& H0 = P.h[0];
+  csr_scaled<T, false>(P.N1, P.PTptr, P.PTcol, Prec<T>::PTv(P), Prec<T>::M1L(P), t, A + H0.ob);
+  for (int i = threadIdx.x; i < P.N1; i += blockDim.x) A[H0.ox + i] = 0;
+  __syncthreads();
+  // step 3: one W-cycle of h-multigrid on A_1 e_1 = r_1
+  wcycle<T>(P, A, row);
+  // step 4: x += (M_p^L)^{-1} P e_1
+  csr_scaled<T, true>(N, P.Pptr, P.Pcol, Prec<T>::Pv(P), Prec<T>::MpL(P), A + H0.ox, x);
+  // step 5: post-smoothing
+  for (int s = 0; s < P.nu2; ++s) {
+    residualT<T>(P, b, x, t, tm, tk);
+    ilut_apply<T>(P, t, row);
+    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += t[i];
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ double block_dot(const double* a, int N, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) s += a[i] * a[i];
+  return block_sum(s, red);
+}
+
+// Spatial solve of A x = b (b, x FP64 in global memory), warm start x.
+// ncycles > 0: exactly ncycles cycles; else cycle until
+// ||b - A x|| <= tol ||b|| (checked before each cycle) or max_cycles.
+// FP64 form: one cycle = one p-multigrid cycle in FP64.  Mixed form: one
+// cycle = FP64 residual r, then `inner` FP32 cycles on A d = r from d = 0,
+// then x += d (iterative refinement).  Returns the number of cycles.
+__device__ int pmg_solve(const PmgD& P, const double* b, double* x, char* arena, double* red,
+                         int ncycles, int* status) {
+  const int N = P.N;
+  const double nb2 = block_dot(b, N, red);
+  if (nb2 == 0.0) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = 0.0;
+    __syncthreads();
+    return 0;
+  }
+  const double tol2 = P.tol * P.tol * nb2;
+  int cyc = 0;
+  if (P.precision == 0) {
+    double* A = (double*)arena;
+    double* t = A + P.o_t;
+    double* tm = A + P.o_u;
+    double* tk = tm + N;
+    while (true) {
+      const double rr = residual64<double>(P, b, x, t, tm, tk, red);
+      if (!(rr == rr)) { record_status(status, ST_NUMERIC); break; }
+      if (ncycles > 0) {
+        if (cyc >= ncycles) break;
+      } else {
+        if (rr <= tol2) break;
+        if (cyc >= P.max_cycles) { record_status(status, ST_NOT_CONVERGED); break; }
+      }
+      pmg_cycle<double>(P, b, x, A, true, false);
+      ++cyc;
+    }
+  } else {
+    float* A = (float*)arena;
+    float* r = A + P.o_r;
+    float* d = A + P.o_d;
+    double* tm64 = (double*)(A + P.o_d);
+    double* tk64 = tm64 + N;
+    while (true) {
+      if (ncycles > 0 && cyc >= ncycles) break;
+      const double rr = residual64<float>(P, b, x, r, tm64, tk64, red);
+      if (!(rr == rr)) { record_status(status, ST_NUMERIC); break; }
+      if (ncycles == 0) {
+        if (rr <= tol2) break;
+        if (cyc >= P.max_cycles) { record_status(status, ST_NOT_CONVERGED); break; }
+      }
+      for (int k = 0; k < P.inner; ++k) pmg_cycle<float>(P, r, d, A, false, k == 0);
+      for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += (double)d[i];
+      __syncthreads();
+      ++cyc;
+    }
+  }
+  return cyc;
+}
+
+// out = M (u + ug) + scale * fhat in FP64 (the right-hand side of one
+// backward-Euler step, Sec. 3: M u^{n-1} + dt f^n).  tm: N doubles scratch.
+__device__ void build_rhs(const PmgD& P, const double* u, const double* ug, double scale,
+                          const double* fhat, double* out, double* tm) {
+  if (P.affine)
+    apply_A_affine<double>(P.n, P.p, P.bM64, (const double*)nullptr, P.bM64,
+                           (const double*)nullptr, u, ug, (const double*)nullptr, out, tm,
+                           (double*)nullptr, (double*)nullptr);
+  else
+    apply_stencil<double>(P.n, P.w, P.sM64, u, ug, (const double*)nullptr, out, (double*)nullptr);
+  if (fhat && scale != 0.0) {
+    for (int i = threadIdx.x; i < P.N; i += blockDim.x) out[i] += scale * fhat[i];
+    __syncthreads();
+  }
+}
+
+}  // namespace igm
