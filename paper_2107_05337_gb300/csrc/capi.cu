@@ -742,7 +742,10 @@ struct mgrit_handle {
   cudaGraphExec_t gA = nullptr, gB = nullptr;
   const double* g_U = nullptr;
   const double* g_fhat = nullptr;
-  cudaStream_t g_stream = nullptr;
+  // the run executes on this stream (graph capture is not allowed on the
+  // legacy default stream), ordered after and before the caller's stream
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // per-launch profile of the last run
   std::vector<ProfRec> prof;
   std::vector<unsigned long long> prof_cyc;  // counter snapshots after each launch
@@ -754,6 +757,9 @@ struct mgrit_handle {
     for (auto& r : prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
     for (auto* h : owned) pmg_destroy(h);
     if (hnorms) cudaFreeHost(hnorms);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (own) cudaStreamDestroy(own);
   }
 };
 
@@ -802,6 +808,9 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   mg->dfcoef = (double*)up.raw(sizeof(double) * (size_t)(o.Nt + 1));
   if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
   CU(cudaMallocHost(&mg->hnorms, sizeof(double) * mg->max_grid));
+  CU(cudaStreamCreateWithFlags(&mg->own, cudaStreamNonBlocking));
+  CU(cudaEventCreateWithFlags(&mg->ev_in, cudaEventDisableTiming));
+  CU(cudaEventCreateWithFlags(&mg->ev_out, cudaEventDisableTiming));
   for (int l = 0; l < nlev; ++l) {
     igm_status r = ensure_arena(L[l].h, mg->max_grid);
     if (r != IGM_OK) return r;
@@ -928,7 +937,10 @@ extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double
                                 const double* fcoef, double* U, mgrit_stats* stats, igm_stream s) {
   if (!mg || !u0 || !U) return fail(IGM_ERR_ARG, "null argument");
   const mgrit_opts& o = mg->o;
-  cudaStream_t st = (cudaStream_t)s;
+  cudaStream_t user = (cudaStream_t)s;
+  cudaStream_t st = mg->own;
+  CU(cudaEventRecord(mg->ev_in, user));
+  CU(cudaStreamWaitEvent(st, mg->ev_in, 0));
   const int N = mg->ops->hi.N;
   const int nlev = (int)mg->L.size();
   const bool profile = o.profile != 0;
@@ -947,7 +959,7 @@ extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double
     mg->dlog = (unsigned long long*)mg->up.raw(sizeof(unsigned long long) * 2 * mg->dlog_cap);
     if (mg->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(mg->up.err));
   }
-  if (use_graphs && (mg->g_U != U || mg->g_fhat != fhat || mg->g_stream != st)) {
+  if (use_graphs && (mg->g_U != U || mg->g_fhat != fhat)) {
     if (mg->gA) cudaGraphExecDestroy(mg->gA);
     if (mg->gB) cudaGraphExecDestroy(mg->gB);
     mg->gA = mg->gB = nullptr;
@@ -1000,9 +1012,10 @@ extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double
     if (use_graphs) {
       mg->g_U = U;
       mg->g_fhat = fhat;
-      mg->g_stream = st;
     }
   }
+  CU(cudaEventRecord(mg->ev_out, st));
+  CU(cudaStreamWaitEvent(user, mg->ev_out, 0));
   CU(cudaStreamSynchronize(st));
   auto t1 = std::chrono::steady_clock::now();
   unsigned long long hc[2] = {0, 0};
