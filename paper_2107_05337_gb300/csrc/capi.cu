@@ -14,7 +14,7 @@
 
 #include "../../include/igamgrit.h"
 #include "host_setup.h"
-#include "solver.cuh"
+#include "kernels.h"
 
 using namespace igm;
 
@@ -107,6 +107,7 @@ struct pmg_handle {
   Uploader up;
   bool arena_smem = true;
   long arena_bytes = 0;
+  long smem_bytes = 0;      // dynamic shared memory per CTA of the solve kernels
   char* garena = nullptr;   // global arena for grid_capacity CTAs when not in shared memory
   int grid_capacity = 0;
 };
@@ -271,166 +272,26 @@ extern "C" igm_status iga_project(const iga_ops* ops, const double* fq, double* 
 // ---------------------------------------------------------------------------
 // kernels
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ char* cta_arena(char* garena, long bytes, bool smem) {
-  extern __shared__ __align__(16) char dyn_smem[];
-  return smem ? dyn_smem : garena + (size_t)blockIdx.x * bytes;
+namespace igm {
+cudaError_t launch_pmg_solve(int prec, const PmgD& P, int grid, long smem, cudaStream_t st,
+                             const double* b, double* x, long ld, int ncycles, int* cycles_out,
+                             int* status, char* garena) {
+  return prec ? launch_pmg_solve_f32(P, grid, smem, st, b, x, ld, ncycles, cycles_out, status, garena)
+              : launch_pmg_solve_f64(P, grid, smem, st, b, x, ld, ncycles, cycles_out, status, garena);
 }
-
-__global__ void __launch_bounds__(kBlock) k_apply_op(PmgD P, int which, const double* x,
-                                                     double* y, long ld, double* scratch) {
-  const double* xc = x + (size_t)blockIdx.x * ld;
-  double* yc = y + (size_t)blockIdx.x * ld;
-  double* tm = scratch + (size_t)blockIdx.x * 2 * P.N;
-  double* tk = tm + P.N;
-  if (P.affine) {
-    if (which == 0)
-      apply_A_affine<double>(P.n, P.p, P.bM64, (const double*)nullptr, P.bM64,
-                             (const double*)nullptr, xc, (const double*)nullptr,
-                             (const double*)nullptr, yc, tm, (double*)nullptr, (double*)nullptr);
-    else
-      apply_A_affine<double>(P.n, P.p, P.bM64, P.bK64, P.bK64, P.bM64, xc, (const double*)nullptr,
-                             (const double*)nullptr, yc, tm, tk, (double*)nullptr);
-  } else {
-    apply_stencil<double>(P.n, P.w, which == 0 ? P.sM64 : P.sA64, xc, (const double*)nullptr,
-                          (const double*)nullptr, yc, (double*)nullptr);
-  }
+cudaError_t launch_ilut_apply(int prec, const PmgD& P, int grid, long smem, cudaStream_t st,
+                              const double* r, double* z, long ld, char* garena, int* status) {
+  return prec ? launch_ilut_apply_f32(P, grid, smem, st, r, z, ld, garena, status)
+              : launch_ilut_apply_f64(P, grid, smem, st, r, z, ld, garena, status);
 }
-
-__global__ void __launch_bounds__(kBlock) k_pmg_solve(PmgD P, const double* b, double* x, long ld,
-                                                      int ncycles, int* cycles_out, int* status,
-                                                      char* garena, int smem) {
-  __shared__ double red[32];
-  char* arena = cta_arena(garena, P.arena_bytes, smem);
-  const double* bc = b + (size_t)blockIdx.x * ld;
-  double* xc = x + (size_t)blockIdx.x * ld;
-  int c = pmg_solve(P, bc, xc, arena, red, ncycles, status);
-  if (threadIdx.x == 0 && cycles_out) cycles_out[blockIdx.x] = c;
+cudaError_t launch_mgrit_sweep(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st) {
+  return prec ? launch_mgrit_sweep_f32(a, grid, smem, st) : launch_mgrit_sweep_f64(a, grid, smem, st);
 }
-
-__global__ void __launch_bounds__(kBlock) k_ilut_apply(PmgD P, const double* r, double* z, long ld,
-                                                       char* garena, int smem) {
-  char* arena = cta_arena(garena, P.arena_bytes, smem);
-  const double* rc = r + (size_t)blockIdx.x * ld;
-  double* zc = z + (size_t)blockIdx.x * ld;
-  if (P.precision == 0) {
-    double* A = (double*)arena;
-    double* t = A + P.o_t;
-    for (int i = threadIdx.x; i < P.N; i += blockDim.x) t[i] = rc[i];
-    __syncthreads();
-    ilut_apply<double>(P, t, A + P.o_row);
-    for (int i = threadIdx.x; i < P.N; i += blockDim.x) zc[i] = t[i];
-  } else {
-    float* A = (float*)arena;
-    float* t = A + P.o_t;
-    for (int i = threadIdx.x; i < P.N; i += blockDim.x) t[i] = (float)rc[i];
-    __syncthreads();
-    ilut_apply<float>(P, t, A + P.o_row);
-    for (int i = threadIdx.x; i < P.N; i += blockDim.x) zc[i] = (double)t[i];
-  }
+cudaError_t set_solver_smem(long bytes) {
+  cudaError_t e = set_smem_f32(bytes);
+  return e == cudaSuccess ? set_smem_f64(bytes) : e;
 }
-
-// MGRIT sweep modes (Sec. 3): F-relaxation, C-relaxation, F-relaxation plus
-// C-point residual and injection, coarse correction plus F-relaxation (ideal
-// interpolation), and sequential stepping on the coarsest level.
-enum : int { MODE_F = 0, MODE_C = 1, MODE_FR = 2, MODE_CF = 3, MODE_SEQ = 4, MODE_R = 5 };
-
-struct SweepArgs {
-  PmgD P;
-  int mode, m, Nl, nint;
-  double* W;              // [Nl+1][N]: the part of u each step's solve produces
-  const double* g;        // [Nl+1][N] right-hand side g^(l) (nullptr on the fine level)
-  const double* Wc;       // next level's W and g (correction)
-  const double* gc;
-  double* gnext;          // next level's g, written by the residual
-  double* norms;          // [nint] ||r_j||^2 (fine level) or nullptr
-  const double* fhat;     // fine level source profile or nullptr
-  const double* fcoef;    // device [Nt+1] time factors
-  double dt0;
-  double* scratch;        // per CTA: 2 N doubles (rhs, residual iterate)
-  char* garena;
-  int smem;
-  int ncycles;
-  unsigned long long* counters;  // [0] solves, [1] cycles
-  int* status;
-};
-
-__device__ void mgrit_step(const SweepArgs& a, char* arena, double* red, int n, bool residual,
-                           int j) {
-  const PmgD& P = a.P;
-  const int N = P.N;
-  double* rhs = a.scratch + (size_t)blockIdx.x * 2 * N;
-  double* xr = rhs + N;
-  double* tm = (P.precision == 0) ? (double*)arena + P.o_u : (double*)((float*)arena + P.o_d);
-  const double* u = a.W + (size_t)(n - 1) * N;
-  const double* ug = a.g ? a.g + (size_t)(n - 1) * N : nullptr;
-  const double scale = a.fhat ? a.dt0 * a.fcoef[n] : 0.0;
-  build_rhs(P, u, ug, scale, a.fhat, rhs, tm);
-  double* Wn = a.W + (size_t)n * N;
-  double* x = Wn;
-  if (residual) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) xr[i] = Wn[i];
-    __syncthreads();
-    x = xr;
-  }
-  int cyc = pmg_solve(P, rhs, x, arena, red, a.ncycles, a.status);
-  if (threadIdx.x == 0 && a.counters) {
-    atomicAdd(&a.counters[0], 1ull);
-    atomicAdd(&a.counters[1], (unsigned long long)cyc);
-  }
-  if (residual) {
-    double* gout = a.gnext + (size_t)(j + 1) * N;
-    double s = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-      const double r = xr[i] - Wn[i];
-      gout[i] = r;
-      s += r * r;
-    }
-    s = block_sum(s, red);
-    if (a.norms && threadIdx.x == 0) a.norms[j] = s;
-  }
-}
-
-__global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
-  __shared__ double red[32];
-  char* arena = cta_arena(a.garena, a.P.arena_bytes, a.smem);
-  const int j = blockIdx.x, m = a.m, N = a.P.N;
-  switch (a.mode) {
-    case MODE_C:
-      mgrit_step(a, arena, red, (j + 1) * m, false, j);
-      break;
-    case MODE_CF: {
-      // u_{jm} += u^(l+1)_j (coarse correction at the C-point owned by this CTA)
-      if (j >= 1) {
-        double* w = a.W + (size_t)(j * m) * N;
-        const double* wc = a.Wc + (size_t)j * N;
-        const double* gc = a.gc + (size_t)j * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
-      }
-      if (j == a.nint - 1) {
-        double* w = a.W + (size_t)a.Nl * N;
-        const double* wc = a.Wc + (size_t)a.nint * N;
-        const double* gc = a.gc + (size_t)a.nint * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
-      }
-      __syncthreads();
-    }  // fall through: F-relaxation from the corrected C-point
-    case MODE_F:
-    case MODE_FR:
-      for (int k = 1; k < m; ++k) mgrit_step(a, arena, red, j * m + k, false, j);
-      if (a.mode == MODE_FR) mgrit_step(a, arena, red, (j + 1) * m, true, j);
-      break;
-    case MODE_R:
-      mgrit_step(a, arena, red, (j + 1) * m, true, j);
-      break;
-    case MODE_SEQ:
-      for (int n = 1; n <= a.Nl; ++n) mgrit_step(a, arena, red, n, false, 0);
-      break;
-  }
-}
-
-static cudaError_t set_smem(const void* fn, long bytes) {
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
+}  // namespace igm
 
 // ---------------------------------------------------------------------------
 // pmg_setup
@@ -464,6 +325,103 @@ static void gen_wcycle(int k, int last, std::vector<int>& ops) {
 
 static int align4(int x) { return (x + 3) & ~3; }
 
+// Pack the block-row records of one triangular factor (layout: RecLayout in
+// device.cuh).  Record k covers grid row k (lower) or n-1-k (upper).
+template <typename T>
+static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>& out,
+                                std::vector<long long>& off, int& max_bytes) {
+  const int n = B.n;
+  const size_t blk = (size_t)n * (n + 1) / 2;
+  out.clear();
+  off.clear();
+  max_bytes = 0;
+  for (int k = 0; k < n; ++k) {
+    const int by = upper ? n - 1 - k : k;
+    const int e0 = B.off.ptr[(size_t)by * n], e1 = B.off.ptr[(size_t)by * n + n];
+    const int nnz = e1 - e0;
+    if (nnz > 65535) return "block row has more than 65535 off-block entries";
+    int base = by * n, cmax = by * n;
+    if (nnz > 0) {
+      base = B.off.col[e0];
+      cmax = base;
+      for (int e = e0; e < e1; ++e) {
+        base = std::min(base, B.off.col[e]);
+        cmax = std::max(cmax, B.off.col[e]);
+      }
+    }
+    if (cmax - base > 65535) return "off-block column span exceeds 16 bits";
+    const RecLayout<T> lay(n, nnz);
+    std::vector<char> rec(lay.bytes, 0);
+    int* hdr = (int*)rec.data();
+    hdr[0] = base; hdr[1] = nnz; hdr[2] = by; hdr[3] = 0;
+    uint16_t* ptr = (uint16_t*)(rec.data() + lay.o_ptr);
+    uint16_t* col = (uint16_t*)(rec.data() + lay.o_col);
+    T* val = (T*)(rec.data() + lay.o_val);
+    T* inv = (T*)(rec.data() + lay.o_inv);
+    for (int r = 0; r <= n; ++r) ptr[r] = (uint16_t)(B.off.ptr[(size_t)by * n + r] - e0);
+    for (int e = e0; e < e1; ++e) {
+      col[e - e0] = (uint16_t)(B.off.col[e] - base);
+      val[e - e0] = (T)B.off.val[e];
+    }
+    for (size_t q = 0; q < blk; ++q) inv[q] = (T)B.inv[(size_t)by * blk + q];
+    off.push_back((long long)out.size());
+    out.insert(out.end(), rec.begin(), rec.end());
+    max_bytes = std::max(max_bytes, lay.bytes);
+  }
+  off.push_back((long long)out.size());
+  return "";
+}
+
+// 1D transfer factor between the interior order-p functions (rows) and the
+// interior order-1 functions (columns) on the same knots with the same rule,
+// stored as bands of width w with per-row starts (Sec. 4, Eq. (PM) on the
+// affine map: P = P1 (x) P1).  Returns false if a row does not fit the band.
+static bool transfer_bands(const Discretisation& hi, const Discretisation& lo, int w,
+                           std::vector<int>& js, std::vector<double>& band,
+                           std::vector<int>& is, std::vector<double>& tband) {
+  const int n = hi.n, n1 = lo.n, p = hi.p, nq = hi.nq;
+  std::vector<double> P1((size_t)n * n1, 0.0), gx, gw;
+  gauss_legendre(nq, gx, gw);
+  std::vector<double> Nh(p + 1), Nl(2);
+  for (int e = 0; e < hi.nel; ++e) {
+    const double x0 = hi.knots[e + p], x1 = hi.knots[e + p + 1];
+    for (int a = 0; a < nq; ++a) {
+      const double x = 0.5 * (x1 - x0) * gx[a] + 0.5 * (x0 + x1);
+      const double wq = 0.5 * (x1 - x0) * gw[a];
+      basis_on_span(hi.knots, p, e + p, x, Nh.data(), nullptr);
+      basis_on_span(lo.knots, 1, e + 1, x, Nl.data(), nullptr);
+      for (int la = 0; la <= p; ++la)
+        for (int lb = 0; lb <= 1; ++lb) {
+          const int i = e + la - 1, j = e + lb - 1;
+          if (i < 0 || j < 0 || i >= n || j >= n1) continue;
+          P1[(size_t)i * n1 + j] += wq * Nh[la] * Nl[lb];
+        }
+    }
+  }
+  if (n1 < w || n < w) return false;
+  auto fill = [&](int rows, int cols, bool trans, std::vector<int>& st, std::vector<double>& bd) {
+    st.assign(rows, 0);
+    bd.assign((size_t)rows * w, 0.0);
+    for (int r = 0; r < rows; ++r) {
+      int lo_c = -1, hi_c = -1;
+      for (int c2 = 0; c2 < cols; ++c2) {
+        const double v = trans ? P1[(size_t)c2 * n1 + r] : P1[(size_t)r * n1 + c2];
+        if (v != 0.0) { if (lo_c < 0) lo_c = c2; hi_c = c2; }
+      }
+      if (lo_c < 0) lo_c = hi_c = 0;
+      if (hi_c - lo_c + 1 > w) return false;
+      const int s0 = std::min(lo_c, cols - w);
+      st[r] = s0;
+      for (int k = 0; k < w; ++k) {
+        const int c2 = s0 + k;
+        bd[(size_t)r * w + k] = trans ? P1[(size_t)c2 * n1 + r] : P1[(size_t)r * n1 + c2];
+      }
+    }
+    return true;
+  };
+  return fill(n, n1, false, js, band) && fill(n1, n, true, is, tband);
+}
+
 extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_opts* opts,
                                 pmg_handle** out) {
   if (!ops || !out) return fail(IGM_ERR_ARG, "null argument");
@@ -475,10 +433,12 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   if (o.precision != 0 && o.precision != 1) return fail(IGM_ERR_ARG, "precision must be 0 or 1");
   if (o.inner_cycles < 1) return fail(IGM_ERR_ARG, "inner_cycles must be >= 1");
   if (o.max_cycles < 1) return fail(IGM_ERR_ARG, "max_cycles must be >= 1");
+  if (!(o.tol >= 0.0)) return fail(IGM_ERR_ARG, "tol must be >= 0");
   h->c = kappa_dt;
   const Discretisation& hi = ops->hi;
   const Discretisation& lo = ops->lo;
   const int n = hi.n, N = hi.N, p = hi.p, W = 2 * p + 1;
+  if (lo.n > 128) return fail(IGM_ERR_ARG, "nel > 129 is not supported by the p=1 sweeps");
   // A = M + c K (Sec. 4: the backward-Euler step matrix)
   Stencil A = hi.M;
   for (size_t i = 0; i < A.val.size(); ++i) A.val[i] = hi.M.val[i] + kappa_dt * hi.K.val[i];
@@ -521,26 +481,56 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.sA64 = up.put(A.val);
   d.sA32 = up.put32(A.val);
   d.sM64 = ops->sM64;
-  d.Lptr = up.put(BL.off.ptr); d.Lcol = up.put(BL.off.col);
-  d.Lval64 = up.put(BL.off.val); d.Lval32 = up.put32(BL.off.val);
-  d.Linv64 = up.put(BL.inv); d.Linv32 = up.put32(BL.inv);
-  d.Uptr = up.put(BU.off.ptr); d.Ucol = up.put(BU.off.col);
-  d.Uval64 = up.put(BU.off.val); d.Uval32 = up.put32(BU.off.val);
-  d.Uinv64 = up.put(BU.inv); d.Uinv32 = up.put32(BU.inv);
-  // a row with no off-block entries still needs a valid pointer array
+  // ILUT records in the smoothing precision
+  std::vector<char> recL, recU;
+  std::vector<long long> offL, offU;
+  int maxL = 0, maxU = 0;
+  if (o.precision == 0) {
+    e = pack_records<double>(BL, false, recL, offL, maxL);
+    if (e.empty()) e = pack_records<double>(BU, true, recU, offU, maxU);
+  } else {
+    e = pack_records<float>(BL, false, recL, offL, maxL);
+    if (e.empty()) e = pack_records<float>(BU, true, recU, offU, maxU);
+  }
+  if (!e.empty()) return fail(IGM_ERR_ARG, e);
+  d.Lrec.recs = up.put(recL); d.Lrec.off = up.put(offL); d.Lrec.max_bytes = maxL;
+  d.Urec.recs = up.put(recU); d.Urec.off = up.put(offU); d.Urec.max_bytes = maxU;
+  d.slot_bytes = (std::max(maxL, maxU) + 127) & ~127;
+  // transfers: CSR always (curved), tensor-product bands on the affine map
   d.N1 = lo.N;
+  d.n1 = lo.n;
   d.Pptr = up.put(ops->P.ptr); d.Pcol = up.put(ops->P.col);
   d.Pval64 = up.put(ops->P.val); d.Pval32 = up.put32(ops->P.val);
   d.PTptr = up.put(ops->PT.ptr); d.PTcol = up.put(ops->PT.col);
   d.PTval64 = up.put(ops->PT.val); d.PTval32 = up.put32(ops->PT.val);
   d.MpL64 = up.put(hi.lumped); d.MpL32 = up.put32(hi.lumped);
   d.M1L64 = up.put(lo.lumped); d.M1L32 = up.put32(lo.lumped);
+  d.wP = p + 2;
+  if (d.affine) {
+    std::vector<int> js, is;
+    std::vector<double> pb, ptb;
+    if (transfer_bands(hi, lo, d.wP, js, pb, is, ptb)) {
+      d.tp = 1;
+      d.Pjs = up.put(js); d.PTis = up.put(is);
+      d.Pb64 = up.put(pb); d.PTb64 = up.put(ptb);
+      d.Pb32 = up.put32(pb); d.PTb32 = up.put32(ptb);
+    }
+  }
+  // h-levels: 9-point stencils and Gauss--Seidel coefficients
   d.nh = (int)H.size();
   for (int k = 0; k < d.nh; ++k) {
-    std::vector<double> G;
-    e = gs_blocks(H[k], G);
-    if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
-    d.h[k].n = H[k].n;
+    const int nk = H[k].n, Nk = nk * nk;
+    std::vector<double> G((size_t)Nk * G_NCOEF);
+    for (int i = 0; i < Nk; ++i) {
+      const double* a = &H[k].val[(size_t)i * 9];
+      if (a[4] == 0.0) return fail(IGM_ERR_NUMERIC, "zero diagonal at p = 1");
+      double* g = &G[(size_t)i * G_NCOEF];
+      g[G_SW] = a[0]; g[G_S] = a[1]; g[G_SE] = a[2]; g[G_E] = a[5];
+      g[G_NW] = a[6]; g[G_N] = a[7]; g[G_NE] = a[8];
+      g[G_ALPHA] = (i % nk) > 0 ? -a[3] / a[4] : 0.0;
+      g[G_INVC] = 1.0 / a[4];
+    }
+    d.h[k].n = nk;
     d.h[k].A64 = up.put(H[k].val);
     d.h[k].A32 = up.put32(H[k].val);
     d.h[k].G64 = up.put(G);
@@ -559,7 +549,9 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.nu2 = o.nu2;
   d.max_cycles = o.max_cycles;
   d.tol = o.tol;
-  // arena layout, in elements of the smoothing precision
+  // arena layout, in elements of the smoothing precision:
+  // [r][d] (mixed only) [t] [U: FP32/64 SpMM temporaries | h-level vectors + transfer temp] [row]
+  // The mixed form's FP64 residual temporaries (2N doubles) alias d, t and U.
   const int es = o.precision == 0 ? 8 : 4;
   int off = 0;
   if (o.precision == 1) {
@@ -574,19 +566,30 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     d.h[k].ob = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
     d.h[k].ot = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
   }
-  off += std::max(align4(2 * N) + align4(N), hsum);
+  d.o_tr = d.o_u + hsum;
+  off += std::max(align4(2 * N) + align4(N), hsum + align4(n * lo.n));
   d.o_row = off;
   off = align4(off + std::max(n, lo.n) + 4);
   h->arena_bytes = (long)off * es;
   d.arena_bytes = h->arena_bytes;
   if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
-  const int optin = dev_smem_optin() - 1024;
-  h->arena_smem = h->arena_bytes <= optin;
+  // shared memory: record ring (2..4 stages) + mbarriers, then the arena if it fits
+  const long optin = dev_smem_optin() - 1024;
+  const long bars = 8 * kMaxStage;
+  auto ring_of = [&](int st) { return (long)st * d.slot_bytes + bars; };
+  d.arena_smem = 0;
+  d.nstage = 0;
+  for (int st = kMaxStage; st >= 2 && !d.nstage; --st)
+    if (ring_of(st) + h->arena_bytes <= optin) { d.nstage = st; d.arena_smem = 1; }
+  for (int st = kMaxStage; st >= 1 && !d.nstage; --st)
+    if (ring_of(st) <= optin) d.nstage = st;
+  if (!d.nstage) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
+  d.ring_bytes = ring_of(d.nstage);
+  h->arena_smem = d.arena_smem != 0;
+  h->smem_bytes = d.ring_bytes + (d.arena_smem ? h->arena_bytes : 0);
   static bool attr_done = false;
   if (!attr_done) {
-    cudaError_t ce = set_smem((const void*)k_pmg_solve, optin);
-    if (ce == cudaSuccess) ce = set_smem((const void*)k_mgrit_sweep, optin);
-    if (ce == cudaSuccess) ce = set_smem((const void*)k_ilut_apply, optin);
+    cudaError_t ce = set_solver_smem(optin);
     if (ce != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(ce));
     attr_done = true;
   }
@@ -611,7 +614,7 @@ static igm_status ensure_arena(pmg_handle* h, int grid) {
   return IGM_OK;
 }
 
-static long smem_of(const pmg_handle* h) { return h->arena_smem ? h->arena_bytes : 0; }
+static long smem_of(const pmg_handle* h) { return h->smem_bytes; }
 
 extern "C" igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long ld,
                                  int ncycles, int* cycles_out, igm_stream s) {
@@ -626,10 +629,9 @@ extern "C" igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, doubl
   CU(cudaMallocAsync(&dcyc, sizeof(int) * (nrhs + 1), st));
   dstat = dcyc + nrhs;
   CU(cudaMemsetAsync(dcyc, 0, sizeof(int) * (nrhs + 1), st));
-  k_pmg_solve<<<nrhs, kBlock, smem_of(h), st>>>(h->d, b, x, ld, ncycles, dcyc, dstat, h->garena,
-                                                 h->arena_smem ? 1 : 0);
+  CU(launch_pmg_solve(h->d.precision, h->d, nrhs, smem_of(h), st, b, x, ld, ncycles, dcyc, dstat,
+                      h->garena));
   g_launches++;
-  CU(cudaGetLastError());
   std::vector<int> hc(nrhs + 1);
   CU(cudaMemcpyAsync(hc.data(), dcyc, sizeof(int) * (nrhs + 1), cudaMemcpyDeviceToHost, st));
   CU(cudaFreeAsync(dcyc, st));
@@ -647,10 +649,9 @@ extern "C" igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, d
   if (nrhs == 0) return IGM_OK;
   igm_status rs = ensure_arena(h, nrhs);
   if (rs != IGM_OK) return rs;
-  k_ilut_apply<<<nrhs, kBlock, smem_of(h), (cudaStream_t)s>>>(h->d, r, z, ld, h->garena,
-                                                                h->arena_smem ? 1 : 0);
+  CU(launch_ilut_apply(h->d.precision, h->d, nrhs, smem_of(h), (cudaStream_t)s, r, z, ld,
+                       h->garena, nullptr));
   g_launches++;
-  CU(cudaGetLastError());
   return IGM_OK;
 }
 
@@ -684,9 +685,8 @@ extern "C" igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const d
   cudaStream_t st = (cudaStream_t)s;
   double* scratch = nullptr;
   CU(cudaMallocAsync(&scratch, sizeof(double) * 2 * (size_t)d.N * nrhs, st));
-  k_apply_op<<<nrhs, kBlock, 0, st>>>(d, which, x, y, ld, scratch);
+  CU(launch_apply_op(d, which, nrhs, x, y, ld, scratch, st));
   g_launches++;
-  CU(cudaGetLastError());
   CU(cudaFreeAsync(scratch, st));
   return IGM_OK;
 }
@@ -848,7 +848,6 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
   a.dt0 = L[0].dt;
   a.scratch = mg->scratch;
   a.garena = L[l].h->garena;
-  a.smem = L[l].h->arena_smem ? 1 : 0;
   a.ncycles = 0;
   a.counters = mg->counters;
   a.status = mg->status;
@@ -858,9 +857,8 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
     CU(cudaEventCreate(&rec.e1));
     CU(cudaEventRecord(rec.e0, st));
   }
-  k_mgrit_sweep<<<grid, kBlock, smem_of(L[l].h), st>>>(a);
+  CU(launch_mgrit_sweep(a.P.precision, a, grid, smem_of(L[l].h), st));
   g_launches++;
-  CU(cudaGetLastError());
   if (profile) {
     CU(cudaEventRecord(rec.e1, st));
     const int k = (int)mg->prof.size();

@@ -14,16 +14,35 @@ namespace igm {
 constexpr int kBlock = 512;       // threads per CTA of the solve kernels
 constexpr int kGroup = 4;         // lanes cooperating on one matrix row
 constexpr int kMaxH = 8;          // max h-multigrid levels at p = 1
+constexpr int kMaxStage = 4;      // max depth of the record ring
+constexpr long kSpinLimit = 1L << 22;  // bounded mbarrier waits (each try_wait may suspend)
 
 enum WOp : int { W_GS = 0, W_RESTRICT = 1, W_COARSE = 2, W_PROLONG = 3 };
+
+// device status codes (the igm_status values)
+enum : int { ST_OK = 0, ST_NOT_CONVERGED = -4, ST_TIMEOUT = -5, ST_NUMERIC = -6 };
+
+// Gauss--Seidel coefficients per unknown, in this order.
+enum GsCoef : int { G_SW = 0, G_S, G_SE, G_E, G_NW, G_N, G_NE, G_ALPHA, G_INVC, G_NCOEF };
 
 struct HLevelD {
   int n;                       // unknowns per direction (N_k = n*n)
   const double* A64;           // 9-point stencil [N_k][9], (dy+1)*3 + (dx+1)
   const float* A32;
-  const double* G64;           // Gauss--Seidel block inverses: n blocks of n(n+1)/2 (lower packed)
-  const float* G32;
+  const double* G64;           // Gauss--Seidel coefficients [N_k][G_NCOEF]:
+  const float* G32;            //   the 7 non-W off-diagonal couplings, alpha = -a_W/a_C, 1/a_C
   int ox, ob, ot;              // arena element offsets of x_k, b_k, t_k
+};
+
+// Block-row records of one triangular factor, streamed into shared memory:
+// record k (grid row k for L, n-1-k for U) at recs + off[k], off[n] = end.
+// Layout (all parts 16-byte aligned): int header[4] = {base, nnz, row, 0};
+// uint16 ptr[n+1] (entry offsets); uint16 col[nnz] (column - base);
+// T val[nnz]; T inv[n(n+1)/2] (packed dense inverse of the diagonal block).
+struct RecSet {
+  const char* recs;
+  const long long* off;
+  int max_bytes;
 };
 
 // Everything one spatial solve needs, by value as a kernel parameter.
@@ -36,15 +55,17 @@ struct PmgD {
   // curved operator: stencils [N][(2p+1)^2]
   const double *sA64, *sM64;
   const float* sA32;
-  // ILUT factors in block-row form
-  const int *Lptr, *Lcol, *Uptr, *Ucol;
-  const double *Lval64, *Uval64, *Linv64, *Uinv64;
-  const float *Lval32, *Uval32, *Linv32, *Uinv32;
+  // ILUT factors as block-row records in the smoothing precision
+  RecSet Lrec, Urec;
+  int nstage, slot_bytes;      // record ring: nstage slots of slot_bytes
   // L2 transfers between order p and order 1 (Sec. 4, Eq. (prolongation))
-  int N1;
-  const int *Pptr, *Pcol, *PTptr, *PTcol;
+  int N1, n1, wP, tp;          // tp: tensor-product transfers with 1D bands of width wP
+  const int *Pptr, *Pcol, *PTptr, *PTcol;        // curved: CSR of P and P^T
   const double *Pval64, *PTval64, *MpL64, *M1L64;
   const float *Pval32, *PTval32, *MpL32, *M1L32;
+  const int *Pjs, *PTis;                          // affine: band starts of P1 [n], P1^T [n1]
+  const double *Pb64, *PTb64;                     // affine: bands [n][wP], [n1][wP]
+  const float *Pb32, *PTb32;
   // h-multigrid at p = 1
   int nh;
   HLevelD h[kMaxH];
@@ -56,9 +77,71 @@ struct PmgD {
   int inner, nu1, nu2, max_cycles;
   double tol;
   // arena layout (element offsets in the smoothing precision)
-  int o_r, o_d, o_t, o_u, o_row;
+  int o_r, o_d, o_t, o_u, o_row, o_tr;  // o_tr: transfer temporary
   long arena_bytes;
+  // dynamic shared memory: [record ring: nstage * slot_bytes][mbarriers: 8 * kMaxStage]
+  // followed by the arena when arena_smem
+  long ring_bytes;
+  int arena_smem;
 };
+
+// ---------------------------------------------------------------------------
+// asynchronous bulk copies (TMA, 1D) into shared memory with mbarriers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"(smem_u32(b)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// Bounded wait: false after kSpinLimit unsuccessful polls (the caller then
+// records IGM_ERR_TIMEOUT and abandons the solve instead of hanging).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (long k = 0; k < kSpinLimit; ++k)
+    if (mbar_try_wait(b, parity)) return true;
+  return false;
+}
+
+// Per-CTA state of the record ring: the expected parity of every stage.
+struct Pipe {
+  char* ring;
+  uint64_t* bar;
+  int nstage, slot;
+  uint32_t phase;
+  bool dead;      // set (CTA-uniformly) after a wait timed out: no further copies
+};
+
+// Initialise the ring's mbarriers (whole CTA; once per kernel).
+__device__ __forceinline__ void pipe_init(Pipe& pp) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < pp.nstage; ++s) mbar_init(&pp.bar[s], 1);
+    fence_mbar_init();
+  }
+  pp.phase = 0;
+  pp.dead = false;
+  __syncthreads();
+}
 
 // ---------------------------------------------------------------------------
 // reductions
@@ -210,104 +293,217 @@ __device__ __forceinline__ size_t upper_off(int i, int n) {
   return (size_t)i * n - (size_t)i * (i - 1) / 2;
 }
 
-// v <- L^{-1} v for a unit lower factor in block-row form.  Grid rows are
-// processed in order; within a grid row, t = v - (off-block part) is formed
-// in parallel, then v_row = inv(L_D) t by a packed dense product.
+__device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
+
+// Byte offsets inside a record (must match the host packing in capi.cu).
 template <typename T>
-__device__ void block_lower_solve(int n, const int* ptr, const int* col, const T* val, const T* inv,
-                                  T* v, T* row) {
-  const size_t blk = lower_off(n);
-  for (int by = 0; by < n; ++by) {
-    for_group_rows(n, [&](int r, bool act, int gl) {
-      T s = 0;
-      if (act) {
-        const int i = by * n + r;
-        for (int k = ptr[i] + gl; k < ptr[i + 1]; k += kGroup) s += val[k] * v[col[k]];
-      }
-      s = group_sum(s);
-      if (act && gl == 0) row[r] = v[by * n + r] - s;
-    });
-    __syncthreads();
-    const T* D = inv + (size_t)by * blk;
-    for_group_rows(n, [&](int r, bool act, int gl) {
-      T s = 0;
-      if (act) {
-        const T* Dr = D + lower_off(r);
-        for (int j = gl; j <= r; j += kGroup) s += Dr[j] * row[j];
-      }
-      s = group_sum(s);
-      if (act && gl == 0) v[by * n + r] = s;
-    });
-    __syncthreads();
+struct RecLayout {
+  int o_ptr, o_col, o_val, o_inv, bytes;
+  __host__ __device__ RecLayout(int n, int nnz) {
+    o_ptr = 16;
+    o_col = o_ptr + ((2 * (n + 1) + 15) & ~15);
+    o_val = o_col + ((2 * nnz + 15) & ~15);
+    o_inv = o_val + (((int)sizeof(T) * nnz + 15) & ~15);
+    bytes = o_inv + (((int)sizeof(T) * (n * (n + 1) / 2) + 15) & ~15);
   }
+};
+
+// Issue the bulk copy of record k of a set into ring slot s (thread 0 only).
+__device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int s) {
+  const long long a = R.off[k], b = R.off[k + 1];
+  bulk_load(pp.ring + (size_t)s * pp.slot, R.recs + a, (uint32_t)(b - a), &pp.bar[s]);
 }
 
-// v <- U^{-1} v, grid rows in reverse order, packed upper block inverses.
-template <typename T>
-__device__ void block_upper_solve(int n, const int* ptr, const int* col, const T* val, const T* inv,
-                                  T* v, T* row) {
-  const size_t blk = upper_off(n, n);
-  for (int by = n - 1; by >= 0; --by) {
-    for_group_rows(n, [&](int r, bool act, int gl) {
-      T s = 0;
-      if (act) {
-        const int i = by * n + r;
-        for (int k = ptr[i] + gl; k < ptr[i + 1]; k += kGroup) s += val[k] * v[col[k]];
+// Block-row triangular sweep v <- D^{-1}-weighted substitution over the n
+// grid rows of a record set (L: grid rows 0..n-1; U: n-1..0).  Per grid row:
+// phase 1 forms t_r = v_i - sum_k val_k v_{base+col_k} over the off-block
+// entries in parallel (kGroup lanes per row); phase 2 writes
+// v_row = inv(D_row) t (packed dense, lower for L, upper for U).  Record k+S
+// is in flight while record k is used.  Returns false after a wait timeout.
+template <typename T, bool UPPER>
+__device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int* status) {
+  if (pp.dead) return false;
+  const int S = pp.nstage < n ? pp.nstage : n;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
+  for (int k = 0; k < n; ++k) {
+    const int s = k % pp.nstage;
+    const bool got = mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u);
+    pp.phase ^= 1u << s;
+    if (__syncthreads_or(!got)) {
+      if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
+      // drain the copies still in flight (bounded) before giving up
+      for (int j = k + 1; j < k + S && j < n; ++j) {
+        const int sj = j % pp.nstage;
+        mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
+        pp.phase ^= 1u << sj;
       }
-      s = group_sum(s);
-      if (act && gl == 0) row[r] = v[by * n + r] - s;
-    });
-    __syncthreads();
-    const T* D = inv + (size_t)by * blk;
-    for_group_rows(n, [&](int r, bool act, int gl) {
-      T s = 0;
-      if (act) {
-        const T* Dr = D + upper_off(r, n);
-        for (int j = r + gl; j < n; j += kGroup) s += Dr[j - r] * row[j];
-      }
-      s = group_sum(s);
-      if (act && gl == 0) v[by * n + r] = s;
-    });
-    __syncthreads();
-  }
-}
-
-// One forward lexicographic Gauss--Seidel sweep on a 9-point operator:
-// per grid row, t = b - (E, S-row, N-row couplings) x, then x_row = (D+W)^{-1} t.
-template <typename T>
-__device__ void gs_sweep(int n, const T* A, const T* ginv, const T* b, T* x, T* row) {
-  const size_t blk = lower_off(n);
-  for (int by = 0; by < n; ++by) {
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      const int i = by * n + r;
-      const T* a = A + (size_t)i * 9;
-      T t = b[i];
-      if (r + 1 < n) t -= a[5] * x[i + 1];
-      if (by > 0) {
-        if (r > 0) t -= a[0] * x[i - n - 1];
-        t -= a[1] * x[i - n];
-        if (r + 1 < n) t -= a[2] * x[i - n + 1];
-      }
-      if (by + 1 < n) {
-        if (r > 0) t -= a[6] * x[i + n - 1];
-        t -= a[7] * x[i + n];
-        if (r + 1 < n) t -= a[8] * x[i + n + 1];
-      }
-      row[r] = t;
+      pp.dead = true;
+      return false;
     }
-    __syncthreads();
-    const T* D = ginv + (size_t)by * blk;
+    const char* rec = pp.ring + (size_t)s * pp.slot;
+    const int* hdr = (const int*)rec;
+    const int base = hdr[0], nnz = hdr[1], by = hdr[2];
+    const RecLayout<T> lay(n, nnz);
+    const uint16_t* ptr = (const uint16_t*)(rec + lay.o_ptr);
+    const uint16_t* col = (const uint16_t*)(rec + lay.o_col);
+    const T* val = (const T*)(rec + lay.o_val);
+    const T* inv = (const T*)(rec + lay.o_inv);
     for_group_rows(n, [&](int r, bool act, int gl) {
-      T s = 0;
-      if (act) {
-        const T* Dr = D + lower_off(r);
-        for (int j = gl; j <= r; j += kGroup) s += Dr[j] * row[j];
-      }
-      s = group_sum(s);
-      if (act && gl == 0) x[by * n + r] = s;
+      T sacc = 0;
+      if (act)
+        for (int e = ptr[r] + gl; e < ptr[r + 1]; e += kGroup) sacc += val[e] * v[base + col[e]];
+      sacc = group_sum(sacc);
+      if (act && gl == 0) row[r] = v[by * n + r] - sacc;
     });
     __syncthreads();
+    for_group_rows(n, [&](int r, bool act, int gl) {
+      T sacc = 0;
+      if (act) {
+        if (!UPPER) {
+          const T* Dr = inv + lower_off(r);
+          for (int j = gl; j <= r; j += kGroup) sacc += Dr[j] * row[j];
+        } else {
+          const T* Dr = inv + upper_off(r, n);
+          for (int j = r + gl; j < n; j += kGroup) sacc += Dr[j - r] * row[j];
+        }
+      }
+      sacc = group_sum(sacc);
+      if (act && gl == 0) v[by * n + r] = sacc;
+    });
+    __syncthreads();
+    if (threadIdx.x == 0 && k + pp.nstage < n) {
+      fence_proxy_async();
+      pipe_issue(pp, R, k + pp.nstage, s);
+    }
   }
+  return true;
+}
+
+// One forward lexicographic Gauss--Seidel sweep on a 9-point operator, run by
+// warp 0 (the caller synchronises the CTA afterwards).  Grid row by: every
+// lane forms t_r = b_r - (E, S-row, N-row couplings) x for its E consecutive
+// unknowns; the in-row recurrence x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha =
+// -a_W/a_C) is an affine map per unknown, composed by a warp-wide scan.  The
+// next row's coefficients are loaded into registers while the current row is
+// solved.
+template <typename T, int EMAX>
+__device__ void gs_sweep_warp(int n, const T* __restrict__ cf, const T* b, T* x) {
+  if (threadIdx.x >= 32) return;
+  // FP32: the next row's coefficients are prefetched into registers; FP64
+  // (the reference form) reads them in place to stay within the register budget
+  constexpr bool kPre = sizeof(T) == 4;
+  constexpr int EP = kPre ? EMAX : 1;
+  const int lane = threadIdx.x;
+  const int E = (n + 31) / 32;
+  const int r0 = lane * E;
+  T c[EP][G_NCOEF], cn[EP][G_NCOEF];
+  if (kPre) {
+#pragma unroll
+    for (int e = 0; e < EP; ++e)
+#pragma unroll
+      for (int q = 0; q < G_NCOEF; ++q)
+        c[e][q] = (e < E && r0 + e < n) ? cf[(size_t)(r0 + e) * G_NCOEF + q] : (T)0;
+  }
+  for (int by = 0; by < n; ++by) {
+    if (kPre && by + 1 < n) {
+#pragma unroll
+      for (int e = 0; e < EP; ++e)
+#pragma unroll
+        for (int q = 0; q < G_NCOEF; ++q)
+          cn[e][q] = (e < E && r0 + e < n) ? cf[(size_t)((by + 1) * n + r0 + e) * G_NCOEF + q] : (T)0;
+    }
+    T beta[EMAX];
+    T A = 1, B = 0;
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      beta[e] = 0;
+      const int r = r0 + e;
+      if (e < E && r < n) {
+        const int i = by * n + r;
+        const T* ce = kPre ? c[kPre ? e : 0] : cf + (size_t)i * G_NCOEF;
+        T t = b[i];
+        if (r + 1 < n) t -= ce[G_E] * x[i + 1];
+        if (by > 0) {
+          if (r > 0) t -= ce[G_SW] * x[i - n - 1];
+          t -= ce[G_S] * x[i - n];
+          if (r + 1 < n) t -= ce[G_SE] * x[i - n + 1];
+        }
+        if (by + 1 < n) {
+          if (r > 0) t -= ce[G_NW] * x[i + n - 1];
+          t -= ce[G_N] * x[i + n];
+          if (r + 1 < n) t -= ce[G_NE] * x[i + n + 1];
+        }
+        beta[e] = ce[G_INVC] * t;
+        B = ce[G_ALPHA] * B + beta[e];
+        A = ce[G_ALPHA] * A;
+      }
+    }
+    // inclusive scan of the lanes' affine maps x_out = A x_in + B
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const T Ap = __shfl_up_sync(0xffffffffu, A, o);
+      const T Bp = __shfl_up_sync(0xffffffffu, B, o);
+      if (lane >= o) {
+        B = A * Bp + B;
+        A = A * Ap;
+      }
+    }
+    T xin = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) xin = 0;
+    __syncwarp();
+#pragma unroll
+    for (int e = 0; e < EMAX; ++e) {
+      const int r = r0 + e;
+      if (e < E && r < n) {
+        const T alpha = kPre ? c[kPre ? e : 0][G_ALPHA] : cf[(size_t)(by * n + r) * G_NCOEF + G_ALPHA];
+        xin = alpha * xin + beta[e];
+        x[by * n + r] = xin;
+      }
+    }
+    __syncwarp();
+    if (kPre) {
+#pragma unroll
+      for (int e = 0; e < EP; ++e)
+#pragma unroll
+        for (int q = 0; q < G_NCOEF; ++q) c[e][q] = cn[e][q];
+    }
+  }
+}
+
+template <typename T>
+__device__ void gs_sweep(int n, const T* cf, const T* b, T* x) {
+  if (n <= 32) gs_sweep_warp<T, 1>(n, cf, b, x);
+  else if (n <= 64) gs_sweep_warp<T, 2>(n, cf, b, x);
+  else gs_sweep_warp<T, 4>(n, cf, b, x);
+  __syncthreads();
+}
+
+// Tensor-product transfer on the affine map, stage along xi then eta:
+// out[jy][jx] (op)= (sum_ky band[jy][ky] sum_kx band[jx][kx] in[s(jy)+ky][s(jx)+kx]) / scale
+// with in an nin x nin grid, out nout x nout, tmp nin x nout.
+template <typename T, bool ADD>
+__device__ void transfer_tp(int nin, int nout, int w, const int* start, const T* band,
+                            const T* scale, const T* in, T* tmp, T* out) {
+  for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) {
+    const int jx = i % nout, iy = i / nout;
+    const T* bd = band + (size_t)jx * w;
+    const T* src = in + (size_t)iy * nin + start[jx];
+    T s = 0;
+    for (int k = 0; k < w; ++k) s += bd[k] * src[k];
+    tmp[i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nout * nout; i += blockDim.x) {
+    const int jx = i % nout, jy = i / nout;
+    const T* bd = band + (size_t)jy * w;
+    const int s0 = start[jy];
+    T s = 0;
+    for (int k = 0; k < w; ++k) s += bd[k] * tmp[(size_t)(s0 + k) * nout + jx];
+    const T v = s / scale[i];
+    if (ADD) out[i] += v; else out[i] = v;
+  }
+  __syncthreads();
 }
 
 // t = b - A x on a 9-point operator.

@@ -1,0 +1,61 @@
+// Kernel launch interface between the host code (capi.cu) and the kernel
+// translation units (kernels_f32.cu: mixed form, kernels_f64.cu: FP64 form).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace igm {
+
+// MGRIT sweep modes (Sec. 3): F-relaxation, C-relaxation, F-relaxation plus
+// C-point residual and injection, coarse correction plus F-relaxation (ideal
+// interpolation), sequential stepping on the coarsest level, and the C-point
+// residual alone.
+enum : int { MODE_F = 0, MODE_C = 1, MODE_FR = 2, MODE_CF = 3, MODE_SEQ = 4, MODE_R = 5 };
+
+struct SweepArgs {
+  PmgD P;
+  int mode, m, Nl, nint;
+  double* W;              // [Nl+1][N]: the part of u each step's solve produces
+  const double* g;        // [Nl+1][N] right-hand side g^(l) (nullptr on the fine level)
+  const double* Wc;       // next level's W and g (correction)
+  const double* gc;
+  double* gnext;          // next level's g, written by the residual
+  double* norms;          // [nint] ||r_j||^2 (fine level) or nullptr
+  const double* fhat;     // fine level source profile or nullptr
+  const double* fcoef;    // device [Nt+1] time factors
+  double dt0;
+  double* scratch;        // per CTA: 2 N doubles (rhs, residual iterate)
+  char* garena;
+  int ncycles;
+  unsigned long long* counters;  // [0] solves, [1] cycles
+  int* status;
+};
+
+// prec: 0 = FP64 form, 1 = mixed form.  Each returns cudaGetLastError().
+cudaError_t launch_pmg_solve(int prec, const PmgD& P, int grid, long smem, cudaStream_t st,
+                             const double* b, double* x, long ld, int ncycles, int* cycles_out,
+                             int* status, char* garena);
+cudaError_t launch_ilut_apply(int prec, const PmgD& P, int grid, long smem, cudaStream_t st,
+                              const double* r, double* z, long ld, char* garena, int* status);
+cudaError_t launch_mgrit_sweep(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st);
+cudaError_t launch_apply_op(const PmgD& P, int which, int nrhs, const double* x, double* y, long ld,
+                            double* scratch, cudaStream_t st);
+// Allow up to `bytes` of dynamic shared memory for the solve kernels.
+cudaError_t set_solver_smem(long bytes);
+
+// per-precision entry points (kernels_f32.cu / kernels_f64.cu)
+cudaError_t launch_pmg_solve_f32(const PmgD&, int, long, cudaStream_t, const double*, double*, long,
+                                 int, int*, int*, char*);
+cudaError_t launch_pmg_solve_f64(const PmgD&, int, long, cudaStream_t, const double*, double*, long,
+                                 int, int*, int*, char*);
+cudaError_t launch_ilut_apply_f32(const PmgD&, int, long, cudaStream_t, const double*, double*, long,
+                                  char*, int*);
+cudaError_t launch_ilut_apply_f64(const PmgD&, int, long, cudaStream_t, const double*, double*, long,
+                                  char*, int*);
+cudaError_t launch_mgrit_sweep_f32(const SweepArgs&, int, long, cudaStream_t);
+cudaError_t launch_mgrit_sweep_f64(const SweepArgs&, int, long, cudaStream_t);
+cudaError_t set_smem_f32(long bytes);
+cudaError_t set_smem_f64(long bytes);
+
+}  // namespace igm

@@ -1,0 +1,130 @@
+// Kernel templates of the solver, instantiated per precision in
+// kernels_f32.cu (mixed form) and kernels_f64.cu (FP64 form).
+#pragma once
+#include <type_traits>
+
+#include "kernels.h"
+#include "solver.cuh"
+
+namespace igm {
+
+// Dynamic shared memory: [record ring][mbarriers] then the CTA's arena when it
+// fits; otherwise the arena is this CTA's slice of the global scratch.
+__device__ __forceinline__ char* cta_setup(const PmgD& P, char* garena, Pipe& pp) {
+  extern __shared__ __align__(128) char dyn_smem[];
+  pp.ring = dyn_smem;
+  pp.bar = (uint64_t*)(dyn_smem + (size_t)P.nstage * P.slot_bytes);
+  pp.nstage = P.nstage;
+  pp.slot = P.slot_bytes;
+  pipe_init(pp);
+  return P.arena_smem ? dyn_smem + P.ring_bytes : garena + (size_t)blockIdx.x * P.arena_bytes;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_pmg_solve(PmgD P, const double* b, double* x, long ld,
+                                                      int ncycles, int* cycles_out, int* status,
+                                                      char* garena) {
+  __shared__ double red[32];
+  Pipe pp;
+  char* arena = cta_setup(P, garena, pp);
+  const double* bc = b + (size_t)blockIdx.x * ld;
+  double* xc = x + (size_t)blockIdx.x * ld;
+  const int c = pmg_solve<PREC>(P, pp, bc, xc, arena, red, ncycles, status);
+  if (threadIdx.x == 0 && cycles_out) cycles_out[blockIdx.x] = c;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_ilut_apply(PmgD P, const double* r, double* z, long ld,
+                                                       char* garena, int* status) {
+  using T = typename std::conditional<PREC == 0, double, float>::type;
+  Pipe pp;
+  char* arena = cta_setup(P, garena, pp);
+  const double* rc = r + (size_t)blockIdx.x * ld;
+  double* zc = z + (size_t)blockIdx.x * ld;
+  T* A = (T*)arena;
+  T* t = A + P.o_t;
+  for (int i = threadIdx.x; i < P.N; i += blockDim.x) t[i] = (T)rc[i];
+  __syncthreads();
+  ilut_apply<T>(P, pp, t, A + P.o_row, status);
+  for (int i = threadIdx.x; i < P.N; i += blockDim.x) zc[i] = (double)t[i];
+}
+
+// One backward-Euler step into point n of the level (Sec. 3: the step
+// u_n = Phi_l(u_{n-1}) + g_n with Phi_l = (M + kappa dt_l K)^{-1} M), or the
+// C-point residual r = Phi_l(u_{n-1}) + g_n - u_n injected into g^(l+1)_{j+1}.
+template <int PREC>
+__device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* arena, double* red,
+                                           int n, bool residual, int j) {
+  const PmgD& P = a.P;
+  const int N = P.N;
+  double* rhs = a.scratch + (size_t)blockIdx.x * 2 * N;
+  double* xr = rhs + N;
+  double* tm = (PREC == 0) ? (double*)arena + P.o_u : (double*)((float*)arena + P.o_d);
+  const double* u = a.W + (size_t)(n - 1) * N;
+  const double* ug = a.g ? a.g + (size_t)(n - 1) * N : nullptr;
+  const double scale = a.fhat ? a.dt0 * a.fcoef[n] : 0.0;
+  build_rhs(P, u, ug, scale, a.fhat, rhs, tm);
+  double* Wn = a.W + (size_t)n * N;
+  double* x = Wn;
+  if (residual) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) xr[i] = Wn[i];
+    __syncthreads();
+    x = xr;
+  }
+  const int cyc = pmg_solve<PREC>(P, pp, rhs, x, arena, red, a.ncycles, a.status);
+  if (threadIdx.x == 0 && a.counters) {
+    atomicAdd(&a.counters[0], 1ull);
+    atomicAdd(&a.counters[1], (unsigned long long)cyc);
+  }
+  if (residual) {
+    double* gout = a.gnext + (size_t)(j + 1) * N;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+      const double r = xr[i] - Wn[i];
+      gout[i] = r;
+      s += r * r;
+    }
+    s = block_sum(s, red);
+    if (a.norms && threadIdx.x == 0) a.norms[j] = s;
+  }
+}
+
+// One CTA per interval j of the level (or one CTA for the sequential coarsest
+// level).  Every mode is a run of consecutive steps n0..n1 of one interval,
+// the last of which may be the C-point residual.
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
+  __shared__ double red[32];
+  Pipe pp;
+  char* arena = cta_setup(a.P, a.garena, pp);
+  const int j = blockIdx.x, m = a.m, N = a.P.N;
+  int n0 = j * m + 1, n1 = j * m + m - 1;
+  bool resid = false;
+  switch (a.mode) {
+    case MODE_C: n0 = n1 = (j + 1) * m; break;
+    case MODE_R: n0 = n1 = (j + 1) * m; resid = true; break;
+    case MODE_FR: n1 = (j + 1) * m; resid = true; break;
+    case MODE_SEQ: n0 = 1; n1 = a.Nl; break;
+    case MODE_CF:
+      // u_{jm} += u^(l+1)_j at the C-point this CTA starts from; the last CTA
+      // also corrects the final C-point (read by no F-relaxation)
+      if (j >= 1) {
+        double* w = a.W + (size_t)(j * m) * N;
+        const double* wc = a.Wc + (size_t)j * N;
+        const double* gc = a.gc + (size_t)j * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
+      }
+      if (j == a.nint - 1) {
+        double* w = a.W + (size_t)a.Nl * N;
+        const double* wc = a.Wc + (size_t)a.nint * N;
+        const double* gc = a.gc + (size_t)a.nint * N;
+        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
+      }
+      __syncthreads();
+      break;
+    default: break;  // MODE_F
+  }
+  for (int n = n0; n <= n1; ++n) mgrit_step<PREC>(a, pp, arena, red, n, resid && n == n1, j);
+}
+
+}  // namespace igm

@@ -5,8 +5,6 @@
 
 namespace igm {
 
-enum : int { ST_OK = 0, ST_NOT_CONVERGED = -4, ST_NUMERIC = -6 };
-
 __device__ __forceinline__ void record_status(int* status, int code) {
   if (status && threadIdx.x == 0) atomicMin(status, code);
 }
@@ -44,36 +42,32 @@ __device__ void residualT<double>(const PmgD& P, const double* b, const double* 
 
 template <typename T> struct Prec;
 template <> struct Prec<float> {
-  __device__ static const int* Lp(const PmgD& P) { return P.Lptr; }
-  __device__ static const float* Lv(const PmgD& P) { return P.Lval32; }
-  __device__ static const float* Li(const PmgD& P) { return P.Linv32; }
-  __device__ static const float* Uv(const PmgD& P) { return P.Uval32; }
-  __device__ static const float* Ui(const PmgD& P) { return P.Uinv32; }
   __device__ static const float* Pv(const PmgD& P) { return P.Pval32; }
   __device__ static const float* PTv(const PmgD& P) { return P.PTval32; }
+  __device__ static const float* Pb(const PmgD& P) { return P.Pb32; }
+  __device__ static const float* PTb(const PmgD& P) { return P.PTb32; }
   __device__ static const float* MpL(const PmgD& P) { return P.MpL32; }
   __device__ static const float* M1L(const PmgD& P) { return P.M1L32; }
   __device__ static const float* HA(const HLevelD& H) { return H.A32; }
   __device__ static const float* HG(const HLevelD& H) { return H.G32; }
 };
 template <> struct Prec<double> {
-  __device__ static const double* Lv(const PmgD& P) { return P.Lval64; }
-  __device__ static const double* Li(const PmgD& P) { return P.Linv64; }
-  __device__ static const double* Uv(const PmgD& P) { return P.Uval64; }
-  __device__ static const double* Ui(const PmgD& P) { return P.Uinv64; }
   __device__ static const double* Pv(const PmgD& P) { return P.Pval64; }
   __device__ static const double* PTv(const PmgD& P) { return P.PTval64; }
+  __device__ static const double* Pb(const PmgD& P) { return P.Pb64; }
+  __device__ static const double* PTb(const PmgD& P) { return P.PTb64; }
   __device__ static const double* MpL(const PmgD& P) { return P.MpL64; }
   __device__ static const double* M1L(const PmgD& P) { return P.M1L64; }
   __device__ static const double* HA(const HLevelD& H) { return H.A64; }
   __device__ static const double* HG(const HLevelD& H) { return H.G64; }
 };
 
-// v <- U^{-1} L^{-1} v (the ILUT smoother S = (LU)^{-1} applied to v).
+// v <- U^{-1} L^{-1} v (the ILUT smoother S = (LU)^{-1} applied to v, Sec. 4).
+// The factor records are in the handle's smoothing precision T.
 template <typename T>
-__device__ void ilut_apply(const PmgD& P, T* v, T* row) {
-  block_lower_solve<T>(P.n, P.Lptr, P.Lcol, Prec<T>::Lv(P), Prec<T>::Li(P), v, row);
-  block_upper_solve<T>(P.n, P.Uptr, P.Ucol, Prec<T>::Uv(P), Prec<T>::Ui(P), v, row);
+__device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, T* row, int* status) {
+  if (!block_sweep<T, false>(P.n, P.Lrec, pp, v, row, status)) return false;
+  return block_sweep<T, true>(P.n, P.Urec, pp, v, row, status);
 }
 
 // x_k = A_k^{-1} b_k on the coarsest h-level with the FP64 inverse.
@@ -102,7 +96,7 @@ __device__ void wcycle(const PmgD& P, T* A, T* row) {
     T* tk = A + H.ot;
     switch (op) {
       case W_GS:
-        gs_sweep<T>(H.n, Prec<T>::HA(H), Prec<T>::HG(H), bk, xk, row);
+        gs_sweep<T>(H.n, Prec<T>::HG(H), bk, xk);
         break;
       case W_RESTRICT:
         residual9<T>(H.n, Prec<T>::HA(H), bk, xk, tk);
@@ -118,11 +112,37 @@ __device__ void wcycle(const PmgD& P, T* A, T* row) {
   }
 }
 
+// r_1 = (M_1^L)^{-1} P^T t into h-level 0's b, and x_0 = 0 (Sec. 4, step 2).
+template <typename T>
+__device__ void restrict_p1(const PmgD& P, const T* t, T* A) {
+  const HLevelD& H0 = P.h[0];
+  if (P.tp)
+    transfer_tp<T, false>(P.n, P.n1, P.wP, P.PTis, Prec<T>::PTb(P), Prec<T>::M1L(P), t, A + P.o_tr,
+                          A + H0.ob);
+  else
+    csr_scaled<T, false>(P.N1, P.PTptr, P.PTcol, Prec<T>::PTv(P), Prec<T>::M1L(P), t, A + H0.ob);
+  for (int i = threadIdx.x; i < P.N1; i += blockDim.x) A[H0.ox + i] = 0;
+  __syncthreads();
+}
+
+// x += (M_p^L)^{-1} P e_1 with e_1 = h-level 0's x (Sec. 4, step 4).
+template <typename T>
+__device__ void prolong_p1(const PmgD& P, T* x, T* A) {
+  const HLevelD& H0 = P.h[0];
+  if (P.tp)
+    transfer_tp<T, true>(P.n1, P.n, P.wP, P.Pjs, Prec<T>::Pb(P), Prec<T>::MpL(P), A + H0.ox,
+                         A + P.o_tr, x);
+  else
+    csr_scaled<T, true>(P.N, P.Pptr, P.Pcol, Prec<T>::Pv(P), Prec<T>::MpL(P), A + H0.ox, x);
+}
+
 // One p-multigrid cycle (Sec. 4, steps 1-5) on A x = b in precision T.
 // t: scratch of N; on entry t may already hold b - A x (t_is_residual).
 // x_is_zero: x = 0 on entry (the first pre-smoothing then needs no product).
+// Returns false if a record wait timed out (the solve is abandoned).
 template <typename T>
-__device__ void pmg_cycle(const PmgD& P, const T* b, T* x, T* A, bool t_is_residual, bool x_is_zero) {
+__device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool t_is_residual,
+                          bool x_is_zero, int* status) {
   const int N = P.N;
   T* t = A + P.o_t;
   T* tm = A + P.o_u;
@@ -136,7 +156,7 @@ __device__ void pmg_cycle(const PmgD& P, const T* b, T* x, T* A, bool t_is_resid
     } else if (!(s == 0 && t_is_residual)) {
       residualT<T>(P, b, x, t, tm, tk);
     }
-    ilut_apply<T>(P, t, row);
+    if (!ilut_apply<T>(P, pp, t, row, status)) return false;
     for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = zero ? t[i] : x[i] + t[i];
     __syncthreads();
   }
@@ -146,21 +166,19 @@ __device__ void pmg_cycle(const PmgD& P, const T* b, T* x, T* A, bool t_is_resid
   }
   // step 2: r_1 = (M_1^L)^{-1} P^T (b - A x)
   residualT<T>(P, b, x, t, tm, tk);
-  const HLevelD& H0 = P.h[0];
-  csr_scaled<T, false>(P.N1, P.PTptr, P.PTcol, Prec<T>::PTv(P), Prec<T>::M1L(P), t, A + H0.ob);
-  for (int i = threadIdx.x; i < P.N1; i += blockDim.x) A[H0.ox + i] = 0;
-  __syncthreads();
+  restrict_p1<T>(P, t, A);
   // step 3: one W-cycle of h-multigrid on A_1 e_1 = r_1
   wcycle<T>(P, A, row);
   // step 4: x += (M_p^L)^{-1} P e_1
-  csr_scaled<T, true>(N, P.Pptr, P.Pcol, Prec<T>::Pv(P), Prec<T>::MpL(P), A + H0.ox, x);
+  prolong_p1<T>(P, x, A);
   // step 5: post-smoothing
   for (int s = 0; s < P.nu2; ++s) {
     residualT<T>(P, b, x, t, tm, tk);
-    ilut_apply<T>(P, t, row);
+    if (!ilut_apply<T>(P, pp, t, row, status)) return false;
     for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += t[i];
     __syncthreads();
   }
+  return true;
 }
 
 __device__ __forceinline__ double block_dot(const double* a, int N, double* red) {
@@ -172,11 +190,13 @@ __device__ __forceinline__ double block_dot(const double* a, int N, double* red)
 // Spatial solve of A x = b (b, x FP64 in global memory), warm start x.
 // ncycles > 0: exactly ncycles cycles; else cycle until
 // ||b - A x|| <= tol ||b|| (checked before each cycle) or max_cycles.
-// FP64 form: one cycle = one p-multigrid cycle in FP64.  Mixed form: one
-// cycle = FP64 residual r, then `inner` FP32 cycles on A d = r from d = 0,
-// then x += d (iterative refinement).  Returns the number of cycles.
-__device__ int pmg_solve(const PmgD& P, const double* b, double* x, char* arena, double* red,
-                         int ncycles, int* status) {
+// PREC 0 (FP64 form): one cycle = one p-multigrid cycle in FP64.
+// PREC 1 (mixed form): one cycle = FP64 residual r, then `inner` FP32
+// p-multigrid cycles on A d = r from d = 0, then x += d (iterative
+// refinement).  Returns the number of cycles.
+template <int PREC>
+__device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, char* arena,
+                         double* red, int ncycles, int* status) {
   const int N = P.N;
   const double nb2 = block_dot(b, N, red);
   if (nb2 == 0.0) {
@@ -186,7 +206,7 @@ __device__ int pmg_solve(const PmgD& P, const double* b, double* x, char* arena,
   }
   const double tol2 = P.tol * P.tol * nb2;
   int cyc = 0;
-  if (P.precision == 0) {
+  if (PREC == 0) {
     double* A = (double*)arena;
     double* t = A + P.o_t;
     double* tm = A + P.o_u;
@@ -200,7 +220,7 @@ __device__ int pmg_solve(const PmgD& P, const double* b, double* x, char* arena,
         if (rr <= tol2) break;
         if (cyc >= P.max_cycles) { record_status(status, ST_NOT_CONVERGED); break; }
       }
-      pmg_cycle<double>(P, b, x, A, true, false);
+      if (!pmg_cycle<double>(P, pp, b, x, A, true, false, status)) break;
       ++cyc;
     }
   } else {
@@ -217,7 +237,10 @@ __device__ int pmg_solve(const PmgD& P, const double* b, double* x, char* arena,
         if (rr <= tol2) break;
         if (cyc >= P.max_cycles) { record_status(status, ST_NOT_CONVERGED); break; }
       }
-      for (int k = 0; k < P.inner; ++k) pmg_cycle<float>(P, r, d, A, false, k == 0);
+      bool ok = true;
+      for (int k = 0; k < P.inner && ok; ++k)
+        ok = pmg_cycle<float>(P, pp, r, d, A, false, k == 0, status);
+      if (!ok) break;
       for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += (double)d[i];
       __syncthreads();
       ++cyc;
