@@ -25,7 +25,7 @@ template <typename T>
 __device__ void residualT(const PmgD& P, const T* b, const T* x, T* t, T* tm, T* tk);
 
 template <>
-__device__ void residualT<float>(const PmgD& P, const float* b, const float* x, float* t, float* tm,
+__device__ inline void residualT<float>(const PmgD& P, const float* b, const float* x, float* t, float* tm,
                                  float* tk) {
   if (P.affine)
     apply_A_affine<float>(P.n, P.p, P.bM32, P.bK32, P.bA32, P.bcM32, x, (const float*)nullptr, b, t,
@@ -35,7 +35,7 @@ __device__ void residualT<float>(const PmgD& P, const float* b, const float* x, 
 }
 
 template <>
-__device__ void residualT<double>(const PmgD& P, const double* b, const double* x, double* t,
+__device__ inline void residualT<double>(const PmgD& P, const double* b, const double* x, double* t,
                                   double* tm, double* tk) {
   residual64<double>(P, b, x, t, tm, tk, (double*)nullptr);
 }
@@ -251,7 +251,7 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
 
 // out = M (u + ug) + scale * fhat in FP64 (the right-hand side of one
 // backward-Euler step, Sec. 3: M u^{n-1} + dt f^n).  tm: N doubles scratch.
-__device__ void build_rhs(const PmgD& P, const double* u, const double* ug, double scale,
+__device__ inline void build_rhs(const PmgD& P, const double* u, const double* ug, double scale,
                           const double* fhat, double* out, double* tm) {
   if (P.affine)
     apply_A_affine<double>(P.n, P.p, P.bM64, (const double*)nullptr, P.bM64,
