@@ -109,6 +109,7 @@ typedef struct {
   int inner_cycles;       /* precision 1: FP32 V-cycles per FP64 refinement step (default 1) */
   double tol;             /* spatial stop: ||b - A x||_2 <= tol ||b||_2 (default 1e-10) */
   int max_cycles;         /* cycle limit of one spatial solve (default 50) */
+  int trace;              /* 1: accumulate SM clock cycles per solver phase (pmg_trace) */
 } pmg_opts;
 
 typedef struct pmg_handle pmg_handle;
@@ -137,6 +138,24 @@ igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long 
  * z = (L U)^{-1} r on nrhs DEVICE columns, in the handle's precision. */
 igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, double* z, long ld,
                           igm_stream s);
+
+/* Solver phases timed when opts.trace = 1 (SM clock cycles of CTA thread 0,
+ * summed over all CTAs and calls since setup or the last reset). */
+typedef enum {
+  IGM_PH_RESIDUAL64 = 0,  /* FP64 residual b - A x and its norm */
+  IGM_PH_RESIDUAL = 1,    /* residuals in the smoothing precision */
+  IGM_PH_ILUT = 2,        /* ILUT sweeps L then U (Sec. 4, smoother) */
+  IGM_PH_RESTRICT = 3,    /* restriction p -> 1 (Sec. 4, step 2) */
+  IGM_PH_WCYCLE = 4,      /* h-multigrid W-cycle at p = 1 (Sec. 4, step 3) */
+  IGM_PH_PROLONG = 5,     /* prolongation 1 -> p (Sec. 4, step 4) */
+  IGM_PH_RHS = 6,         /* MGRIT step right-hand side M u + dt f */
+  IGM_PH_GS = 7,          /* Gauss--Seidel sweeps inside the W-cycle */
+  IGM_PH_COUNT = 8
+} igm_phase;
+
+/* Copy the accumulated phase clocks (HOST out[IGM_PH_COUNT]); reset = 1
+ * zeroes them afterwards.  The handle must have been set up with trace = 1. */
+igm_status pmg_trace(pmg_handle* h, long long* out, int reset);
 
 /* Host copies of the ILUT factors in CSR (L strictly lower, U upper with the
  * diagonal), for pattern comparisons.  Pass NULL arrays to query sizes

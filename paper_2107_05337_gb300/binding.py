@@ -30,7 +30,8 @@ class IgaDesc(ctypes.Structure):
 class PmgOpts(ctypes.Structure):
     _fields_ = [("nu1", c_int), ("nu2", c_int), ("ilut_droptol", c_double),
                 ("ilut_fill", c_double), ("hmg_coarsest_nel", c_int), ("precision", c_int),
-                ("inner_cycles", c_int), ("tol", c_double), ("max_cycles", c_int)]
+                ("inner_cycles", c_int), ("tol", c_double), ("max_cycles", c_int),
+                ("trace", c_int)]
 
 
 class MgritOpts(ctypes.Structure):
@@ -60,6 +61,7 @@ EXPORTS = {
     "pmg_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int, POINTER(c_int),
                            c_void_p]),
     "pmg_ilut_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_void_p]),
+    "pmg_trace": (c_int, [c_void_p, POINTER(ctypes.c_longlong), c_int]),
     "pmg_ilut_factors": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                  POINTER(c_int), POINTER(c_double), POINTER(c_int),
                                  POINTER(c_int), POINTER(c_double)]),
@@ -237,6 +239,14 @@ class PMG:
         Z = torch.empty_like(R)
         _check(lib().pmg_ilut_apply(self.h, R.shape[0], _dptr(R), _dptr(Z), self.N, _stream()))
         return Z
+
+    PHASES = ("residual64", "residual", "ilut", "restrict", "wcycle", "prolong", "rhs", "gs")
+
+    def trace(self, reset=True):
+        """Accumulated SM clocks per solver phase (handle set up with trace=1)."""
+        out = (ctypes.c_longlong * len(self.PHASES))()
+        _check(lib().pmg_trace(self.h, out, 1 if reset else 0))
+        return dict(zip(self.PHASES, list(out)))
 
     def factors(self):
         """(L, U) as scipy CSR matrices (host copies of the ILUT factors)."""

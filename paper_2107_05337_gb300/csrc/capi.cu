@@ -307,6 +307,7 @@ extern "C" void pmg_default_opts(pmg_opts* o) {
   o->inner_cycles = 1;
   o->tol = 1e-10;
   o->max_cycles = 50;
+  o->trace = 0;
 }
 
 static void gen_wcycle(int k, int last, std::vector<int>& ops) {
@@ -543,6 +544,7 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     return fail(IGM_ERR_ARG, "h-multigrid hierarchy too deep for the W-cycle program");
   d.nops = (int)wops.size();
   for (int i = 0; i < d.nops; ++i) d.ops[i] = wops[i];
+  if (o.trace) d.trace = (unsigned long long*)up.raw(sizeof(unsigned long long) * IGM_PH_COUNT);
   d.precision = o.precision;
   d.inner = o.inner_cycles;
   d.nu1 = o.nu1;
@@ -652,6 +654,15 @@ extern "C" igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, d
   CU(launch_ilut_apply(h->d.precision, h->d, nrhs, smem_of(h), (cudaStream_t)s, r, z, ld,
                        h->garena, nullptr));
   g_launches++;
+  return IGM_OK;
+}
+
+extern "C" igm_status pmg_trace(pmg_handle* h, long long* out, int reset) {
+  if (!h || !out) return fail(IGM_ERR_ARG, "null argument");
+  if (!h->d.trace) return fail(IGM_ERR_ARG, "handle was set up without trace");
+  CU(cudaDeviceSynchronize());
+  CU(cudaMemcpy(out, h->d.trace, sizeof(long long) * IGM_PH_COUNT, cudaMemcpyDeviceToHost));
+  if (reset) CU(cudaMemset(h->d.trace, 0, sizeof(long long) * IGM_PH_COUNT));
   return IGM_OK;
 }
 

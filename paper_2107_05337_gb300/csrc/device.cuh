@@ -73,6 +73,7 @@ struct PmgD {
   int nops;
   int ops[160];                // W-cycle program: op | (level << 8)
   // options
+  unsigned long long* trace;   // per-phase SM clocks (IGM_PH_*) or nullptr
   int precision;               // 0 FP64, 1 mixed
   int inner, nu1, nu2, max_cycles;
   double tol;
@@ -142,6 +143,18 @@ __device__ __forceinline__ void pipe_init(Pipe& pp) {
   pp.dead = false;
   __syncthreads();
 }
+
+// Phase timing (thread 0 of each CTA; the phase ends with a CTA barrier).
+struct PhaseClock {
+  unsigned long long* acc;
+  long long t0;
+  __device__ __forceinline__ PhaseClock(unsigned long long* a) : acc(a), t0(0) {
+    if (acc && threadIdx.x == 0) t0 = clock64();
+  }
+  __device__ __forceinline__ void stop(int phase) {
+    if (acc && threadIdx.x == 0) atomicAdd(&acc[phase], (unsigned long long)(clock64() - t0));
+  }
+};
 
 // ---------------------------------------------------------------------------
 // reductions

@@ -63,7 +63,11 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
   const double* u = a.W + (size_t)(n - 1) * N;
   const double* ug = a.g ? a.g + (size_t)(n - 1) * N : nullptr;
   const double scale = a.fhat ? a.dt0 * a.fcoef[n] : 0.0;
-  build_rhs(P, u, ug, scale, a.fhat, rhs, tm);
+  {
+    PhaseClock pc(P.trace);
+    build_rhs(P, u, ug, scale, a.fhat, rhs, tm);
+    pc.stop(6);
+  }
   double* Wn = a.W + (size_t)n * N;
   double* x = Wn;
   if (residual) {

@@ -66,8 +66,11 @@ template <> struct Prec<double> {
 // The factor records are in the handle's smoothing precision T.
 template <typename T>
 __device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, T* row, int* status) {
-  if (!block_sweep<T, false>(P.n, P.Lrec, pp, v, row, status)) return false;
-  return block_sweep<T, true>(P.n, P.Urec, pp, v, row, status);
+  PhaseClock pc(P.trace);
+  bool ok = block_sweep<T, false>(P.n, P.Lrec, pp, v, row, status) &&
+            block_sweep<T, true>(P.n, P.Urec, pp, v, row, status);
+  pc.stop(2);
+  return ok;
 }
 
 // x_k = A_k^{-1} b_k on the coarsest h-level with the FP64 inverse.
@@ -95,9 +98,12 @@ __device__ void wcycle(const PmgD& P, T* A, T* row) {
     T* bk = A + H.ob;
     T* tk = A + H.ot;
     switch (op) {
-      case W_GS:
+      case W_GS: {
+        PhaseClock pc(P.trace);
         gs_sweep<T>(H.n, Prec<T>::HG(H), bk, xk);
+        pc.stop(7);
         break;
+      }
       case W_RESTRICT:
         residual9<T>(H.n, Prec<T>::HA(H), bk, xk, tk);
         restrict_bilinear<T>(H.n, tk, A + P.h[k + 1].ob, A + P.h[k + 1].ox);
@@ -154,7 +160,9 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
       for (int i = threadIdx.x; i < N; i += blockDim.x) t[i] = b[i];
       __syncthreads();
     } else if (!(s == 0 && t_is_residual)) {
+      PhaseClock pc(P.trace);
       residualT<T>(P, b, x, t, tm, tk);
+      pc.stop(1);
     }
     if (!ilut_apply<T>(P, pp, t, row, status)) return false;
     for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = zero ? t[i] : x[i] + t[i];
@@ -165,15 +173,35 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
     __syncthreads();
   }
   // step 2: r_1 = (M_1^L)^{-1} P^T (b - A x)
-  residualT<T>(P, b, x, t, tm, tk);
-  restrict_p1<T>(P, t, A);
+  {
+    PhaseClock pc(P.trace);
+    residualT<T>(P, b, x, t, tm, tk);
+    pc.stop(1);
+  }
+  {
+    PhaseClock pc(P.trace);
+    restrict_p1<T>(P, t, A);
+    pc.stop(3);
+  }
   // step 3: one W-cycle of h-multigrid on A_1 e_1 = r_1
-  wcycle<T>(P, A, row);
+  {
+    PhaseClock pc(P.trace);
+    wcycle<T>(P, A, row);
+    pc.stop(4);
+  }
   // step 4: x += (M_p^L)^{-1} P e_1
-  prolong_p1<T>(P, x, A);
+  {
+    PhaseClock pc(P.trace);
+    prolong_p1<T>(P, x, A);
+    pc.stop(5);
+  }
   // step 5: post-smoothing
   for (int s = 0; s < P.nu2; ++s) {
-    residualT<T>(P, b, x, t, tm, tk);
+    {
+      PhaseClock pc(P.trace);
+      residualT<T>(P, b, x, t, tm, tk);
+      pc.stop(1);
+    }
     if (!ilut_apply<T>(P, pp, t, row, status)) return false;
     for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += t[i];
     __syncthreads();
@@ -212,7 +240,9 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
     double* tm = A + P.o_u;
     double* tk = tm + N;
     while (true) {
+      PhaseClock pc(P.trace);
       const double rr = residual64<double>(P, b, x, t, tm, tk, red);
+      pc.stop(0);
       if (!(rr == rr)) { record_status(status, ST_NUMERIC); break; }
       if (ncycles > 0) {
         if (cyc >= ncycles) break;
@@ -231,7 +261,9 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
     double* tk64 = tm64 + N;
     while (true) {
       if (ncycles > 0 && cyc >= ncycles) break;
+      PhaseClock pc(P.trace);
       const double rr = residual64<float>(P, b, x, r, tm64, tk64, red);
+      pc.stop(0);
       if (!(rr == rr)) { record_status(status, ST_NUMERIC); break; }
       if (ncycles == 0) {
         if (rr <= tol2) break;
