@@ -150,7 +150,10 @@ typedef enum {
   IGM_PH_PROLONG = 5,     /* prolongation 1 -> p (Sec. 4, step 4) */
   IGM_PH_RHS = 6,         /* MGRIT step right-hand side M u + dt f */
   IGM_PH_GS = 7,          /* Gauss--Seidel sweeps inside the W-cycle */
-  IGM_PH_COUNT = 8
+  IGM_PH_ILUT_WAIT = 8,   /* ILUT: waits for streamed factor records */
+  IGM_PH_ILUT_OFF = 9,    /* ILUT: off-block products of a grid row */
+  IGM_PH_ILUT_DIAG = 10,  /* ILUT: dense diagonal-block products */
+  IGM_PH_COUNT = 11
 } igm_phase;
 
 /* Copy the accumulated phase clocks (HOST out[IGM_PH_COUNT]); reset = 1

@@ -240,7 +240,8 @@ class PMG:
         _check(lib().pmg_ilut_apply(self.h, R.shape[0], _dptr(R), _dptr(Z), self.N, _stream()))
         return Z
 
-    PHASES = ("residual64", "residual", "ilut", "restrict", "wcycle", "prolong", "rhs", "gs")
+    PHASES = ("residual64", "residual", "ilut", "restrict", "wcycle", "prolong", "rhs", "gs",
+              "ilut_wait", "ilut_off", "ilut_diag")
 
     def trace(self, reset=True):
         """Accumulated SM clocks per solver phase (handle set up with trace=1)."""

@@ -338,11 +338,12 @@ static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>
   max_bytes = 0;
   for (int k = 0; k < n; ++k) {
     const int by = upper ? n - 1 - k : k;
-    const int e0 = B.off.ptr[(size_t)by * n], e1 = B.off.ptr[(size_t)by * n + n];
-    const int nnz = e1 - e0;
-    if (nnz > 65535) return "block row has more than 65535 off-block entries";
+    const int* rp = &B.off.ptr[(size_t)by * n];
+    const int e0 = rp[0], e1 = rp[n];
+    int K = 0;
+    for (int r = 0; r < n; ++r) K = std::max(K, rp[r + 1] - rp[r]);
     int base = by * n, cmax = by * n;
-    if (nnz > 0) {
+    if (e1 > e0) {
       base = B.off.col[e0];
       cmax = base;
       for (int e = e0; e < e1; ++e) {
@@ -351,20 +352,30 @@ static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>
       }
     }
     if (cmax - base > 65535) return "off-block column span exceeds 16 bits";
-    const RecLayout<T> lay(n, nnz);
+    const RecLayout<T> lay(n, K);
     std::vector<char> rec(lay.bytes, 0);
     int* hdr = (int*)rec.data();
-    hdr[0] = base; hdr[1] = nnz; hdr[2] = by; hdr[3] = 0;
-    uint16_t* ptr = (uint16_t*)(rec.data() + lay.o_ptr);
+    hdr[0] = base; hdr[1] = K; hdr[2] = by; hdr[3] = 0;
     uint16_t* col = (uint16_t*)(rec.data() + lay.o_col);
     T* val = (T*)(rec.data() + lay.o_val);
     T* inv = (T*)(rec.data() + lay.o_inv);
-    for (int r = 0; r <= n; ++r) ptr[r] = (uint16_t)(B.off.ptr[(size_t)by * n + r] - e0);
-    for (int e = e0; e < e1; ++e) {
-      col[e - e0] = (uint16_t)(B.off.col[e] - base);
-      val[e - e0] = (T)B.off.val[e];
+    for (int r = 0; r < n; ++r)
+      for (int e = rp[r]; e < rp[r + 1]; ++e) {
+        const int slot = e - rp[r];
+        col[(size_t)slot * n + r] = (uint16_t)(B.off.col[e] - base);
+        val[(size_t)slot * n + r] = (T)B.off.val[e];
+      }
+    // dense inverse: host rows (row-major packed) -> column-major packed
+    const double* src = &B.inv[(size_t)by * blk];
+    for (int r = 0; r < n; ++r) {
+      if (!upper) {
+        for (int j = 0; j <= r; ++j)
+          inv[(size_t)j * n - (size_t)j * (j - 1) / 2 + (r - j)] = (T)src[(size_t)r * (r + 1) / 2 + j];
+      } else {
+        const size_t ro = (size_t)r * n - (size_t)r * (r - 1) / 2;
+        for (int j = r; j < n; ++j) inv[(size_t)j * (j + 1) / 2 + r] = (T)src[ro + (j - r)];
+      }
     }
-    for (size_t q = 0; q < blk; ++q) inv[q] = (T)B.inv[(size_t)by * blk + q];
     off.push_back((long long)out.size());
     out.insert(out.end(), rec.begin(), rec.end());
     max_bytes = std::max(max_bytes, lay.bytes);
@@ -517,26 +528,45 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
       d.Pb32 = up.put32(pb); d.PTb32 = up.put32(ptb);
     }
   }
-  // h-levels: 9-point stencils and Gauss--Seidel coefficients
+  // h-levels: 9-point stencils and Gauss--Seidel row records (lane-interleaved)
   d.nh = (int)H.size();
+  int gs_max = 0;
   for (int k = 0; k < d.nh; ++k) {
-    const int nk = H[k].n, Nk = nk * nk;
-    std::vector<double> G((size_t)Nk * G_NCOEF);
-    for (int i = 0; i < Nk; ++i) {
-      const double* a = &H[k].val[(size_t)i * 9];
-      if (a[4] == 0.0) return fail(IGM_ERR_NUMERIC, "zero diagonal at p = 1");
-      double* g = &G[(size_t)i * G_NCOEF];
-      g[G_SW] = a[0]; g[G_S] = a[1]; g[G_SE] = a[2]; g[G_E] = a[5];
-      g[G_NW] = a[6]; g[G_N] = a[7]; g[G_NE] = a[8];
-      g[G_ALPHA] = (i % nk) > 0 ? -a[3] / a[4] : 0.0;
-      g[G_INVC] = 1.0 / a[4];
+    const int nk = H[k].n;
+    const int E = (nk + 31) / 32;
+    const int es_g = o.precision == 0 ? 8 : 4;
+    const int rec_bytes = G_NCOEF * E * 32 * es_g;  // multiple of 128
+    std::vector<char> recs((size_t)rec_bytes * nk, 0);
+    std::vector<long long> goff(nk + 1);
+    for (int by = 0; by < nk; ++by) {
+      goff[by] = (long long)by * rec_bytes;
+      char* rec = recs.data() + (size_t)by * rec_bytes;
+      for (int r = 0; r < nk; ++r) {
+        const double* a = &H[k].val[(size_t)(by * nk + r) * 9];
+        if (a[4] == 0.0) return fail(IGM_ERR_NUMERIC, "zero diagonal at p = 1");
+        double g[G_NCOEF];
+        g[G_SW] = a[0]; g[G_S] = a[1]; g[G_SE] = a[2]; g[G_E] = a[5];
+        g[G_NW] = a[6]; g[G_N] = a[7]; g[G_NE] = a[8];
+        g[G_ALPHA] = r > 0 ? -a[3] / a[4] : 0.0;
+        g[G_INVC] = 1.0 / a[4];
+        const int lane = r / E, e = r % E;
+        for (int q = 0; q < G_NCOEF; ++q) {
+          const size_t idx = (size_t)(q * E + e) * 32 + lane;
+          if (o.precision == 0) ((double*)rec)[idx] = g[q];
+          else ((float*)rec)[idx] = (float)g[q];
+        }
+      }
     }
+    goff[nk] = (long long)nk * rec_bytes;
     d.h[k].n = nk;
     d.h[k].A64 = up.put(H[k].val);
     d.h[k].A32 = up.put32(H[k].val);
-    d.h[k].G64 = up.put(G);
-    d.h[k].G32 = up.put32(G);
+    d.h[k].G.recs = up.put(recs);
+    d.h[k].G.off = up.put(goff);
+    d.h[k].G.max_bytes = rec_bytes;
+    gs_max = std::max(gs_max, rec_bytes);
   }
+  d.slot_bytes = (std::max(d.slot_bytes, gs_max) + 127) & ~127;
   d.Cinv = up.put(Cinv);
   std::vector<int> wops;
   gen_wcycle(0, d.nh - 1, wops);

@@ -25,15 +25,6 @@ enum : int { ST_OK = 0, ST_NOT_CONVERGED = -4, ST_TIMEOUT = -5, ST_NUMERIC = -6 
 // Gauss--Seidel coefficients per unknown, in this order.
 enum GsCoef : int { G_SW = 0, G_S, G_SE, G_E, G_NW, G_N, G_NE, G_ALPHA, G_INVC, G_NCOEF };
 
-struct HLevelD {
-  int n;                       // unknowns per direction (N_k = n*n)
-  const double* A64;           // 9-point stencil [N_k][9], (dy+1)*3 + (dx+1)
-  const float* A32;
-  const double* G64;           // Gauss--Seidel coefficients [N_k][G_NCOEF]:
-  const float* G32;            //   the 7 non-W off-diagonal couplings, alpha = -a_W/a_C, 1/a_C
-  int ox, ob, ot;              // arena element offsets of x_k, b_k, t_k
-};
-
 // Block-row records of one triangular factor, streamed into shared memory:
 // record k (grid row k for L, n-1-k for U) at recs + off[k], off[n] = end.
 // Layout (all parts 16-byte aligned): int header[4] = {base, nnz, row, 0};
@@ -43,6 +34,16 @@ struct RecSet {
   const char* recs;
   const long long* off;
   int max_bytes;
+};
+
+struct HLevelD {
+  int n;                       // unknowns per direction (N_k = n*n)
+  const double* A64;           // 9-point stencil [N_k][9], (dy+1)*3 + (dx+1)
+  const float* A32;
+  RecSet G;                    // Gauss--Seidel row records in the smoothing precision:
+                               // per grid row, coefficient q of unknown r = lane*E + e at
+                               // (q*E + e)*32 + lane (q: GsCoef, E = ceil(n/32))
+  int ox, ob, ot;              // arena element offsets of x_k, b_k, t_k
 };
 
 // Everything one spatial solve needs, by value as a kernel parameter.
@@ -205,54 +206,69 @@ __device__ __forceinline__ T src(const S* x, const S* x2, int i) {
   return v;
 }
 
-// Stage 1 of the sum factorisation along xi: tm = (I (x) M1) x, tk = (I (x) K1) x.
-template <typename T, typename S>
-__device__ void sf_stage1(int n, int p, const T* bM, const T* bK, const S* x, const S* x2, T* tm,
-                          T* tk) {
-  const int W = 2 * p + 1, N = n * n;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const int ix = i % n, row0 = i - ix;
+// Sum factorisation on the affine map (A = M1 (x) M1 + c (K1 (x) M1 + M1 (x) K1)):
+//   stage 1 (along xi):  tm = (I (x) bM) x,  tk = (I (x) bK) x
+//   stage 2 (along eta): y  = (bA (x) I) tm + (bcM (x) I) tk
+// With bM = M1, bK = K1, bA = M1 + c K1, bcM = c M1 this is A; with
+// bK = bcM = nullptr and bA = M1 it is the mass matrix.  Bands are [n][W],
+// W = 2p+1, zero outside the grid.  Each thread owns one band row (held in
+// registers: W is a template parameter) and walks the other grid direction.
+// If b != nullptr, out = b - y and, when red != nullptr, the CTA-wide sum of
+// out^2 is returned; else out = y.
+template <typename T, int W, typename S>
+__device__ void sf_stage1_w(int n, const T* bM, const T* bK, const S* x, const S* x2, T* tm, T* tk) {
+  constexpr int p = (W - 1) / 2;
+  const int R = blockDim.x / n;
+  if ((int)threadIdx.x >= R * n) return;
+  const int ix = threadIdx.x % n, g = threadIdx.x / n;
+  T m[W], k[W];
+  int jx[W];
+#pragma unroll
+  for (int o = 0; o < W; ++o) {
+    m[o] = bM[(size_t)ix * W + o];
+    k[o] = bK ? bK[(size_t)ix * W + o] : (T)0;
+    const int j = ix + o - p;
+    jx[o] = j < 0 ? 0 : (j >= n ? n - 1 : j);   // coefficient is 0 outside the grid
+  }
+  for (int iy = g; iy < n; iy += R) {
+    const int row0 = iy * n;
     T sm = 0, sk = 0;
-    const T* m = bM + (size_t)ix * W;
-    const T* k = bK ? bK + (size_t)ix * W : nullptr;
+#pragma unroll
     for (int o = 0; o < W; ++o) {
-      const int jx = ix + o - p;
-      if (jx < 0 || jx >= n) continue;
-      const T xv = src<T>(x, x2, row0 + jx);
+      const T xv = src<T>(x, x2, row0 + jx[o]);
       sm += m[o] * xv;
-      if (k) sk += k[o] * xv;
+      sk += k[o] * xv;
     }
-    tm[i] = sm;
-    if (tk) tk[i] = sk;
+    tm[row0 + ix] = sm;
+    if (tk) tk[row0 + ix] = sk;
   }
 }
 
-// y = A x by sum factorisation on the affine map:
-//   stage 1 (along xi):  tm = (I (x) bM) x,  tk = (I (x) bK) x
-//   stage 2 (along eta): y  = (bA (x) I) tm + (bcM (x) I) tk
-// With bM = M1, bK = K1, bA = M1 + c K1, bcM = c M1 this is
-// A = M1 (x) M1 + c (K1 (x) M1 + M1 (x) K1); with bK = bcM = nullptr and
-// bA = M1 it is the mass matrix.  If b != nullptr, out = b - y and, when red
-// != nullptr, the CTA-wide sum of out^2 is returned; else out = y.
-template <typename T, typename S, typename B, typename O>
-__device__ double apply_A_affine(int n, int p, const T* bM, const T* bK, const T* bA,
-                                 const T* bcM, const S* x, const S* x2, const B* b, O* out, T* tm,
-                                 T* tk, double* red) {
-  const int W = 2 * p + 1, N = n * n;
-  sf_stage1<T>(n, p, bM, bK, x, x2, tm, tk);
-  __syncthreads();
+template <typename T, int W, typename B, typename O>
+__device__ double sf_stage2_w(int n, const T* bA, const T* bcM, const T* tm, const T* tk,
+                              const B* b, O* out) {
+  constexpr int p = (W - 1) / 2;
+  const int R = blockDim.x / n;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const int ix = i % n, iy = i / n;
-    const T* a = bA + (size_t)iy * W;
-    const T* cm = bcM ? bcM + (size_t)iy * W : nullptr;
+  if ((int)threadIdx.x >= R * n) return acc;
+  const int iy = threadIdx.x % n, g = threadIdx.x / n;
+  T a[W], cm[W];
+  int jy[W];
+#pragma unroll
+  for (int o = 0; o < W; ++o) {
+    a[o] = bA[(size_t)iy * W + o];
+    cm[o] = bcM ? bcM[(size_t)iy * W + o] : (T)0;
+    const int j = iy + o - p;
+    jy[o] = (j < 0 ? 0 : (j >= n ? n - 1 : j)) * n;
+  }
+  for (int ix = g; ix < n; ix += R) {
     T y = 0;
+#pragma unroll
     for (int o = 0; o < W; ++o) {
-      const int jy = iy + o - p;
-      if (jy < 0 || jy >= n) continue;
-      y += a[o] * tm[ix + n * jy];
-      if (cm) y += cm[o] * tk[ix + n * jy];
+      y += a[o] * tm[jy[o] + ix];
+      if (bcM) y += cm[o] * tk[jy[o] + ix];
     }
+    const int i = iy * n + ix;
     if (b) {
       const T r = (T)b[i] - y;
       out[i] = (O)r;
@@ -261,9 +277,34 @@ __device__ double apply_A_affine(int n, int p, const T* bM, const T* bK, const T
       out[i] = (O)y;
     }
   }
+  return acc;
+}
+
+template <typename T, int W, typename S, typename B, typename O>
+__device__ double apply_A_affine_w(int n, const T* bM, const T* bK, const T* bA, const T* bcM,
+                                   const S* x, const S* x2, const B* b, O* out, T* tm, T* tk,
+                                   double* red) {
+  sf_stage1_w<T, W>(n, bM, bK, x, x2, tm, tk);
+  __syncthreads();
+  const double acc = sf_stage2_w<T, W>(n, bA, bcM, tm, tk, b, out);
   if (b && red) return block_sum(acc, red);
   __syncthreads();
   return 0.0;
+}
+
+template <typename T, typename S, typename B, typename O>
+__device__ double apply_A_affine(int n, int p, const T* bM, const T* bK, const T* bA,
+                                 const T* bcM, const S* x, const S* x2, const B* b, O* out, T* tm,
+                                 T* tk, double* red) {
+  switch (p) {
+    case 2: return apply_A_affine_w<T, 5>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    case 3: return apply_A_affine_w<T, 7>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    case 4: return apply_A_affine_w<T, 9>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    case 5: return apply_A_affine_w<T, 11>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    case 6: return apply_A_affine_w<T, 13>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    case 7: return apply_A_affine_w<T, 15>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    default: return apply_A_affine_w<T, 17>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+  }
 }
 
 // Curved: y = A x from the (2p+1)^2 stencil; same out/b convention.
@@ -308,15 +349,20 @@ __device__ __forceinline__ size_t upper_off(int i, int n) {
 
 __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
-// Byte offsets inside a record (must match the host packing in capi.cu).
+// Byte offsets inside a factor record (must match the host packing in
+// capi.cu).  Record of grid row `by`: int header[4] = {base, K, by, 0};
+// uint16 col[K][n] and T val[K][n]: the off-block entries of the grid row's n
+// rows in ELL form, slot-major (entry k of row r at k*n + r; padding has
+// val 0, col 0); T inv[n(n+1)/2]: the dense inverse of the diagonal block,
+// packed column-major (lower: column j holds rows j..n-1 at j*n - j(j-1)/2;
+// upper: column j holds rows 0..j at j(j+1)/2).  Every part 16-byte aligned.
 template <typename T>
 struct RecLayout {
-  int o_ptr, o_col, o_val, o_inv, bytes;
-  __host__ __device__ RecLayout(int n, int nnz) {
-    o_ptr = 16;
-    o_col = o_ptr + ((2 * (n + 1) + 15) & ~15);
-    o_val = o_col + ((2 * nnz + 15) & ~15);
-    o_inv = o_val + (((int)sizeof(T) * nnz + 15) & ~15);
+  int o_col, o_val, o_inv, bytes;
+  __host__ __device__ RecLayout(int n, int K) {
+    o_col = 16;
+    o_val = o_col + ((2 * K * n + 15) & ~15);
+    o_inv = o_val + (((int)sizeof(T) * K * n + 15) & ~15);
     bytes = o_inv + (((int)sizeof(T) * (n * (n + 1) / 2) + 15) & ~15);
   }
 };
@@ -334,15 +380,18 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int
 // v_row = inv(D_row) t (packed dense, lower for L, upper for U).  Record k+S
 // is in flight while record k is used.  Returns false after a wait timeout.
 template <typename T, bool UPPER>
-__device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int* status) {
+__device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int* status,
+                            unsigned long long* trace = nullptr) {
   if (pp.dead) return false;
   const int S = pp.nstage < n ? pp.nstage : n;
   if (threadIdx.x == 0)
     for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
   for (int k = 0; k < n; ++k) {
     const int s = k % pp.nstage;
+    PhaseClock pw(trace);
     const bool got = mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u);
     pp.phase ^= 1u << s;
+    pw.stop(8);
     if (__syncthreads_or(!got)) {
       if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
       // drain the copies still in flight (bounded) before giving up
@@ -356,35 +405,56 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     }
     const char* rec = pp.ring + (size_t)s * pp.slot;
     const int* hdr = (const int*)rec;
-    const int base = hdr[0], nnz = hdr[1], by = hdr[2];
-    const RecLayout<T> lay(n, nnz);
-    const uint16_t* ptr = (const uint16_t*)(rec + lay.o_ptr);
+    const int base = hdr[0], K = hdr[1], by = hdr[2];
+    const RecLayout<T> lay(n, K);
     const uint16_t* col = (const uint16_t*)(rec + lay.o_col);
     const T* val = (const T*)(rec + lay.o_val);
     const T* inv = (const T*)(rec + lay.o_inv);
-    for_group_rows(n, [&](int r, bool act, int gl) {
-      T sacc = 0;
-      if (act)
-        for (int e = ptr[r] + gl; e < ptr[r + 1]; e += kGroup) sacc += val[e] * v[base + col[e]];
-      sacc = group_sum(sacc);
-      if (act && gl == 0) row[r] = v[by * n + r] - sacc;
-    });
-    __syncthreads();
-    for_group_rows(n, [&](int r, bool act, int gl) {
-      T sacc = 0;
-      if (act) {
-        if (!UPPER) {
-          const T* Dr = inv + lower_off(r);
-          for (int j = gl; j <= r; j += kGroup) sacc += Dr[j] * row[j];
-        } else {
-          const T* Dr = inv + upper_off(r, n);
-          for (int j = r + gl; j < n; j += kGroup) sacc += Dr[j - r] * row[j];
-        }
+    PhaseClock p1(trace);
+    // phase 1: t_r = v_i - sum_k val[k][r] v[base + col[k][r]] (one thread per row;
+    // a warp reads consecutive slot entries and, for shift-invariant patterns,
+    // consecutive v entries)
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      int kk = 0;
+      for (; kk + 4 <= K; kk += 4) {
+        s0 += val[(kk + 0) * n + r] * v[base + col[(kk + 0) * n + r]];
+        s1 += val[(kk + 1) * n + r] * v[base + col[(kk + 1) * n + r]];
+        s2 += val[(kk + 2) * n + r] * v[base + col[(kk + 2) * n + r]];
+        s3 += val[(kk + 3) * n + r] * v[base + col[(kk + 3) * n + r]];
       }
-      sacc = group_sum(sacc);
-      if (act && gl == 0) v[by * n + r] = sacc;
-    });
+      for (; kk < K; ++kk) s0 += val[kk * n + r] * v[base + col[kk * n + r]];
+      row[r] = v[by * n + r] - ((s0 + s1) + (s2 + s3));
+    }
     __syncthreads();
+    p1.stop(9);
+    PhaseClock p2(trace);
+    // phase 2: v_row = inv(D) t, one thread per row, column-major inverse
+    for (int r = threadIdx.x; r < n; r += blockDim.x) {
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      if (!UPPER) {
+        int j = 0;
+        for (; j + 4 <= r + 1; j += 4) {
+          s0 += inv[(size_t)(j + 0) * n - (size_t)(j + 0) * (j - 1) / 2 + (r - j - 0)] * row[j + 0];
+          s1 += inv[(size_t)(j + 1) * n - (size_t)(j + 1) * (j + 0) / 2 + (r - j - 1)] * row[j + 1];
+          s2 += inv[(size_t)(j + 2) * n - (size_t)(j + 2) * (j + 1) / 2 + (r - j - 2)] * row[j + 2];
+          s3 += inv[(size_t)(j + 3) * n - (size_t)(j + 3) * (j + 2) / 2 + (r - j - 3)] * row[j + 3];
+        }
+        for (; j <= r; ++j) s0 += inv[(size_t)j * n - (size_t)j * (j - 1) / 2 + (r - j)] * row[j];
+      } else {
+        int j = r;
+        for (; j + 4 <= n; j += 4) {
+          s0 += inv[(size_t)(j + 0) * (j + 1) / 2 + r] * row[j + 0];
+          s1 += inv[(size_t)(j + 1) * (j + 2) / 2 + r] * row[j + 1];
+          s2 += inv[(size_t)(j + 2) * (j + 3) / 2 + r] * row[j + 2];
+          s3 += inv[(size_t)(j + 3) * (j + 4) / 2 + r] * row[j + 3];
+        }
+        for (; j < n; ++j) s0 += inv[(size_t)j * (j + 1) / 2 + r] * row[j];
+      }
+      v[by * n + r] = (s0 + s1) + (s2 + s3);
+    }
+    __syncthreads();
+    p2.stop(10);
     if (threadIdx.x == 0 && k + pp.nstage < n) {
       fence_proxy_async();
       pipe_issue(pp, R, k + pp.nstage, s);
@@ -393,63 +463,64 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
   return true;
 }
 
-// One forward lexicographic Gauss--Seidel sweep on a 9-point operator, run by
-// warp 0 (the caller synchronises the CTA afterwards).  Grid row by: every
-// lane forms t_r = b_r - (E, S-row, N-row couplings) x for its E consecutive
-// unknowns; the in-row recurrence x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha =
-// -a_W/a_C) is an affine map per unknown, composed by a warp-wide scan.  The
-// next row's coefficients are loaded into registers while the current row is
-// solved.
+// One forward lexicographic Gauss--Seidel sweep on a 9-point operator.  Warp 0
+// does the work; each grid row's coefficients arrive in the record ring ahead
+// of use.  Grid row by: every lane forms t_r = b_r - (E, S-row, N-row
+// couplings) x for its E consecutive unknowns; the in-row recurrence
+// x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha = -a_W/a_C) is an affine map per
+// unknown, composed by a warp-wide scan.  All threads keep the ring's phase
+// bits in step; returns false (CTA-uniformly) after a wait timed out.
 template <typename T, int EMAX>
-__device__ void gs_sweep_warp(int n, const T* __restrict__ cf, const T* b, T* x) {
-  if (threadIdx.x >= 32) return;
-  // FP32: the next row's coefficients are prefetched into registers; FP64
-  // (the reference form) reads them in place to stay within the register budget
-  constexpr bool kPre = sizeof(T) == 4;
-  constexpr int EP = kPre ? EMAX : 1;
-  const int lane = threadIdx.x;
+__device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status) {
+  const int lane = threadIdx.x & 31;
   const int E = (n + 31) / 32;
   const int r0 = lane * E;
-  T c[EP][G_NCOEF], cn[EP][G_NCOEF];
-  if (kPre) {
-#pragma unroll
-    for (int e = 0; e < EP; ++e)
-#pragma unroll
-      for (int q = 0; q < G_NCOEF; ++q)
-        c[e][q] = (e < E && r0 + e < n) ? cf[(size_t)(r0 + e) * G_NCOEF + q] : (T)0;
-  }
+  const int S = pp.nstage < n ? pp.nstage : n;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
   for (int by = 0; by < n; ++by) {
-    if (kPre && by + 1 < n) {
-#pragma unroll
-      for (int e = 0; e < EP; ++e)
-#pragma unroll
-        for (int q = 0; q < G_NCOEF; ++q)
-          cn[e][q] = (e < E && r0 + e < n) ? cf[(size_t)((by + 1) * n + r0 + e) * G_NCOEF + q] : (T)0;
+    const int s = by % pp.nstage;
+    if (!mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
+      if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
+      pp.dead = true;
     }
-    T beta[EMAX];
+    pp.phase ^= 1u << s;
+    if (__any_sync(0xffffffffu, pp.dead)) {
+      pp.dead = true;
+      for (int j = by + 1; j < by + S && j < n; ++j) {
+        const int sj = j % pp.nstage;
+        mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
+        pp.phase ^= 1u << sj;
+      }
+      return;
+    }
+    const T* cf = (const T*)(pp.ring + (size_t)s * pp.slot);
+    T beta[EMAX], alpha[EMAX];
     T A = 1, B = 0;
 #pragma unroll
     for (int e = 0; e < EMAX; ++e) {
       beta[e] = 0;
+      alpha[e] = 0;
       const int r = r0 + e;
       if (e < E && r < n) {
         const int i = by * n + r;
-        const T* ce = kPre ? c[kPre ? e : 0] : cf + (size_t)i * G_NCOEF;
+        auto c = [&](int q) { return cf[(q * E + e) * 32 + lane]; };
         T t = b[i];
-        if (r + 1 < n) t -= ce[G_E] * x[i + 1];
+        if (r + 1 < n) t -= c(G_E) * x[i + 1];
         if (by > 0) {
-          if (r > 0) t -= ce[G_SW] * x[i - n - 1];
-          t -= ce[G_S] * x[i - n];
-          if (r + 1 < n) t -= ce[G_SE] * x[i - n + 1];
+          if (r > 0) t -= c(G_SW) * x[i - n - 1];
+          t -= c(G_S) * x[i - n];
+          if (r + 1 < n) t -= c(G_SE) * x[i - n + 1];
         }
         if (by + 1 < n) {
-          if (r > 0) t -= ce[G_NW] * x[i + n - 1];
-          t -= ce[G_N] * x[i + n];
-          if (r + 1 < n) t -= ce[G_NE] * x[i + n + 1];
+          if (r > 0) t -= c(G_NW) * x[i + n - 1];
+          t -= c(G_N) * x[i + n];
+          if (r + 1 < n) t -= c(G_NE) * x[i + n + 1];
         }
-        beta[e] = ce[G_INVC] * t;
-        B = ce[G_ALPHA] * B + beta[e];
-        A = ce[G_ALPHA] * A;
+        alpha[e] = c(G_ALPHA);
+        beta[e] = c(G_INVC) * t;
+        B = alpha[e] * B + beta[e];
+        A = alpha[e] * A;
       }
     }
     // inclusive scan of the lanes' affine maps x_out = A x_in + B
@@ -469,27 +540,33 @@ __device__ void gs_sweep_warp(int n, const T* __restrict__ cf, const T* b, T* x)
     for (int e = 0; e < EMAX; ++e) {
       const int r = r0 + e;
       if (e < E && r < n) {
-        const T alpha = kPre ? c[kPre ? e : 0][G_ALPHA] : cf[(size_t)(by * n + r) * G_NCOEF + G_ALPHA];
-        xin = alpha * xin + beta[e];
+        xin = alpha[e] * xin + beta[e];
         x[by * n + r] = xin;
       }
     }
     __syncwarp();
-    if (kPre) {
-#pragma unroll
-      for (int e = 0; e < EP; ++e)
-#pragma unroll
-        for (int q = 0; q < G_NCOEF; ++q) c[e][q] = cn[e][q];
+    if (threadIdx.x == 0 && by + pp.nstage < n) {
+      fence_proxy_async();
+      pipe_issue(pp, R, by + pp.nstage, s);
     }
   }
 }
 
 template <typename T>
-__device__ void gs_sweep(int n, const T* cf, const T* b, T* x) {
-  if (n <= 32) gs_sweep_warp<T, 1>(n, cf, b, x);
-  else if (n <= 64) gs_sweep_warp<T, 2>(n, cf, b, x);
-  else gs_sweep_warp<T, 4>(n, cf, b, x);
-  __syncthreads();
+__device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status) {
+  if (pp.dead) return false;
+  if (threadIdx.x < 32) {
+    if (n <= 32) gs_rows_warp<T, 1>(n, R, pp, b, x, status);
+    else if (n <= 64) gs_rows_warp<T, 2>(n, R, pp, b, x, status);
+    else gs_rows_warp<T, 4>(n, R, pp, b, x, status);
+  } else {
+    // keep this thread's copy of the ring parities in step with warp 0
+    for (int by = 0; by < n; ++by) pp.phase ^= 1u << (by % pp.nstage);
+  }
+  // warp 0's phase bits and dead flag are the CTA's
+  const bool dead = __syncthreads_or(pp.dead);
+  pp.dead = dead;
+  return !dead;
 }
 
 // Tensor-product transfer on the affine map, stage along xi then eta:

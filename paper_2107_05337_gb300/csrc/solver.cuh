@@ -49,7 +49,6 @@ template <> struct Prec<float> {
   __device__ static const float* MpL(const PmgD& P) { return P.MpL32; }
   __device__ static const float* M1L(const PmgD& P) { return P.M1L32; }
   __device__ static const float* HA(const HLevelD& H) { return H.A32; }
-  __device__ static const float* HG(const HLevelD& H) { return H.G32; }
 };
 template <> struct Prec<double> {
   __device__ static const double* Pv(const PmgD& P) { return P.Pval64; }
@@ -59,7 +58,6 @@ template <> struct Prec<double> {
   __device__ static const double* MpL(const PmgD& P) { return P.MpL64; }
   __device__ static const double* M1L(const PmgD& P) { return P.M1L64; }
   __device__ static const double* HA(const HLevelD& H) { return H.A64; }
-  __device__ static const double* HG(const HLevelD& H) { return H.G64; }
 };
 
 // v <- U^{-1} L^{-1} v (the ILUT smoother S = (LU)^{-1} applied to v, Sec. 4).
@@ -67,8 +65,8 @@ template <> struct Prec<double> {
 template <typename T>
 __device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, T* row, int* status) {
   PhaseClock pc(P.trace);
-  bool ok = block_sweep<T, false>(P.n, P.Lrec, pp, v, row, status) &&
-            block_sweep<T, true>(P.n, P.Urec, pp, v, row, status);
+  bool ok = block_sweep<T, false>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
+            block_sweep<T, true>(P.n, P.Urec, pp, v, row, status, P.trace);
   pc.stop(2);
   return ok;
 }
@@ -90,7 +88,7 @@ __device__ void coarse_solve(int Nc, const double* Cinv, const T* b, T* x) {
 // host-generated op list.  h-level 0 holds b_0 = restricted residual and
 // x_0 = 0 on entry and the coarse correction on exit.
 template <typename T>
-__device__ void wcycle(const PmgD& P, T* A, T* row) {
+__device__ bool wcycle(const PmgD& P, Pipe& pp, T* A, int* status) {
   for (int o = 0; o < P.nops; ++o) {
     const int op = P.ops[o] & 0xff, k = P.ops[o] >> 8;
     const HLevelD& H = P.h[k];
@@ -100,8 +98,9 @@ __device__ void wcycle(const PmgD& P, T* A, T* row) {
     switch (op) {
       case W_GS: {
         PhaseClock pc(P.trace);
-        gs_sweep<T>(H.n, Prec<T>::HG(H), bk, xk);
+        const bool ok = gs_sweep<T>(H.n, H.G, pp, bk, xk, status);
         pc.stop(7);
+        if (!ok) return false;
         break;
       }
       case W_RESTRICT:
@@ -116,6 +115,7 @@ __device__ void wcycle(const PmgD& P, T* A, T* row) {
         break;
     }
   }
+  return true;
 }
 
 // r_1 = (M_1^L)^{-1} P^T t into h-level 0's b, and x_0 = 0 (Sec. 4, step 2).
@@ -186,8 +186,9 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
   // step 3: one W-cycle of h-multigrid on A_1 e_1 = r_1
   {
     PhaseClock pc(P.trace);
-    wcycle<T>(P, A, row);
+    const bool ok = wcycle<T>(P, pp, A, status);
     pc.stop(4);
+    if (!ok) return false;
   }
   // step 4: x += (M_p^L)^{-1} P e_1
   {
