@@ -241,7 +241,7 @@ class PMG:
         return Z
 
     PHASES = ("residual64", "residual", "ilut", "restrict", "wcycle", "prolong", "rhs", "gs",
-              "ilut_wait", "ilut_off", "ilut_diag")
+              "ilut_wait", "ilut_off", "ilut_diag", "gs_wait", "gs_row", "gs_scan")
 
     def trace(self, reset=True):
         """Accumulated SM clocks per solver phase (handle set up with trace=1)."""

@@ -353,27 +353,27 @@ static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>
     }
     if (cmax - base > 65535) return "off-block column span exceeds 16 bits";
     const RecLayout<T> lay(n, K);
+    const int np = lay.npad;
     std::vector<char> rec(lay.bytes, 0);
     int* hdr = (int*)rec.data();
-    hdr[0] = base; hdr[1] = K; hdr[2] = by; hdr[3] = 0;
+    hdr[0] = base; hdr[1] = K; hdr[2] = by; hdr[3] = np;
     uint16_t* col = (uint16_t*)(rec.data() + lay.o_col);
     T* val = (T*)(rec.data() + lay.o_val);
     T* inv = (T*)(rec.data() + lay.o_inv);
     for (int r = 0; r < n; ++r)
       for (int e = rp[r]; e < rp[r + 1]; ++e) {
         const int slot = e - rp[r];
-        col[(size_t)slot * n + r] = (uint16_t)(B.off.col[e] - base);
-        val[(size_t)slot * n + r] = (T)B.off.val[e];
+        col[(size_t)slot * np + r] = (uint16_t)(B.off.col[e] - base);
+        val[(size_t)slot * np + r] = (T)B.off.val[e];
       }
-    // dense inverse: host rows (row-major packed) -> column-major packed
+    // dense inverse: host rows (row-major packed) -> full column-major square
     const double* src = &B.inv[(size_t)by * blk];
     for (int r = 0; r < n; ++r) {
       if (!upper) {
-        for (int j = 0; j <= r; ++j)
-          inv[(size_t)j * n - (size_t)j * (j - 1) / 2 + (r - j)] = (T)src[(size_t)r * (r + 1) / 2 + j];
+        for (int j = 0; j <= r; ++j) inv[(size_t)j * np + r] = (T)src[(size_t)r * (r + 1) / 2 + j];
       } else {
         const size_t ro = (size_t)r * n - (size_t)r * (r - 1) / 2;
-        for (int j = r; j < n; ++j) inv[(size_t)j * (j + 1) / 2 + r] = (T)src[ro + (j - r)];
+        for (int j = r; j < n; ++j) inv[(size_t)j * np + r] = (T)src[ro + (j - r)];
       }
     }
     off.push_back((long long)out.size());

@@ -349,21 +349,27 @@ __device__ __forceinline__ size_t upper_off(int i, int n) {
 
 __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
+// Row stride of the padded record arrays: the smallest value >= n that is
+// 8 mod 32, so that the 4 lane classes of a warp (8 rows x 4 classes) hit 4
+// disjoint 8-bank ranges.
+__host__ __device__ __forceinline__ int rec_pad(int n) { return n + ((8 - n) % 32 + 32) % 32; }
+
 // Byte offsets inside a factor record (must match the host packing in
-// capi.cu).  Record of grid row `by`: int header[4] = {base, K, by, 0};
-// uint16 col[K][n] and T val[K][n]: the off-block entries of the grid row's n
-// rows in ELL form, slot-major (entry k of row r at k*n + r; padding has
-// val 0, col 0); T inv[n(n+1)/2]: the dense inverse of the diagonal block,
-// packed column-major (lower: column j holds rows j..n-1 at j*n - j(j-1)/2;
-// upper: column j holds rows 0..j at j(j+1)/2).  Every part 16-byte aligned.
+// capi.cu).  Record of grid row `by`: int header[4] = {base, K, by, npad};
+// uint16 col[K][npad] and T val[K][npad]: the off-block entries of the grid
+// row's n rows in ELL form, slot-major (entry k of row r at k*npad + r;
+// padding has val 0, col 0); T inv[n][npad]: the dense inverse of the
+// diagonal block as a full column-major square (column j at j*npad, zeros
+// outside the triangle).  Every part 16-byte aligned.
 template <typename T>
 struct RecLayout {
-  int o_col, o_val, o_inv, bytes;
+  int npad, o_col, o_val, o_inv, bytes;
   __host__ __device__ RecLayout(int n, int K) {
+    npad = rec_pad(n);
     o_col = 16;
-    o_val = o_col + ((2 * K * n + 15) & ~15);
-    o_inv = o_val + (((int)sizeof(T) * K * n + 15) & ~15);
-    bytes = o_inv + (((int)sizeof(T) * (n * (n + 1) / 2) + 15) & ~15);
+    o_val = o_col + ((2 * K * npad + 15) & ~15);
+    o_inv = o_val + (((int)sizeof(T) * K * npad + 15) & ~15);
+    bytes = o_inv + (((int)sizeof(T) * n * npad + 15) & ~15);
   }
 };
 
@@ -407,52 +413,42 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     const int* hdr = (const int*)rec;
     const int base = hdr[0], K = hdr[1], by = hdr[2];
     const RecLayout<T> lay(n, K);
+    const int np = lay.npad, NN = n * n;
     const uint16_t* col = (const uint16_t*)(rec + lay.o_col);
     const T* val = (const T*)(rec + lay.o_val);
     const T* inv = (const T*)(rec + lay.o_inv);
     PhaseClock p1(trace);
-    // phase 1: t_r = v_i - sum_k val[k][r] v[base + col[k][r]] (one thread per row;
-    // a warp reads consecutive slot entries and, for shift-invariant patterns,
-    // consecutive v entries)
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      int kk = 0;
-      for (; kk + 4 <= K; kk += 4) {
-        s0 += val[(kk + 0) * n + r] * v[base + col[(kk + 0) * n + r]];
-        s1 += val[(kk + 1) * n + r] * v[base + col[(kk + 1) * n + r]];
-        s2 += val[(kk + 2) * n + r] * v[base + col[(kk + 2) * n + r]];
-        s3 += val[(kk + 3) * n + r] * v[base + col[(kk + 3) * n + r]];
-      }
-      for (; kk < K; ++kk) s0 += val[kk * n + r] * v[base + col[kk * n + r]];
-      row[r] = v[by * n + r] - ((s0 + s1) + (s2 + s3));
-    }
+    // phase 1: t_r = v_i - sum_k val[k][r] v[base + col[k][r]]; a warp covers
+    // 8 rows x 4 slot classes (k = c, c+4, ...), reduced by two shuffles
+    for_group_rows(n, [&](int r, bool act, int c) {
+      T sacc = 0;
+      if (act)
+        for (int kk = c; kk < K; kk += kGroup) {
+          const int idx = base + col[kk * np + r];
+          sacc += val[kk * np + r] * v[idx < NN ? idx : 0];
+        }
+      sacc = group_sum(sacc);
+      if (act && c == 0) row[r] = v[by * n + r] - sacc;
+    });
     __syncthreads();
     p1.stop(9);
     PhaseClock p2(trace);
-    // phase 2: v_row = inv(D) t, one thread per row, column-major inverse
-    for (int r = threadIdx.x; r < n; r += blockDim.x) {
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    // phase 2: v_row = inv(D) t; the warp's 8 rows share the column index j of
+    // every step (zeros outside the triangle), so reads are conflict-free
+    for_group_rows(n, [&](int r, bool act, int c) {
+      T sacc = 0;
+      const int rw = r & ~7;  // first row of this warp
       if (!UPPER) {
-        int j = 0;
-        for (; j + 4 <= r + 1; j += 4) {
-          s0 += inv[(size_t)(j + 0) * n - (size_t)(j + 0) * (j - 1) / 2 + (r - j - 0)] * row[j + 0];
-          s1 += inv[(size_t)(j + 1) * n - (size_t)(j + 1) * (j + 0) / 2 + (r - j - 1)] * row[j + 1];
-          s2 += inv[(size_t)(j + 2) * n - (size_t)(j + 2) * (j + 1) / 2 + (r - j - 2)] * row[j + 2];
-          s3 += inv[(size_t)(j + 3) * n - (size_t)(j + 3) * (j + 2) / 2 + (r - j - 3)] * row[j + 3];
-        }
-        for (; j <= r; ++j) s0 += inv[(size_t)j * n - (size_t)j * (j - 1) / 2 + (r - j)] * row[j];
+        const int jend = (rw + 7 < n - 1) ? rw + 7 : n - 1;
+        if (act)
+          for (int j = c; j <= jend; j += kGroup) sacc += inv[j * np + r] * row[j];
       } else {
-        int j = r;
-        for (; j + 4 <= n; j += 4) {
-          s0 += inv[(size_t)(j + 0) * (j + 1) / 2 + r] * row[j + 0];
-          s1 += inv[(size_t)(j + 1) * (j + 2) / 2 + r] * row[j + 1];
-          s2 += inv[(size_t)(j + 2) * (j + 3) / 2 + r] * row[j + 2];
-          s3 += inv[(size_t)(j + 3) * (j + 4) / 2 + r] * row[j + 3];
-        }
-        for (; j < n; ++j) s0 += inv[(size_t)j * (j + 1) / 2 + r] * row[j];
+        if (act)
+          for (int j = rw + c; j < n; j += kGroup) sacc += inv[j * np + r] * row[j];
       }
-      v[by * n + r] = (s0 + s1) + (s2 + s3);
-    }
+      sacc = group_sum(sacc);
+      if (act && c == 0) v[by * n + r] = sacc;
+    });
     __syncthreads();
     p2.stop(10);
     if (threadIdx.x == 0 && k + pp.nstage < n) {
@@ -471,7 +467,8 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
 // unknown, composed by a warp-wide scan.  All threads keep the ring's phase
 // bits in step; returns false (CTA-uniformly) after a wait timed out.
 template <typename T, int EMAX>
-__device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status) {
+__device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status,
+                             unsigned long long* trace) {
   const int lane = threadIdx.x & 31;
   const int E = (n + 31) / 32;
   const int r0 = lane * E;
@@ -480,6 +477,7 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
     for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
   for (int by = 0; by < n; ++by) {
     const int s = by % pp.nstage;
+    PhaseClock pw(trace);
     if (!mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
       if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
       pp.dead = true;
@@ -494,6 +492,8 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
       }
       return;
     }
+    pw.stop(11);
+    PhaseClock pt(trace);
     const T* cf = (const T*)(pp.ring + (size_t)s * pp.slot);
     T beta[EMAX], alpha[EMAX];
     T A = 1, B = 0;
@@ -523,6 +523,8 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
         A = alpha[e] * A;
       }
     }
+    pt.stop(12);
+    PhaseClock ps(trace);
     // inclusive scan of the lanes' affine maps x_out = A x_in + B
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -545,6 +547,7 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
       }
     }
     __syncwarp();
+    ps.stop(13);
     if (threadIdx.x == 0 && by + pp.nstage < n) {
       fence_proxy_async();
       pipe_issue(pp, R, by + pp.nstage, s);
@@ -553,12 +556,13 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
 }
 
 template <typename T>
-__device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status) {
+__device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status,
+                         unsigned long long* trace = nullptr) {
   if (pp.dead) return false;
   if (threadIdx.x < 32) {
-    if (n <= 32) gs_rows_warp<T, 1>(n, R, pp, b, x, status);
-    else if (n <= 64) gs_rows_warp<T, 2>(n, R, pp, b, x, status);
-    else gs_rows_warp<T, 4>(n, R, pp, b, x, status);
+    if (n <= 32) gs_rows_warp<T, 1>(n, R, pp, b, x, status, trace);
+    else if (n <= 64) gs_rows_warp<T, 2>(n, R, pp, b, x, status, trace);
+    else gs_rows_warp<T, 4>(n, R, pp, b, x, status, trace);
   } else {
     // keep this thread's copy of the ring parities in step with warp 0
     for (int by = 0; by < n; ++by) pp.phase ^= 1u << (by % pp.nstage);
