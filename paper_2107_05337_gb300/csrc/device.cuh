@@ -395,15 +395,18 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
   for (int k = 0; k < n; ++k) {
     const int s = k % pp.nstage;
     PhaseClock pw(trace);
-    const bool got = mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u);
+    // thread 0 observes the copy's completion (acquire); the barrier then
+    // orders the record's contents before every thread's reads
+    const bool got = threadIdx.x == 0 ? mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u) : true;
     pp.phase ^= 1u << s;
+    const bool timeout = __syncthreads_or(!got);
     pw.stop(8);
-    if (__syncthreads_or(!got)) {
+    if (timeout) {
       if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
       // drain the copies still in flight (bounded) before giving up
       for (int j = k + 1; j < k + S && j < n; ++j) {
         const int sj = j % pp.nstage;
-        mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
+        if (threadIdx.x == 0) mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
         pp.phase ^= 1u << sj;
       }
       pp.dead = true;
@@ -421,13 +424,26 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     // phase 1: t_r = v_i - sum_k val[k][r] v[base + col[k][r]]; a warp covers
     // 8 rows x 4 slot classes (k = c, c+4, ...), reduced by two shuffles
     for_group_rows(n, [&](int r, bool act, int c) {
-      T sacc = 0;
-      if (act)
-        for (int kk = c; kk < K; kk += kGroup) {
-          const int idx = base + col[kk * np + r];
-          sacc += val[kk * np + r] * v[idx < NN ? idx : 0];
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      if (act) {
+        int kk = c;
+        // 4 independent chains keep 4 gathers in flight
+        for (; kk + 3 * kGroup < K; kk += 4 * kGroup) {
+          const int i0 = base + col[(kk + 0 * kGroup) * np + r];
+          const int i1 = base + col[(kk + 1 * kGroup) * np + r];
+          const int i2 = base + col[(kk + 2 * kGroup) * np + r];
+          const int i3 = base + col[(kk + 3 * kGroup) * np + r];
+          s0 += val[(kk + 0 * kGroup) * np + r] * v[i0 < NN ? i0 : 0];
+          s1 += val[(kk + 1 * kGroup) * np + r] * v[i1 < NN ? i1 : 0];
+          s2 += val[(kk + 2 * kGroup) * np + r] * v[i2 < NN ? i2 : 0];
+          s3 += val[(kk + 3 * kGroup) * np + r] * v[i3 < NN ? i3 : 0];
         }
-      sacc = group_sum(sacc);
+        for (; kk < K; kk += kGroup) {
+          const int i0 = base + col[kk * np + r];
+          s0 += val[kk * np + r] * v[i0 < NN ? i0 : 0];
+        }
+      }
+      T sacc = group_sum((s0 + s1) + (s2 + s3));
       if (act && c == 0) row[r] = v[by * n + r] - sacc;
     });
     __syncthreads();
@@ -436,17 +452,21 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     // phase 2: v_row = inv(D) t; the warp's 8 rows share the column index j of
     // every step (zeros outside the triangle), so reads are conflict-free
     for_group_rows(n, [&](int r, bool act, int c) {
-      T sacc = 0;
+      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
       const int rw = r & ~7;  // first row of this warp
-      if (!UPPER) {
-        const int jend = (rw + 7 < n - 1) ? rw + 7 : n - 1;
-        if (act)
-          for (int j = c; j <= jend; j += kGroup) sacc += inv[j * np + r] * row[j];
-      } else {
-        if (act)
-          for (int j = rw + c; j < n; j += kGroup) sacc += inv[j * np + r] * row[j];
+      const int j0 = UPPER ? rw + c : c;
+      const int jend = UPPER ? n : ((rw + 8 < n) ? rw + 8 : n);  // exclusive
+      if (act) {
+        int j = j0;
+        for (; j + 3 * kGroup < jend; j += 4 * kGroup) {
+          s0 += inv[(j + 0 * kGroup) * np + r] * row[j + 0 * kGroup];
+          s1 += inv[(j + 1 * kGroup) * np + r] * row[j + 1 * kGroup];
+          s2 += inv[(j + 2 * kGroup) * np + r] * row[j + 2 * kGroup];
+          s3 += inv[(j + 3 * kGroup) * np + r] * row[j + 3 * kGroup];
+        }
+        for (; j < jend; j += kGroup) s0 += inv[j * np + r] * row[j];
       }
-      sacc = group_sum(sacc);
+      T sacc = group_sum((s0 + s1) + (s2 + s3));
       if (act && c == 0) v[by * n + r] = sacc;
     });
     __syncthreads();
@@ -478,8 +498,9 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
   for (int by = 0; by < n; ++by) {
     const int s = by % pp.nstage;
     PhaseClock pw(trace);
-    if (!mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
-      if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
+    // lane 0 observes the copy's completion; __syncwarp orders the reads
+    if (lane == 0 && !mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
+      if (status) atomicMin(status, ST_TIMEOUT);
       pp.dead = true;
     }
     pp.phase ^= 1u << s;
@@ -487,7 +508,7 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
       pp.dead = true;
       for (int j = by + 1; j < by + S && j < n; ++j) {
         const int sj = j % pp.nstage;
-        mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
+        if (lane == 0) mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
         pp.phase ^= 1u << sj;
       }
       return;
@@ -505,18 +526,20 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
       if (e < E && r < n) {
         const int i = by * n + r;
         auto c = [&](int q) { return cf[(q * E + e) * 32 + lane]; };
-        T t = b[i];
-        if (r + 1 < n) t -= c(G_E) * x[i + 1];
-        if (by > 0) {
-          if (r > 0) t -= c(G_SW) * x[i - n - 1];
-          t -= c(G_S) * x[i - n];
-          if (r + 1 < n) t -= c(G_SE) * x[i - n + 1];
-        }
-        if (by + 1 < n) {
-          if (r > 0) t -= c(G_NW) * x[i + n - 1];
-          t -= c(G_N) * x[i + n];
-          if (r + 1 < n) t -= c(G_NE) * x[i + n + 1];
-        }
+        // neighbours outside the grid have coefficient 0: clamp their index
+        const bool hasE = r + 1 < n, hasW = r > 0, hasS = by > 0, hasN = by + 1 < n;
+        const int iE = hasE ? i + 1 : i;
+        const int iS = hasS ? i - n : i, iN = hasN ? i + n : i;
+        const T xE = x[iE];
+        const T xSW = x[hasW ? iS - 1 : iS], xS = x[iS], xSE = x[hasE ? iS + 1 : iS];
+        const T xNW = x[hasW ? iN - 1 : iN], xN = x[iN], xNE = x[hasE ? iN + 1 : iN];
+        const T cE = hasE ? c(G_E) : (T)0;
+        const T cSW = (hasS && hasW) ? c(G_SW) : (T)0, cS = hasS ? c(G_S) : (T)0;
+        const T cSE = (hasS && hasE) ? c(G_SE) : (T)0;
+        const T cNW = (hasN && hasW) ? c(G_NW) : (T)0, cN = hasN ? c(G_N) : (T)0;
+        const T cNE = (hasN && hasE) ? c(G_NE) : (T)0;
+        const T t = b[i] - (((cE * xE + cSW * xSW) + (cS * xS + cSE * xSE)) +
+                            ((cNW * xNW + cN * xN) + cNE * xNE));
         alpha[e] = c(G_ALPHA);
         beta[e] = c(G_INVC) * t;
         B = alpha[e] * B + beta[e];
