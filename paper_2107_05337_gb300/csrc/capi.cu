@@ -352,28 +352,31 @@ static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>
       }
     }
     if (cmax - base > 65535) return "off-block column span exceeds 16 bits";
-    const RecLayout<T> lay(n, K);
+    const RecLayout<T> lay(n, K, upper);
     const int np = lay.npad;
     std::vector<char> rec(lay.bytes, 0);
     int* hdr = (int*)rec.data();
     hdr[0] = base; hdr[1] = K; hdr[2] = by; hdr[3] = np;
     uint16_t* col = (uint16_t*)(rec.data() + lay.o_col);
     T* val = (T*)(rec.data() + lay.o_val);
-    T* inv = (T*)(rec.data() + lay.o_inv);
     for (int r = 0; r < n; ++r)
       for (int e = rp[r]; e < rp[r + 1]; ++e) {
         const int slot = e - rp[r];
         col[(size_t)slot * np + r] = (uint16_t)(B.off.col[e] - base);
         val[(size_t)slot * np + r] = (T)B.off.val[e];
       }
-    // dense inverse: host rows (row-major packed) -> full column-major square
+    // dense inverse by rows in 16-byte chunks (zero outside the triangle)
+    constexpr int V = 16 / (int)sizeof(T);
     const double* src = &B.inv[(size_t)by * blk];
     for (int r = 0; r < n; ++r) {
-      if (!upper) {
-        for (int j = 0; j <= r; ++j) inv[(size_t)j * np + r] = (T)src[(size_t)r * (r + 1) / 2 + j];
-      } else {
-        const size_t ro = (size_t)r * n - (size_t)r * (r - 1) / 2;
-        for (int j = r; j < n; ++j) inv[(size_t)j * np + r] = (T)src[ro + (j - r)];
+      T* dst = (T*)(rec.data() + lay.o_inv + 16 * (size_t)RecLayout<T>::rec_inv_row(r, n, upper));
+      const int j0 = upper ? r - r % V : 0;
+      const int jend = upper ? ((n + V - 1) / V) * V : (r / V + 1) * V;
+      for (int j = j0; j < jend; ++j) {
+        double vv = 0.0;
+        if (!upper && j <= r) vv = src[(size_t)r * (r + 1) / 2 + j];
+        if (upper && j >= r && j < n) vv = src[(size_t)r * n - (size_t)r * (r - 1) / 2 + (j - r)];
+        dst[j - j0] = (T)vv;
       }
     }
     off.push_back((long long)out.size());
@@ -533,7 +536,7 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   int gs_max = 0;
   for (int k = 0; k < d.nh; ++k) {
     const int nk = H[k].n;
-    const int E = (nk + 31) / 32;
+    const int E = nk <= 32 ? 1 : (nk <= 64 ? 2 : 4);  // lanes' width in gs_sweep
     const int es_g = o.precision == 0 ? 8 : 4;
     const int rec_bytes = G_NCOEF * E * 32 * es_g;  // multiple of 128
     std::vector<char> recs((size_t)rec_bytes * nk, 0);

@@ -9,6 +9,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace igm {
 
 constexpr int kBlock = 512;       // threads per CTA of the solve kernels
@@ -189,7 +191,9 @@ template <typename F>
 __device__ __forceinline__ void for_group_rows(int nrows, F&& f) {
   const int gl = threadIdx.x % kGroup;
   const int per = blockDim.x / kGroup;
+  const int wrow = (int)(threadIdx.x & ~31u) / kGroup;  // first row of this warp in a pass
   for (int r0 = 0; r0 < nrows; r0 += per) {
+    if (r0 + wrow >= nrows) break;  // the whole warp is past the last row
     const int r = r0 + (int)threadIdx.x / kGroup;
     f(r, r < nrows, gl);
   }
@@ -357,19 +361,33 @@ __host__ __device__ __forceinline__ int rec_pad(int n) { return n + ((8 - n) % 3
 // Byte offsets inside a factor record (must match the host packing in
 // capi.cu).  Record of grid row `by`: int header[4] = {base, K, by, npad};
 // uint16 col[K][npad] and T val[K][npad]: the off-block entries of the grid
-// row's n rows in ELL form, slot-major (entry k of row r at k*npad + r;
-// padding has val 0, col 0); T inv[n][npad]: the dense inverse of the
-// diagonal block as a full column-major square (column j at j*npad, zeros
-// outside the triangle).  Every part 16-byte aligned.
+// row's n rows in ELL form, slot-major (entry k of row r at k*npad + r,
+// column base + col; padding has val 0, col 0); then the dense inverse of
+// the diagonal block stored by rows in 16-byte chunks of V = 16/sizeof(T)
+// columns: row r covers the chunks of columns [0, r] (lower) or
+// [r - r % V, n) (upper), zero-padded, at chunk offset rec_inv_row(r).
 template <typename T>
 struct RecLayout {
   int npad, o_col, o_val, o_inv, bytes;
-  __host__ __device__ RecLayout(int n, int K) {
+  __host__ __device__ RecLayout(int n, int K, bool upper) {
     npad = rec_pad(n);
     o_col = 16;
     o_val = o_col + ((2 * K * npad + 15) & ~15);
     o_inv = o_val + (((int)sizeof(T) * K * npad + 15) & ~15);
-    bytes = o_inv + (((int)sizeof(T) * n * npad + 15) & ~15);
+    bytes = o_inv + 16 * rec_inv_row(n, n, upper);
+  }
+  // chunk offset of row r (r = n gives the total number of chunks)
+  __host__ __device__ static int rec_inv_row(int r, int n, bool upper) {
+    constexpr int V = 16 / (int)sizeof(T);
+    const int nc = (n + V - 1) / V;  // chunks in a full row
+    if (!upper) {
+      // row i has floor(i/V) + 1 chunks
+      int q = r / V, rem = r % V;
+      return V * q * (q + 1) / 2 + rem * (q + 1);
+    }
+    // row i has nc - floor(i/V) chunks
+    int q = r / V, rem = r % V;
+    return V * (q * nc - q * (q - 1) / 2) + rem * (nc - q);
   }
 };
 
@@ -392,6 +410,8 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
   const int S = pp.nstage < n ? pp.nstage : n;
   if (threadIdx.x == 0)
     for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
+  // the vector loads of phase 2 read t up to the next 16-byte boundary past n
+  if (threadIdx.x < 16 / sizeof(T)) row[n + threadIdx.x] = (T)0;
   for (int k = 0; k < n; ++k) {
     const int s = k % pp.nstage;
     PhaseClock pw(trace);
@@ -415,11 +435,11 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     const char* rec = pp.ring + (size_t)s * pp.slot;
     const int* hdr = (const int*)rec;
     const int base = hdr[0], K = hdr[1], by = hdr[2];
-    const RecLayout<T> lay(n, K);
-    const int np = lay.npad, NN = n * n;
+    const RecLayout<T> lay(n, K, UPPER);
+    const int np = lay.npad;
     const uint16_t* col = (const uint16_t*)(rec + lay.o_col);
     const T* val = (const T*)(rec + lay.o_val);
-    const T* inv = (const T*)(rec + lay.o_inv);
+    const char* inv = rec + lay.o_inv;
     PhaseClock p1(trace);
     // phase 1: t_r = v_i - sum_k val[k][r] v[base + col[k][r]]; a warp covers
     // 8 rows x 4 slot classes (k = c, c+4, ...), reduced by two shuffles
@@ -428,20 +448,19 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
       if (act) {
         int kk = c;
         // 4 independent chains keep 4 gathers in flight
+        // indices were validated on the host (base + col < n*n)
+        const uint16_t* cp = col + r;
+        const T* vp = val + r;
+        const T* vb = v + base;
         for (; kk + 3 * kGroup < K; kk += 4 * kGroup) {
-          const int i0 = base + col[(kk + 0 * kGroup) * np + r];
-          const int i1 = base + col[(kk + 1 * kGroup) * np + r];
-          const int i2 = base + col[(kk + 2 * kGroup) * np + r];
-          const int i3 = base + col[(kk + 3 * kGroup) * np + r];
-          s0 += val[(kk + 0 * kGroup) * np + r] * v[i0 < NN ? i0 : 0];
-          s1 += val[(kk + 1 * kGroup) * np + r] * v[i1 < NN ? i1 : 0];
-          s2 += val[(kk + 2 * kGroup) * np + r] * v[i2 < NN ? i2 : 0];
-          s3 += val[(kk + 3 * kGroup) * np + r] * v[i3 < NN ? i3 : 0];
+          const int i0 = cp[(kk + 0 * kGroup) * np], i1 = cp[(kk + 1 * kGroup) * np];
+          const int i2 = cp[(kk + 2 * kGroup) * np], i3 = cp[(kk + 3 * kGroup) * np];
+          s0 += vp[(kk + 0 * kGroup) * np] * vb[i0];
+          s1 += vp[(kk + 1 * kGroup) * np] * vb[i1];
+          s2 += vp[(kk + 2 * kGroup) * np] * vb[i2];
+          s3 += vp[(kk + 3 * kGroup) * np] * vb[i3];
         }
-        for (; kk < K; kk += kGroup) {
-          const int i0 = base + col[kk * np + r];
-          s0 += val[kk * np + r] * v[i0 < NN ? i0 : 0];
-        }
+        for (; kk < K; kk += kGroup) s0 += vp[kk * np] * vb[cp[kk * np]];
       }
       T sacc = group_sum((s0 + s1) + (s2 + s3));
       if (act && c == 0) row[r] = v[by * n + r] - sacc;
@@ -449,24 +468,34 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     __syncthreads();
     p1.stop(9);
     PhaseClock p2(trace);
-    // phase 2: v_row = inv(D) t; the warp's 8 rows share the column index j of
-    // every step (zeros outside the triangle), so reads are conflict-free
+    // phase 2: v_row = inv(D) t.  Lane class c of row r takes the 16-byte
+    // chunks c, c+4, ... of the row's stored column range: one vector load of
+    // the inverse and one (broadcast) of t per V columns.
     for_group_rows(n, [&](int r, bool act, int c) {
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      const int rw = r & ~7;  // first row of this warp
-      const int j0 = UPPER ? rw + c : c;
-      const int jend = UPPER ? n : ((rw + 8 < n) ? rw + 8 : n);  // exclusive
+      constexpr int V = 16 / (int)sizeof(T);
+      using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+      T s0 = 0, s1 = 0;
       if (act) {
-        int j = j0;
-        for (; j + 3 * kGroup < jend; j += 4 * kGroup) {
-          s0 += inv[(j + 0 * kGroup) * np + r] * row[j + 0 * kGroup];
-          s1 += inv[(j + 1 * kGroup) * np + r] * row[j + 1 * kGroup];
-          s2 += inv[(j + 2 * kGroup) * np + r] * row[j + 2 * kGroup];
-          s3 += inv[(j + 3 * kGroup) * np + r] * row[j + 3 * kGroup];
+        const int j0 = UPPER ? r - r % V : 0;
+        const int nch = UPPER ? (n - j0 + V - 1) / V : r / V + 1;
+        const Vec* ip = (const Vec*)(inv + 16 * RecLayout<T>::rec_inv_row(r, n, UPPER));
+        const Vec* tp = (const Vec*)(row + j0);
+        for (int q = c; q < nch; q += kGroup) {
+          const Vec a = ip[q], t = tp[q];
+          if (sizeof(T) == 4) {
+            const float4& af = reinterpret_cast<const float4&>(a);
+            const float4& tf = reinterpret_cast<const float4&>(t);
+            s0 += af.x * tf.x + af.y * tf.y;
+            s1 += af.z * tf.z + af.w * tf.w;
+          } else {
+            const double2& ad = reinterpret_cast<const double2&>(a);
+            const double2& td = reinterpret_cast<const double2&>(t);
+            s0 += ad.x * td.x;
+            s1 += ad.y * td.y;
+          }
         }
-        for (; j < jend; j += kGroup) s0 += inv[j * np + r] * row[j];
       }
-      T sacc = group_sum((s0 + s1) + (s2 + s3));
+      const T sacc = group_sum(s0 + s1);
       if (act && c == 0) v[by * n + r] = sacc;
     });
     __syncthreads();
@@ -490,7 +519,7 @@ template <typename T, int EMAX>
 __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status,
                              unsigned long long* trace) {
   const int lane = threadIdx.x & 31;
-  const int E = (n + 31) / 32;
+  constexpr int E = EMAX;  // unknowns per lane (the host packs rows for this width)
   const int r0 = lane * E;
   const int S = pp.nstage < n ? pp.nstage : n;
   if (threadIdx.x == 0)
@@ -523,7 +552,7 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
       beta[e] = 0;
       alpha[e] = 0;
       const int r = r0 + e;
-      if (e < E && r < n) {
+      if (r < n) {
         const int i = by * n + r;
         auto c = [&](int q) { return cf[(q * E + e) * 32 + lane]; };
         // neighbours outside the grid have coefficient 0: clamp their index
@@ -564,7 +593,7 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
 #pragma unroll
     for (int e = 0; e < EMAX; ++e) {
       const int r = r0 + e;
-      if (e < E && r < n) {
+      if (r < n) {
         xin = alpha[e] * xin + beta[e];
         x[by * n + r] = xin;
       }
