@@ -330,12 +330,12 @@ static int align4(int x) { return (x + 3) & ~3; }
 // device.cuh).  Record k covers grid row k (lower) or n-1-k (upper).
 template <typename T>
 static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>& out,
-                                std::vector<long long>& off, int& max_bytes) {
+                                int& rec_bytes) {
+  std::vector<long long> off;
+  int max_bytes = 0;
   const int n = B.n;
   const size_t blk = (size_t)n * (n + 1) / 2;
-  out.clear();
-  off.clear();
-  max_bytes = 0;
+  std::vector<char> packed;
   for (int k = 0; k < n; ++k) {
     const int by = upper ? n - 1 - k : k;
     const int* rp = &B.off.ptr[(size_t)by * n];
@@ -379,11 +379,16 @@ static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>
         dst[j - j0] = (T)vv;
       }
     }
-    off.push_back((long long)out.size());
-    out.insert(out.end(), rec.begin(), rec.end());
+    off.push_back((long long)packed.size());
+    packed.insert(packed.end(), rec.begin(), rec.end());
     max_bytes = std::max(max_bytes, lay.bytes);
   }
-  off.push_back((long long)out.size());
+  off.push_back((long long)packed.size());
+  // every record padded to the same size (a multiple of 128 bytes)
+  rec_bytes = (max_bytes + 127) & ~127;
+  out.assign((size_t)rec_bytes * n, 0);
+  for (int k = 0; k < n; ++k)
+    std::copy(packed.begin() + off[k], packed.begin() + off[k + 1], out.begin() + (size_t)k * rec_bytes);
   return "";
 }
 
@@ -498,19 +503,18 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.sM64 = ops->sM64;
   // ILUT records in the smoothing precision
   std::vector<char> recL, recU;
-  std::vector<long long> offL, offU;
   int maxL = 0, maxU = 0;
   if (o.precision == 0) {
-    e = pack_records<double>(BL, false, recL, offL, maxL);
-    if (e.empty()) e = pack_records<double>(BU, true, recU, offU, maxU);
+    e = pack_records<double>(BL, false, recL, maxL);
+    if (e.empty()) e = pack_records<double>(BU, true, recU, maxU);
   } else {
-    e = pack_records<float>(BL, false, recL, offL, maxL);
-    if (e.empty()) e = pack_records<float>(BU, true, recU, offU, maxU);
+    e = pack_records<float>(BL, false, recL, maxL);
+    if (e.empty()) e = pack_records<float>(BU, true, recU, maxU);
   }
   if (!e.empty()) return fail(IGM_ERR_ARG, e);
-  d.Lrec.recs = up.put(recL); d.Lrec.off = up.put(offL); d.Lrec.max_bytes = maxL;
-  d.Urec.recs = up.put(recU); d.Urec.off = up.put(offU); d.Urec.max_bytes = maxU;
-  d.slot_bytes = (std::max(maxL, maxU) + 127) & ~127;
+  d.Lrec.recs = up.put(recL); d.Lrec.bytes = maxL;
+  d.Urec.recs = up.put(recU); d.Urec.bytes = maxU;
+  d.slot_bytes = std::max(maxL, maxU);
   // transfers: CSR always (curved), tensor-product bands on the affine map
   d.N1 = lo.N;
   d.n1 = lo.n;
@@ -540,9 +544,7 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     const int es_g = o.precision == 0 ? 8 : 4;
     const int rec_bytes = G_NCOEF * E * 32 * es_g;  // multiple of 128
     std::vector<char> recs((size_t)rec_bytes * nk, 0);
-    std::vector<long long> goff(nk + 1);
     for (int by = 0; by < nk; ++by) {
-      goff[by] = (long long)by * rec_bytes;
       char* rec = recs.data() + (size_t)by * rec_bytes;
       for (int r = 0; r < nk; ++r) {
         const double* a = &H[k].val[(size_t)(by * nk + r) * 9];
@@ -560,13 +562,11 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
         }
       }
     }
-    goff[nk] = (long long)nk * rec_bytes;
     d.h[k].n = nk;
     d.h[k].A64 = up.put(H[k].val);
     d.h[k].A32 = up.put32(H[k].val);
     d.h[k].G.recs = up.put(recs);
-    d.h[k].G.off = up.put(goff);
-    d.h[k].G.max_bytes = rec_bytes;
+    d.h[k].G.bytes = rec_bytes;
     gs_max = std::max(gs_max, rec_bytes);
   }
   d.slot_bytes = (std::max(d.slot_bytes, gs_max) + 127) & ~127;

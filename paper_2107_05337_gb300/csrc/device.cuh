@@ -27,15 +27,12 @@ enum : int { ST_OK = 0, ST_NOT_CONVERGED = -4, ST_TIMEOUT = -5, ST_NUMERIC = -6 
 // Gauss--Seidel coefficients per unknown, in this order.
 enum GsCoef : int { G_SW = 0, G_S, G_SE, G_E, G_NW, G_N, G_NE, G_ALPHA, G_INVC, G_NCOEF };
 
-// Block-row records of one triangular factor, streamed into shared memory:
-// record k (grid row k for L, n-1-k for U) at recs + off[k], off[n] = end.
-// Layout (all parts 16-byte aligned): int header[4] = {base, nnz, row, 0};
-// uint16 ptr[n+1] (entry offsets); uint16 col[nnz] (column - base);
-// T val[nnz]; T inv[n(n+1)/2] (packed dense inverse of the diagonal block).
+// Block-row records of one triangular factor (or of Gauss--Seidel rows),
+// streamed into shared memory: record k is grid row k (L, Gauss--Seidel) or
+// n-1-k (U); the layout is described at RecLayout.
 struct RecSet {
-  const char* recs;
-  const long long* off;
-  int max_bytes;
+  const char* recs;        // record k at recs + k * bytes (every record padded to `bytes`)
+  int bytes;
 };
 
 struct HLevelD {
@@ -392,9 +389,11 @@ struct RecLayout {
 };
 
 // Issue the bulk copy of record k of a set into ring slot s (thread 0 only).
+// Records have a fixed size so that no offset needs to be loaded here (a
+// global load at this point would sit on every row's critical path).
 __device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int s) {
-  const long long a = R.off[k], b = R.off[k + 1];
-  bulk_load(pp.ring + (size_t)s * pp.slot, R.recs + a, (uint32_t)(b - a), &pp.bar[s]);
+  bulk_load(pp.ring + (size_t)s * pp.slot, R.recs + (size_t)k * R.bytes, (uint32_t)R.bytes,
+            &pp.bar[s]);
 }
 
 // Block-row triangular sweep v <- D^{-1}-weighted substitution over the n
