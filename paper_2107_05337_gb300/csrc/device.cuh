@@ -181,6 +181,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Strided CTA loop whose trip count is the same for every thread; the bound
+// test is a predicate inside the body.  (A loop whose trip count differs
+// between the lanes of a warp needs a reconvergence point and makes the next
+// CTA barrier several times more expensive on this GPU.)
+#define IGM_FOR_CTA(i, lim)                                                          \
+  for (int i##_b = 0, i##_n = (lim); i##_b < i##_n; i##_b += (int)blockDim.x)        \
+    if (const int i = i##_b + (int)threadIdx.x; i < i##_n)
+
 // Warp-uniform loop over rows with kGroup lanes per row: every lane of every
 // warp runs the same number of passes, so the group shuffles inside f are
 // always executed by the full warp.  f(row, active, lane_in_group).
@@ -220,8 +228,8 @@ template <typename T, int W, typename S>
 __device__ void sf_stage1_w(int n, const T* bM, const T* bK, const S* x, const S* x2, T* tm, T* tk) {
   constexpr int p = (W - 1) / 2;
   const int R = blockDim.x / n;
-  if ((int)threadIdx.x >= R * n) return;
-  const int ix = threadIdx.x % n, g = threadIdx.x / n;
+  const bool on = (int)threadIdx.x < R * n;
+  const int ix = on ? threadIdx.x % n : 0, g = threadIdx.x / n;
   T m[W], k[W];
   int jx[W];
 #pragma unroll
@@ -231,7 +239,10 @@ __device__ void sf_stage1_w(int n, const T* bM, const T* bK, const S* x, const S
     const int j = ix + o - p;
     jx[o] = j < 0 ? 0 : (j >= n ? n - 1 : j);   // coefficient is 0 outside the grid
   }
-  for (int iy = g; iy < n; iy += R) {
+  const int iters = (n + R - 1) / R;  // the same for every thread
+  for (int t = 0; t < iters; ++t) {
+    const int iy = g + t * R;
+    if (!on || iy >= n) continue;
     const int row0 = iy * n;
     T sm = 0, sk = 0;
 #pragma unroll
@@ -251,8 +262,8 @@ __device__ double sf_stage2_w(int n, const T* bA, const T* bcM, const T* tm, con
   constexpr int p = (W - 1) / 2;
   const int R = blockDim.x / n;
   double acc = 0.0;
-  if ((int)threadIdx.x >= R * n) return acc;
-  const int iy = threadIdx.x % n, g = threadIdx.x / n;
+  const bool on = (int)threadIdx.x < R * n;
+  const int iy = on ? threadIdx.x % n : 0, g = threadIdx.x / n;
   T a[W], cm[W];
   int jy[W];
 #pragma unroll
@@ -262,7 +273,10 @@ __device__ double sf_stage2_w(int n, const T* bA, const T* bcM, const T* tm, con
     const int j = iy + o - p;
     jy[o] = (j < 0 ? 0 : (j >= n ? n - 1 : j)) * n;
   }
-  for (int ix = g; ix < n; ix += R) {
+  const int iters = (n + R - 1) / R;
+  for (int t = 0; t < iters; ++t) {
+    const int ix = g + t * R;
+    if (!on || ix >= n) continue;
     T y = 0;
 #pragma unroll
     for (int o = 0; o < W; ++o) {
@@ -314,7 +328,7 @@ __device__ double apply_stencil(int n, int w, const T* sA, const S* x, const S* 
                                 O* out, double* red) {
   const int W = 2 * w + 1, N = n * n;
   double acc = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  IGM_FOR_CTA(i, N) {
     const int ix = i % n, iy = i / n;
     const T* a = sA + (size_t)i * W * W;
     T y = 0;
@@ -414,9 +428,9 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
   for (int k = 0; k < n; ++k) {
     const int s = k % pp.nstage;
     PhaseClock pw(trace);
-    // thread 0 observes the copy's completion (acquire); the barrier then
+    // warp 0 observes the copy's completion (acquire); the barrier then
     // orders the record's contents before every thread's reads
-    const bool got = threadIdx.x == 0 ? mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u) : true;
+    const bool got = threadIdx.x < 32 ? mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u) : true;
     pp.phase ^= 1u << s;
     const bool timeout = __syncthreads_or(!got);
     pw.stop(8);
@@ -425,7 +439,7 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
       // drain the copies still in flight (bounded) before giving up
       for (int j = k + 1; j < k + S && j < n; ++j) {
         const int sj = j % pp.nstage;
-        if (threadIdx.x == 0) mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
+        if (threadIdx.x < 32) mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
         pp.phase ^= 1u << sj;
       }
       pp.dead = true;
@@ -474,12 +488,19 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
       constexpr int V = 16 / (int)sizeof(T);
       using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
       T s0 = 0, s1 = 0;
-      if (act) {
-        const int j0 = UPPER ? r - r % V : 0;
-        const int nch = UPPER ? (n - j0 + V - 1) / V : r / V + 1;
-        const Vec* ip = (const Vec*)(inv + 16 * RecLayout<T>::rec_inv_row(r, n, UPPER));
-        const Vec* tp = (const Vec*)(row + j0);
-        for (int q = c; q < nch; q += kGroup) {
+      const int rr = act ? r : 0;
+      const int j0 = UPPER ? rr - rr % V : 0;
+      const int nch = UPPER ? (n - j0 + V - 1) / V : rr / V + 1;
+      // warp-uniform trip count: the most chunks any of the warp's 8 rows has
+      const int rw = r & ~7;
+      const int nch_w = UPPER ? (n - (rw - rw % V) + V - 1) / V
+                              : ((rw + 7 < n ? rw + 7 : n - 1) / V + 1);
+      const Vec* ip = (const Vec*)(inv + 16 * RecLayout<T>::rec_inv_row(rr, n, UPPER));
+      const Vec* tp = (const Vec*)(row + j0);
+      const int steps = (nch_w + kGroup - 1) / kGroup;
+      for (int st = 0; st < steps; ++st) {
+        const int q = c + st * kGroup;
+        if (act && q < nch) {
           const Vec a = ip[q], t = tp[q];
           if (sizeof(T) == 4) {
             const float4& af = reinterpret_cast<const float4&>(a);
@@ -526,9 +547,8 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
   for (int by = 0; by < n; ++by) {
     const int s = by % pp.nstage;
     PhaseClock pw(trace);
-    // lane 0 observes the copy's completion; __syncwarp orders the reads
-    if (lane == 0 && !mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
-      if (status) atomicMin(status, ST_TIMEOUT);
+    if (!mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
+      if (status && lane == 0) atomicMin(status, ST_TIMEOUT);
       pp.dead = true;
     }
     pp.phase ^= 1u << s;
@@ -536,7 +556,7 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
       pp.dead = true;
       for (int j = by + 1; j < by + S && j < n; ++j) {
         const int sj = j % pp.nstage;
-        if (lane == 0) mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
+        mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
         pp.phase ^= 1u << sj;
       }
       return;
@@ -630,7 +650,7 @@ __device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int
 template <typename T, bool ADD>
 __device__ void transfer_tp(int nin, int nout, int w, const int* start, const T* band,
                             const T* scale, const T* in, T* tmp, T* out) {
-  for (int i = threadIdx.x; i < nin * nout; i += blockDim.x) {
+  IGM_FOR_CTA(i, nin * nout) {
     const int jx = i % nout, iy = i / nout;
     const T* bd = band + (size_t)jx * w;
     const T* src = in + (size_t)iy * nin + start[jx];
@@ -639,7 +659,7 @@ __device__ void transfer_tp(int nin, int nout, int w, const int* start, const T*
     tmp[i] = s;
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < nout * nout; i += blockDim.x) {
+  IGM_FOR_CTA(i, nout * nout) {
     const int jx = i % nout, jy = i / nout;
     const T* bd = band + (size_t)jy * w;
     const int s0 = start[jy];
@@ -655,7 +675,7 @@ __device__ void transfer_tp(int nin, int nout, int w, const int* start, const T*
 template <typename T>
 __device__ void residual9(int n, const T* A, const T* b, const T* x, T* t) {
   const int N = n * n;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+  IGM_FOR_CTA(i, N) {
     const int ix = i % n, iy = i / n;
     const T* a = A + (size_t)i * 9;
     T y = 0;
@@ -678,7 +698,7 @@ __device__ void residual9(int n, const T* A, const T* b, const T* x, T* t) {
 template <typename T>
 __device__ void restrict_bilinear(int nf, const T* t, T* bc, T* xc) {
   const int nc = (nf - 1) / 2, Nc = nc * nc;
-  for (int I = threadIdx.x; I < Nc; I += blockDim.x) {
+  IGM_FOR_CTA(I, Nc) {
     const int cx = I % nc, cy = I / nc;
     T s = 0;
     for (int fy = 2 * cy; fy <= 2 * cy + 2; ++fy) {
@@ -698,24 +718,20 @@ __device__ void restrict_bilinear(int nf, const T* t, T* bc, T* xc) {
 template <typename T>
 __device__ void prolong_bilinear(int nf, const T* xc, T* xf) {
   const int nc = (nf - 1) / 2, Nf = nf * nf;
-  for (int i = threadIdx.x; i < Nf; i += blockDim.x) {
+  IGM_FOR_CTA(i, Nf) {
     const int fx = i % nf, fy = i / nf;
-    int cxs[2], cys[2];
-    T wxs[2], wys[2];
-    int nxs = 0, nys = 0;
-    if (fx & 1) { cxs[0] = (fx - 1) / 2; wxs[0] = 1; nxs = 1; }
-    else {
-      if (fx / 2 - 1 >= 0) { cxs[nxs] = fx / 2 - 1; wxs[nxs++] = 0.5; }
-      if (fx / 2 < nc) { cxs[nxs] = fx / 2; wxs[nxs++] = 0.5; }
-    }
-    if (fy & 1) { cys[0] = (fy - 1) / 2; wys[0] = 1; nys = 1; }
-    else {
-      if (fy / 2 - 1 >= 0) { cys[nys] = fy / 2 - 1; wys[nys++] = 0.5; }
-      if (fy / 2 < nc) { cys[nys] = fy / 2; wys[nys++] = 0.5; }
-    }
+    // odd fine index 2c+1: coarse c with weight 1; even 2c: coarse c-1 and c with 1/2
+    const bool ox = fx & 1, oy = fy & 1;
+    const int cx0 = ox ? (fx - 1) / 2 : fx / 2 - 1, cx1 = fx / 2;
+    const int cy0 = oy ? (fy - 1) / 2 : fy / 2 - 1, cy1 = fy / 2;
+    const T wx0 = ox ? (T)1 : (T)0.5, wy0 = oy ? (T)1 : (T)0.5;
+    const bool vx0 = cx0 >= 0 && cx0 < nc, vx1 = !ox && cx1 < nc;
+    const bool vy0 = cy0 >= 0 && cy0 < nc, vy1 = !oy && cy1 < nc;
     T s = 0;
-    for (int b = 0; b < nys; ++b)
-      for (int a = 0; a < nxs; ++a) s += wxs[a] * wys[b] * xc[cxs[a] + nc * cys[b]];
+    if (vy0 && vx0) s += wx0 * wy0 * xc[cx0 + nc * cy0];
+    if (vy0 && vx1) s += (T)0.5 * wy0 * xc[cx1 + nc * cy0];
+    if (vy1 && vx0) s += wx0 * (T)0.5 * xc[cx0 + nc * cy1];
+    if (vy1 && vx1) s += (T)0.25 * xc[cx1 + nc * cy1];
     xf[i] += s;
   }
   __syncthreads();

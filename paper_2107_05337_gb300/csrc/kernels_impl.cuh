@@ -43,10 +43,10 @@ __global__ void __launch_bounds__(kBlock) k_ilut_apply(PmgD P, const double* r, 
   double* zc = z + (size_t)blockIdx.x * ld;
   T* A = (T*)arena;
   T* t = A + P.o_t;
-  for (int i = threadIdx.x; i < P.N; i += blockDim.x) t[i] = (T)rc[i];
+  IGM_FOR_CTA(i, P.N) t[i] = (T)rc[i];
   __syncthreads();
   ilut_apply<T>(P, pp, t, A + P.o_row, status);
-  for (int i = threadIdx.x; i < P.N; i += blockDim.x) zc[i] = (double)t[i];
+  IGM_FOR_CTA(i, P.N) zc[i] = (double)t[i];
 }
 
 // One backward-Euler step into point n of the level (Sec. 3: the step
@@ -71,7 +71,7 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
   double* Wn = a.W + (size_t)n * N;
   double* x = Wn;
   if (residual) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) xr[i] = Wn[i];
+    IGM_FOR_CTA(i, N) xr[i] = Wn[i];
     __syncthreads();
     x = xr;
   }
@@ -83,7 +83,7 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
   if (residual) {
     double* gout = a.gnext + (size_t)(j + 1) * N;
     double s = 0.0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    IGM_FOR_CTA(i, N) {
       const double r = xr[i] - Wn[i];
       gout[i] = r;
       s += r * r;
@@ -116,13 +116,13 @@ __global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
         double* w = a.W + (size_t)(j * m) * N;
         const double* wc = a.Wc + (size_t)j * N;
         const double* gc = a.gc + (size_t)j * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
+        IGM_FOR_CTA(i, N) w[i] += wc[i] + gc[i];
       }
       if (j == a.nint - 1) {
         double* w = a.W + (size_t)a.Nl * N;
         const double* wc = a.Wc + (size_t)a.nint * N;
         const double* gc = a.gc + (size_t)a.nint * N;
-        for (int i = threadIdx.x; i < N; i += blockDim.x) w[i] += wc[i] + gc[i];
+        IGM_FOR_CTA(i, N) w[i] += wc[i] + gc[i];
       }
       __syncthreads();
       break;

@@ -127,7 +127,7 @@ __device__ void restrict_p1(const PmgD& P, const T* t, T* A) {
                           A + H0.ob);
   else
     csr_scaled<T, false>(P.N1, P.PTptr, P.PTcol, Prec<T>::PTv(P), Prec<T>::M1L(P), t, A + H0.ob);
-  for (int i = threadIdx.x; i < P.N1; i += blockDim.x) A[H0.ox + i] = 0;
+  IGM_FOR_CTA(i, P.N1) A[H0.ox + i] = 0;
   __syncthreads();
 }
 
@@ -157,7 +157,7 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
   for (int s = 0; s < P.nu1; ++s) {
     const bool zero = x_is_zero && s == 0;
     if (zero) {
-      for (int i = threadIdx.x; i < N; i += blockDim.x) t[i] = b[i];
+      IGM_FOR_CTA(i, N) t[i] = b[i];
       __syncthreads();
     } else if (!(s == 0 && t_is_residual)) {
       PhaseClock pc(P.trace);
@@ -165,11 +165,11 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
       pc.stop(1);
     }
     if (!ilut_apply<T>(P, pp, t, row, status)) return false;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = zero ? t[i] : x[i] + t[i];
+    IGM_FOR_CTA(i, N) x[i] = zero ? t[i] : x[i] + t[i];
     __syncthreads();
   }
   if (P.nu1 == 0 && x_is_zero) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = 0;
+    IGM_FOR_CTA(i, N) x[i] = 0;
     __syncthreads();
   }
   // step 2: r_1 = (M_1^L)^{-1} P^T (b - A x)
@@ -204,7 +204,7 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
       pc.stop(1);
     }
     if (!ilut_apply<T>(P, pp, t, row, status)) return false;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += t[i];
+    IGM_FOR_CTA(i, N) x[i] += t[i];
     __syncthreads();
   }
   return true;
@@ -212,7 +212,7 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
 
 __device__ __forceinline__ double block_dot(const double* a, int N, double* red) {
   double s = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) s += a[i] * a[i];
+  IGM_FOR_CTA(i, N) s += a[i] * a[i];
   return block_sum(s, red);
 }
 
@@ -229,7 +229,7 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
   const int N = P.N;
   const double nb2 = block_dot(b, N, red);
   if (nb2 == 0.0) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] = 0.0;
+    IGM_FOR_CTA(i, N) x[i] = 0.0;
     __syncthreads();
     return 0;
   }
@@ -274,7 +274,7 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
       for (int k = 0; k < P.inner && ok; ++k)
         ok = pmg_cycle<float>(P, pp, r, d, A, false, k == 0, status);
       if (!ok) break;
-      for (int i = threadIdx.x; i < N; i += blockDim.x) x[i] += (double)d[i];
+      IGM_FOR_CTA(i, N) x[i] += (double)d[i];
       __syncthreads();
       ++cyc;
     }
@@ -293,7 +293,7 @@ __device__ inline void build_rhs(const PmgD& P, const double* u, const double* u
   else
     apply_stencil<double>(P.n, P.w, P.sM64, u, ug, (const double*)nullptr, out, (double*)nullptr);
   if (fhat && scale != 0.0) {
-    for (int i = threadIdx.x; i < P.N; i += blockDim.x) out[i] += scale * fhat[i];
+    IGM_FOR_CTA(i, P.N) out[i] += scale * fhat[i];
     __syncthreads();
   }
 }
