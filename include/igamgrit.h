@@ -134,6 +134,25 @@ void pmg_destroy(pmg_handle* h);
 igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long ld, int ncycles,
                       int* cycles_out, igm_stream s);
 
+/* pmg_vcycle for callers that cannot allocate device memory.  This entry point
+ * has no counterpart in the paper; it exists for users of the library whose
+ * device memory is committed elsewhere (a host application that reserves
+ * the GPU's memory up front for its own pool, or a real-time loop in which an
+ * allocation would synchronise the device and break its timing): it calls no
+ * cudaMalloc, cudaFree or other allocating routine.  Same arguments, results
+ * and statuses as pmg_vcycle; the handle must already be set up (pmg_setup
+ * allocates).  Its scratch (status word, per-column cycle counts, and the
+ * per-column working vectors when they do not fit in shared memory) lives in
+ * one static 16 MiB device buffer that every device which loads the library
+ * holds until the process exits.  Calls needing more than 16 MiB of scratch
+ * return IGM_ERR_ARG with the required size in igm_last_error().  The first
+ * call on a device looks up the buffer's device address, so make that first
+ * call before any stream capture.  All calls share the buffer, which keeps
+ * the last call's contents (the call clears what must start at zero): calls
+ * that overlap on the GPU (other streams, other host threads) race. */
+igm_status pmg_vcycle_static(pmg_handle* h, int nrhs, const double* b, double* x, long ld,
+                             int ncycles, int* cycles_out, igm_stream s);
+
 /* Block-row triangular sweeps with the ILUT factors (diagnostics and tests):
  * z = (L U)^{-1} r on nrhs DEVICE columns, in the handle's precision. */
 igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, double* z, long ld,

@@ -60,6 +60,8 @@ EXPORTS = {
     "pmg_destroy": (None, [c_void_p]),
     "pmg_vcycle": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int, POINTER(c_int),
                            c_void_p]),
+    "pmg_vcycle_static": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int,
+                                  POINTER(c_int), c_void_p]),
     "pmg_ilut_apply": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_void_p]),
     "pmg_trace": (c_int, [c_void_p, POINTER(ctypes.c_longlong), c_int]),
     "pmg_ilut_factors": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -230,6 +232,17 @@ class PMG:
         nrhs = B.shape[0]
         cyc = (c_int * nrhs)()
         st = lib().pmg_vcycle(self.h, nrhs, _dptr(B), _dptr(X), self.N, ncycles, cyc, _stream())
+        if check:
+            _check(st)
+        return np.array(cyc[:], dtype=np.int64), st
+
+    def solve_static(self, B, X, ncycles=0, check=True):
+        """As solve(), through pmg_vcycle_static (no device allocation)."""
+        assert B.dtype == X.dtype and B.is_contiguous() and X.is_contiguous()
+        nrhs = B.shape[0]
+        cyc = (c_int * nrhs)()
+        st = lib().pmg_vcycle_static(self.h, nrhs, _dptr(B), _dptr(X), self.N, ncycles, cyc,
+                                     _stream())
         if check:
             _check(st)
         return np.array(cyc[:], dtype=np.int64), st

@@ -9,6 +9,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -674,6 +675,72 @@ extern "C" igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, doubl
   if (cycles_out) std::memcpy(cycles_out, hc.data(), sizeof(int) * nrhs);
   if (hc[nrhs] == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
   if (hc[nrhs] == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "spatial solve hit max_cycles");
+  return IGM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pmg_vcycle_static: the same solve with no allocation at all.  Its scratch
+// (status word, per-column cycle counts and, when the working vectors do not
+// fit in shared memory, the per-CTA arenas) lives in this file-scope device
+// array.  Host code must not use the array's name as a device address: the
+// address is looked up once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB on every device
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+static std::mutex g_static_mutex;
+static void* g_static_ptr[128] = {nullptr};
+
+// Device address of g_static_scratch on the current device (looked up on the
+// first call for that device).
+static igm_status static_scratch(void** out) {
+  int dev = 0;
+  CU(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 128) return fail(IGM_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_static_mutex);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    CU(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return IGM_OK;
+}
+
+extern "C" igm_status pmg_vcycle_static(pmg_handle* h, int nrhs, const double* b, double* x,
+                                        long ld, int ncycles, int* cycles_out, igm_stream s) {
+  if (!h || !b || !x) return fail(IGM_ERR_ARG, "null argument");
+  if (nrhs < 0 || ncycles < 0 || ld < h->d.N) return fail(IGM_ERR_ARG, "bad nrhs/ld/ncycles");
+  if (nrhs == 0) return IGM_OK;
+  // layout: [status: 256 B][cycle counts: nrhs ints, 256-aligned][arenas]
+  const size_t o_cyc = 256;
+  const size_t o_arena = o_cyc + (((size_t)nrhs * sizeof(int) + 255) & ~(size_t)255);
+  const size_t arena_total = h->arena_smem ? 0 : (size_t)h->arena_bytes * nrhs;
+  const size_t need = o_arena + arena_total;
+  if (need > kStaticScratchBytes)
+    return fail(IGM_ERR_ARG, "pmg_vcycle_static: " + std::to_string(nrhs) + " columns need " +
+                                 std::to_string(need) + " bytes of scratch; the static buffer holds " +
+                                 std::to_string(kStaticScratchBytes));
+  void* base = nullptr;
+  igm_status rs = static_scratch(&base);
+  if (rs != IGM_OK) return rs;
+  char* scratch = (char*)base;
+  int* dstat = (int*)scratch;
+  int* dcyc = (int*)(scratch + o_cyc);
+  char* garena = h->arena_smem ? nullptr : scratch + o_arena;
+  cudaStream_t st = (cudaStream_t)s;
+  // the buffer keeps the previous call's contents: clear what must start at zero
+  CU(cudaMemsetAsync(scratch, 0, o_arena, st));
+  CU(launch_pmg_solve(h->d.precision, h->d, nrhs, smem_of(h), st, b, x, ld, ncycles, dcyc, dstat,
+                      garena));
+  g_launches++;
+  int hstat = 0;
+  if (cycles_out)
+    CU(cudaMemcpyAsync(cycles_out, dcyc, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(&hstat, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  if (hstat == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
+  if (hstat == ST_TIMEOUT) return fail(IGM_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (hstat == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "spatial solve hit max_cycles");
   return IGM_OK;
 }
 
