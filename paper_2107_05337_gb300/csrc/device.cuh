@@ -17,7 +17,7 @@ constexpr int kBlock = 512;       // threads per CTA of the solve kernels
 constexpr int kGroup = 4;         // lanes cooperating on one matrix row
 constexpr int kMaxH = 8;          // max h-multigrid levels at p = 1
 constexpr int kMaxStage = 4;      // max depth of the record ring
-constexpr long kSpinLimit = 1L << 22;  // bounded mbarrier waits (each try_wait may suspend)
+constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier polls (~1 s), then IGM_ERR_TIMEOUT
 
 enum WOp : int { W_GS = 0, W_RESTRICT = 1, W_COARSE = 2, W_PROLONG = 3 };
 
@@ -108,10 +108,12 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
       ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(b)) : "memory");
 }
+// Non-blocking probe of the phase with the given parity (test_wait never
+// suspends the thread; the records are normally complete long before use).
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n"
       " selp.u32 %0, 1, 0, p;\n}"
       : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
   return ok != 0;
