@@ -327,44 +327,37 @@ static void gen_wcycle(int k, int last, std::vector<int>& ops) {
 
 static int align4(int x) { return (x + 3) & ~3; }
 
-// Pack the block-row records of one triangular factor (layout: RecLayout in
-// device.cuh).  Record k covers grid row k (lower) or n-1-k (upper).
+// Pack the block-row records of one triangular factor for G lanes per row
+// (layout: RecLayout in device.cuh).  Record k covers grid row k (lower) or
+// n-1-k (upper); every record is padded to the same size (a multiple of 128
+// bytes) so that record k starts at k * rec_bytes.
 template <typename T>
-static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>& out,
+static std::string pack_records(const BlockTri& B, bool upper, int G, std::vector<char>& out,
                                 int& rec_bytes) {
-  std::vector<long long> off;
-  int max_bytes = 0;
   const int n = B.n;
+  const int N = n * n;
   const size_t blk = (size_t)n * (n + 1) / 2;
-  std::vector<char> packed;
+  std::vector<std::vector<char>> recs;
+  int max_bytes = 0;
   for (int k = 0; k < n; ++k) {
     const int by = upper ? n - 1 - k : k;
     const int* rp = &B.off.ptr[(size_t)by * n];
-    const int e0 = rp[0], e1 = rp[n];
     int K = 0;
     for (int r = 0; r < n; ++r) K = std::max(K, rp[r + 1] - rp[r]);
-    int base = by * n, cmax = by * n;
-    if (e1 > e0) {
-      base = B.off.col[e0];
-      cmax = base;
-      for (int e = e0; e < e1; ++e) {
-        base = std::min(base, B.off.col[e]);
-        cmax = std::max(cmax, B.off.col[e]);
-      }
-    }
-    if (cmax - base > 65535) return "off-block column span exceeds 16 bits";
-    const RecLayout<T> lay(n, K, upper);
-    const int np = lay.npad;
+    const int KL = (K + G - 1) / G;
+    const RecLayout<T> lay(n, KL, G, upper);
     std::vector<char> rec(lay.bytes, 0);
     int* hdr = (int*)rec.data();
-    hdr[0] = base; hdr[1] = K; hdr[2] = by; hdr[3] = np;
-    uint16_t* col = (uint16_t*)(rec.data() + lay.o_col);
-    T* val = (T*)(rec.data() + lay.o_val);
+    hdr[0] = KL; hdr[1] = by; hdr[2] = G; hdr[3] = 0;
+    RecEntry<T>* ent = (RecEntry<T>*)(rec.data() + lay.o_ent);
     for (int r = 0; r < n; ++r)
       for (int e = rp[r]; e < rp[r + 1]; ++e) {
         const int slot = e - rp[r];
-        col[(size_t)slot * np + r] = (uint16_t)(B.off.col[e] - base);
-        val[(size_t)slot * np + r] = (T)B.off.val[e];
+        const int col = B.off.col[e];
+        if (col < 0 || col >= N) return "factor column out of range";
+        RecEntry<T>& x = ent[((size_t)(slot / G) * n + r) * G + slot % G];
+        x.val = (T)B.off.val[e];
+        x.off = col * (int)sizeof(T);
       }
     // dense inverse by rows in 16-byte chunks (zero outside the triangle)
     constexpr int V = 16 / (int)sizeof(T);
@@ -380,16 +373,12 @@ static std::string pack_records(const BlockTri& B, bool upper, std::vector<char>
         dst[j - j0] = (T)vv;
       }
     }
-    off.push_back((long long)packed.size());
-    packed.insert(packed.end(), rec.begin(), rec.end());
     max_bytes = std::max(max_bytes, lay.bytes);
+    recs.push_back(std::move(rec));
   }
-  off.push_back((long long)packed.size());
-  // every record padded to the same size (a multiple of 128 bytes)
   rec_bytes = (max_bytes + 127) & ~127;
   out.assign((size_t)rec_bytes * n, 0);
-  for (int k = 0; k < n; ++k)
-    std::copy(packed.begin() + off[k], packed.begin() + off[k + 1], out.begin() + (size_t)k * rec_bytes);
+  for (int k = 0; k < n; ++k) std::copy(recs[k].begin(), recs[k].end(), out.begin() + (size_t)k * rec_bytes);
   return "";
 }
 
@@ -505,12 +494,14 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   // ILUT records in the smoothing precision
   std::vector<char> recL, recU;
   int maxL = 0, maxU = 0;
+  d.rec_lanes = (8 * n <= kBlock) ? 8 : 4;
+  if (4 * n > kBlock) return fail(IGM_ERR_ARG, "grid rows longer than kBlock/4 unknowns");
   if (o.precision == 0) {
-    e = pack_records<double>(BL, false, recL, maxL);
-    if (e.empty()) e = pack_records<double>(BU, true, recU, maxU);
+    e = pack_records<double>(BL, false, d.rec_lanes, recL, maxL);
+    if (e.empty()) e = pack_records<double>(BU, true, d.rec_lanes, recU, maxU);
   } else {
-    e = pack_records<float>(BL, false, recL, maxL);
-    if (e.empty()) e = pack_records<float>(BU, true, recU, maxU);
+    e = pack_records<float>(BL, false, d.rec_lanes, recL, maxL);
+    if (e.empty()) e = pack_records<float>(BU, true, d.rec_lanes, recU, maxU);
   }
   if (!e.empty()) return fail(IGM_ERR_ARG, e);
   d.Lrec.recs = up.put(recL); d.Lrec.bytes = maxL;

@@ -13,7 +13,8 @@
 
 namespace igm {
 
-constexpr int kBlock = 512;       // threads per CTA of the solve kernels
+constexpr int kBlock = 544;       // threads per CTA of the solve kernels (17 warps:
+                                  // 8 lanes for each of up to 68 rows of a grid row)
 constexpr int kGroup = 4;         // lanes cooperating on one matrix row
 constexpr int kMaxH = 8;          // max h-multigrid levels at p = 1
 constexpr int kMaxStage = 4;      // max depth of the record ring
@@ -57,6 +58,7 @@ struct PmgD {
   const float* sA32;
   // ILUT factors as block-row records in the smoothing precision
   RecSet Lrec, Urec;
+  int rec_lanes;               // lanes per row G of the factor records (4 or 8)
   int nstage, slot_bytes;      // record ring: nstage slots of slot_bytes
   // L2 transfers between order p and order 1 (Sec. 4, Eq. (prolongation))
   int N1, n1, wP, tp;          // tp: tensor-product transfers with 1D bands of width wP
@@ -204,6 +206,26 @@ __device__ __forceinline__ void for_group_rows(int nrows, F&& f) {
     const int r = r0 + (int)threadIdx.x / kGroup;
     f(r, r < nrows, gl);
   }
+}
+
+// As for_group_rows with G lanes per row (G a power of two <= 32).
+template <int G, typename F>
+__device__ __forceinline__ void for_rows_g(int nrows, F&& f) {
+  const int gl = threadIdx.x % G;
+  const int per = blockDim.x / G;
+  const int wrow = (int)(threadIdx.x & ~31u) / G;
+  for (int r0 = 0; r0 < nrows; r0 += per) {
+    if (r0 + wrow >= nrows) break;
+    const int r = r0 + (int)threadIdx.x / G;
+    f(r, r < nrows, gl);
+  }
+}
+
+template <int G, typename T>
+__device__ __forceinline__ T group_sum_g(T s) {
+#pragma unroll
+  for (int o = 1; o < G; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -366,41 +388,38 @@ __device__ __forceinline__ size_t upper_off(int i, int n) {
 
 __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
-// Row stride of the padded record arrays: the smallest value >= n that is
-// 8 mod 32, so that the 4 lane classes of a warp (8 rows x 4 classes) hit 4
-// disjoint 8-bank ranges.
-__host__ __device__ __forceinline__ int rec_pad(int n) { return n + ((8 - n) % 32 + 32) % 32; }
+// One off-block entry of a factor record: the value and the byte offset of
+// the coupled unknown in the vector being solved.
+template <typename T>
+struct alignas(sizeof(T) == 4 ? 8 : 16) RecEntry {
+  T val;
+  int off;
+};
 
 // Byte offsets inside a factor record (must match the host packing in
-// capi.cu).  Record of grid row `by`: int header[4] = {base, K, by, npad};
-// uint16 col[K][npad] and T val[K][npad]: the off-block entries of the grid
-// row's n rows in ELL form, slot-major (entry k of row r at k*npad + r,
-// column base + col; padding has val 0, col 0); then the dense inverse of
-// the diagonal block stored by rows in 16-byte chunks of V = 16/sizeof(T)
-// columns: row r covers the chunks of columns [0, r] (lower) or
-// [r - r % V, n) (upper), zero-padded, at chunk offset rec_inv_row(r).
+// capi.cu).  Record of grid row `by` for G lanes per row: int header[4] =
+// {KL, by, G, 0}; RecEntry ent[KL][n][G]: the off-block entries of the grid
+// row's n rows, entry k of row r at ((k / G) * n + r) * G + k % G, KL =
+// ceil(max entries per row / G), padding entries (0, 0); then the dense
+// inverse of the diagonal block stored by rows in 16-byte chunks of
+// V = 16/sizeof(T) columns: row r covers the chunks of columns [0, r]
+// (lower) or [r - r % V, n) (upper), zero-padded, at chunk offset
+// rec_inv_row(r).  Every part 16-byte aligned.
 template <typename T>
 struct RecLayout {
-  int npad, o_col, o_val, o_inv, bytes;
-  __host__ __device__ RecLayout(int n, int K, bool upper) {
-    npad = rec_pad(n);
-    o_col = 16;
-    o_val = o_col + ((2 * K * npad + 15) & ~15);
-    o_inv = o_val + (((int)sizeof(T) * K * npad + 15) & ~15);
+  int o_ent, o_inv, bytes;
+  __host__ __device__ RecLayout(int n, int KL, int G, bool upper) {
+    o_ent = 16;
+    o_inv = o_ent + (((int)sizeof(RecEntry<T>) * KL * n * G + 15) & ~15);
     bytes = o_inv + 16 * rec_inv_row(n, n, upper);
   }
   // chunk offset of row r (r = n gives the total number of chunks)
   __host__ __device__ static int rec_inv_row(int r, int n, bool upper) {
     constexpr int V = 16 / (int)sizeof(T);
     const int nc = (n + V - 1) / V;  // chunks in a full row
-    if (!upper) {
-      // row i has floor(i/V) + 1 chunks
-      int q = r / V, rem = r % V;
-      return V * q * (q + 1) / 2 + rem * (q + 1);
-    }
-    // row i has nc - floor(i/V) chunks
-    int q = r / V, rem = r % V;
-    return V * (q * nc - q * (q - 1) / 2) + rem * (nc - q);
+    const int q = r / V, rem = r % V;
+    if (!upper) return V * q * (q + 1) / 2 + rem * (q + 1);   // row i: floor(i/V)+1 chunks
+    return V * (q * nc - q * (q - 1) / 2) + rem * (nc - q);   // row i: nc-floor(i/V) chunks
   }
 };
 
@@ -418,7 +437,7 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int
 // entries in parallel (kGroup lanes per row); phase 2 writes
 // v_row = inv(D_row) t (packed dense, lower for L, upper for U).  Record k+S
 // is in flight while record k is used.  Returns false after a wait timeout.
-template <typename T, bool UPPER>
+template <typename T, bool UPPER, int G>
 __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int* status,
                             unsigned long long* trace = nullptr) {
   if (pp.dead) return false;
@@ -449,75 +468,76 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
     }
     const char* rec = pp.ring + (size_t)s * pp.slot;
     const int* hdr = (const int*)rec;
-    const int base = hdr[0], K = hdr[1], by = hdr[2];
-    const RecLayout<T> lay(n, K, UPPER);
-    const int np = lay.npad;
-    const uint16_t* col = (const uint16_t*)(rec + lay.o_col);
-    const T* val = (const T*)(rec + lay.o_val);
+    const int KL = hdr[0], by = hdr[1];
+    const RecLayout<T> lay(n, KL, G, UPPER);
+    const RecEntry<T>* ent = (const RecEntry<T>*)(rec + lay.o_ent);
     const char* inv = rec + lay.o_inv;
+    const char* vbytes = (const char*)v;
     PhaseClock p1(trace);
-    // phase 1: t_r = v_i - sum_k val[k][r] v[base + col[k][r]]; a warp covers
-    // 8 rows x 4 slot classes (k = c, c+4, ...), reduced by two shuffles
-    for_group_rows(n, [&](int r, bool act, int c) {
+    // phase 1: t_r = v_i - sum over the row's off-block entries of val * v[off];
+    // a warp covers 32/G rows x G lanes and reads 32 consecutive entries per
+    // step; KL is the same for every lane (padding entries are (0, 0))
+    for_rows_g<G>(n, [&](int r, bool act, int c) {
+      const RecEntry<T>* ep = ent + (size_t)(act ? r : 0) * G + c;
+      const int stride = n * G;
       T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      if (act) {
-        int kk = c;
-        // 4 independent chains keep 4 gathers in flight
-        // indices were validated on the host (base + col < n*n)
-        const uint16_t* cp = col + r;
-        const T* vp = val + r;
-        const T* vb = v + base;
-        for (; kk + 3 * kGroup < K; kk += 4 * kGroup) {
-          const int i0 = cp[(kk + 0 * kGroup) * np], i1 = cp[(kk + 1 * kGroup) * np];
-          const int i2 = cp[(kk + 2 * kGroup) * np], i3 = cp[(kk + 3 * kGroup) * np];
-          s0 += vp[(kk + 0 * kGroup) * np] * vb[i0];
-          s1 += vp[(kk + 1 * kGroup) * np] * vb[i1];
-          s2 += vp[(kk + 2 * kGroup) * np] * vb[i2];
-          s3 += vp[(kk + 3 * kGroup) * np] * vb[i3];
-        }
-        for (; kk < K; kk += kGroup) s0 += vp[kk * np] * vb[cp[kk * np]];
+      int u = 0;
+      for (; u + 4 <= KL; u += 4) {
+        const RecEntry<T> e0 = ep[(u + 0) * stride], e1 = ep[(u + 1) * stride];
+        const RecEntry<T> e2 = ep[(u + 2) * stride], e3 = ep[(u + 3) * stride];
+        s0 += e0.val * *(const T*)(vbytes + e0.off);
+        s1 += e1.val * *(const T*)(vbytes + e1.off);
+        s2 += e2.val * *(const T*)(vbytes + e2.off);
+        s3 += e3.val * *(const T*)(vbytes + e3.off);
       }
-      T sacc = group_sum((s0 + s1) + (s2 + s3));
+      for (; u < KL; ++u) {
+        const RecEntry<T> e0 = ep[u * stride];
+        s0 += e0.val * *(const T*)(vbytes + e0.off);
+      }
+      const T sacc = group_sum_g<G>((s0 + s1) + (s2 + s3));
       if (act && c == 0) row[r] = v[by * n + r] - sacc;
     });
     __syncthreads();
     p1.stop(9);
     PhaseClock p2(trace);
-    // phase 2: v_row = inv(D) t.  Lane class c of row r takes the 16-byte
-    // chunks c, c+4, ... of the row's stored column range: one vector load of
-    // the inverse and one (broadcast) of t per V columns.
-    for_group_rows(n, [&](int r, bool act, int c) {
+    // phase 2: v_row = inv(D) t.  Lane c of row r takes the 16-byte chunks
+    // c, c+G, ... of the row's stored column range (one vector load of the
+    // inverse and one broadcast load of t per V columns); the trip count is
+    // the warp's maximum, out-of-range chunks are skipped by a predicate
+    for_rows_g<G>(n, [&](int r, bool act, int c) {
       constexpr int V = 16 / (int)sizeof(T);
       using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-      T s0 = 0, s1 = 0;
       const int rr = act ? r : 0;
       const int j0 = UPPER ? rr - rr % V : 0;
       const int nch = UPPER ? (n - j0 + V - 1) / V : rr / V + 1;
-      // warp-uniform trip count: the most chunks any of the warp's 8 rows has
-      const int rw = r & ~7;
-      const int nch_w = UPPER ? (n - (rw - rw % V) + V - 1) / V
-                              : ((rw + 7 < n ? rw + 7 : n - 1) / V + 1);
+      constexpr int RW = 32 / G;  // rows per warp
+      const int rw = r & ~(RW - 1);
+      const int rl = rw + RW - 1 < n ? rw + RW - 1 : n - 1;
+      const int nch_w = UPPER ? (n - (rw - rw % V) + V - 1) / V : rl / V + 1;
       const Vec* ip = (const Vec*)(inv + 16 * RecLayout<T>::rec_inv_row(rr, n, UPPER));
       const Vec* tp = (const Vec*)(row + j0);
-      const int steps = (nch_w + kGroup - 1) / kGroup;
+      T s0 = 0, s1 = 0;
+      const int steps = (nch_w + G - 1) / G;
       for (int st = 0; st < steps; ++st) {
-        const int q = c + st * kGroup;
-        if (act && q < nch) {
-          const Vec a = ip[q], t = tp[q];
-          if (sizeof(T) == 4) {
-            const float4& af = reinterpret_cast<const float4&>(a);
-            const float4& tf = reinterpret_cast<const float4&>(t);
-            s0 += af.x * tf.x + af.y * tf.y;
-            s1 += af.z * tf.z + af.w * tf.w;
-          } else {
-            const double2& ad = reinterpret_cast<const double2&>(a);
-            const double2& td = reinterpret_cast<const double2&>(t);
-            s0 += ad.x * td.x;
-            s1 += ad.y * td.y;
-          }
+        const int q = c + st * G;
+        const bool ok = act && q < nch;
+        const int qq = ok ? q : 0;
+        const Vec a = ip[qq], t = tp[qq];
+        if (sizeof(T) == 4) {
+          const float4& af = reinterpret_cast<const float4&>(a);
+          const float4& tf = reinterpret_cast<const float4&>(t);
+          const T w = ok ? (T)1 : (T)0;
+          s0 += w * (af.x * tf.x + af.y * tf.y);
+          s1 += w * (af.z * tf.z + af.w * tf.w);
+        } else {
+          const double2& ad = reinterpret_cast<const double2&>(a);
+          const double2& td = reinterpret_cast<const double2&>(t);
+          const T w = ok ? (T)1 : (T)0;
+          s0 += w * (ad.x * td.x);
+          s1 += w * (ad.y * td.y);
         }
       }
-      const T sacc = group_sum(s0 + s1);
+      const T sacc = group_sum_g<G>(s0 + s1);
       if (act && c == 0) v[by * n + r] = sacc;
     });
     __syncthreads();

@@ -65,8 +65,13 @@ template <> struct Prec<double> {
 template <typename T>
 __device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, T* row, int* status) {
   PhaseClock pc(P.trace);
-  bool ok = block_sweep<T, false>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
-            block_sweep<T, true>(P.n, P.Urec, pp, v, row, status, P.trace);
+  bool ok;
+  if (P.rec_lanes == 8)
+    ok = block_sweep<T, false, 8>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
+         block_sweep<T, true, 8>(P.n, P.Urec, pp, v, row, status, P.trace);
+  else
+    ok = block_sweep<T, false, 4>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
+         block_sweep<T, true, 4>(P.n, P.Urec, pp, v, row, status, P.trace);
   pc.stop(2);
   return ok;
 }
