@@ -13,8 +13,7 @@
 
 namespace igm {
 
-constexpr int kBlock = 544;       // threads per CTA of the solve kernels (17 warps:
-                                  // 8 lanes for each of up to 68 rows of a grid row)
+constexpr int kBlock = 512;       // threads per CTA of the solve kernels
 constexpr int kGroup = 4;         // lanes cooperating on one matrix row
 constexpr int kMaxH = 8;          // max h-multigrid levels at p = 1
 constexpr int kMaxStage = 4;      // max depth of the record ring
