@@ -251,6 +251,13 @@ igm_status mgrit_solve(const iga_ops* ops, const mgrit_opts* opts, const double*
 igm_status mgrit_profile(const mgrit_handle* mg, int cap, int* count, int* level, int* grid,
                          int* mode, float* ms, long* cycles);
 
+/* Failure-detection self-test: launches one kernel whose bounded mbarrier
+ * wait (the same wait the solver uses for its streamed factor records) has
+ * nothing to wait for; after `spins` polls the kernel records the timeout and
+ * returns, and the call returns IGM_ERR_TIMEOUT with the device still usable.
+ * Returns IGM_OK only if the wait completed, which would be a fault. */
+igm_status igm_wait_selftest(long spins, igm_stream s);
+
 /* Thread-local text of the last error (empty string if none). */
 const char* igm_last_error(void);
 

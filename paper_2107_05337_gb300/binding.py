@@ -76,6 +76,7 @@ EXPORTS = {
                             c_void_p, POINTER(MgritStats), c_void_p]),
     "mgrit_profile": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int), POINTER(ctypes.c_float), POINTER(c_long)]),
+    "igm_wait_selftest": (c_int, [c_long, c_void_p]),
     "igm_last_error": (ctypes.c_char_p, []),
     "igm_kernel_launches": (c_long, []),
 }
@@ -358,6 +359,11 @@ def mgrit_solve(problem, u0, fhat=None, fcoef=None, U=None, check=True, **opts):
     if check:
         _check(status)
     return U, _stats(st), status
+
+
+def wait_selftest(spins=1 << 16):
+    """Status of igm_wait_selftest (IGM_ERR_TIMEOUT = -5 when the bound works)."""
+    return lib().igm_wait_selftest(spins, _stream())
 
 
 def kernel_launches():

@@ -494,8 +494,8 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   // ILUT records in the smoothing precision
   std::vector<char> recL, recU;
   int maxL = 0, maxU = 0;
-  d.rec_lanes = (8 * n <= kBlock) ? 8 : 4;
-  if (4 * n > kBlock) return fail(IGM_ERR_ARG, "grid rows longer than kBlock/4 unknowns");
+  d.rec_lanes = (8 * n <= kBlock) ? 8 : (4 * n <= kBlock ? 4 : 2);
+  if (2 * n > kBlock) return fail(IGM_ERR_ARG, "grid rows longer than 256 unknowns are not supported");
   if (o.precision == 0) {
     e = pack_records<double>(BL, false, d.rec_lanes, recL, maxL);
     if (e.empty()) e = pack_records<double>(BU, true, d.rec_lanes, recU, maxU);
@@ -745,6 +745,22 @@ extern "C" igm_status pmg_ilut_apply(pmg_handle* h, int nrhs, const double* r, d
   CU(launch_ilut_apply(h->d.precision, h->d, nrhs, smem_of(h), (cudaStream_t)s, r, z, ld,
                        h->garena, nullptr));
   g_launches++;
+  return IGM_OK;
+}
+
+extern "C" igm_status igm_wait_selftest(long spins, igm_stream s) {
+  if (spins < 1) return fail(IGM_ERR_ARG, "spins must be >= 1");
+  int* dstat = nullptr;
+  cudaStream_t st = (cudaStream_t)s;
+  CU(cudaMallocAsync(&dstat, sizeof(int), st));
+  CU(cudaMemsetAsync(dstat, 0, sizeof(int), st));
+  CU(launch_wait_selftest(spins, dstat, st));
+  g_launches++;
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaFreeAsync(dstat, st));
+  CU(cudaStreamSynchronize(st));
+  if (h == ST_TIMEOUT) return fail(IGM_ERR_TIMEOUT, "bounded mbarrier wait gave up as intended");
   return IGM_OK;
 }
 

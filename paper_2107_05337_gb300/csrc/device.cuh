@@ -119,10 +119,10 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
       : "=r"(ok) : "r"(smem_u32(b)), "r"(parity) : "memory");
   return ok != 0;
 }
-// Bounded wait: false after kSpinLimit unsuccessful polls (the caller then
+// Bounded wait: false after `limit` unsuccessful polls (the caller then
 // records IGM_ERR_TIMEOUT and abandons the solve instead of hanging).
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  for (long k = 0; k < kSpinLimit; ++k)
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long limit = kSpinLimit) {
+  for (long k = 0; k < limit; ++k)
     if (mbar_try_wait(b, parity)) return true;
   return false;
 }

@@ -41,6 +41,9 @@ cudaError_t launch_ilut_apply(int prec, const PmgD& P, int grid, long smem, cuda
 cudaError_t launch_mgrit_sweep(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st);
 cudaError_t launch_apply_op(const PmgD& P, int which, int nrhs, const double* x, double* y, long ld,
                             double* scratch, cudaStream_t st);
+// One CTA waits (bounded by `spins` polls) on an mbarrier that no copy or
+// arrival will ever complete, and records ST_TIMEOUT in *status.
+cudaError_t launch_wait_selftest(long spins, int* status, cudaStream_t st);
 // Allow up to `bytes` of dynamic shared memory for the solve kernels.
 cudaError_t set_solver_smem(long bytes);
 

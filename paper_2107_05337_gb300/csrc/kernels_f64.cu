@@ -54,6 +54,24 @@ __global__ void __launch_bounds__(kBlock) k_apply_op(PmgD P, int which, const do
   }
 }
 
+// Failure-detection self-test: the same bounded wait the record ring uses, on
+// a barrier that nothing completes; the kernel then returns normally.
+__global__ void k_wait_selftest(long spins, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const bool got = mbar_wait(&bar, 0u, spins);
+  if (!got && threadIdx.x == 0) atomicMin(status, ST_TIMEOUT);
+}
+
+cudaError_t launch_wait_selftest(long spins, int* status, cudaStream_t st) {
+  k_wait_selftest<<<1, 32, 0, st>>>(spins, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_apply_op(const PmgD& P, int which, int nrhs, const double* x, double* y, long ld,
                             double* scratch, cudaStream_t st) {
   k_apply_op<<<nrhs, kBlock, 0, st>>>(P, which, x, y, ld, scratch);

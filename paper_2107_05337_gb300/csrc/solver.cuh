@@ -69,9 +69,12 @@ __device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, T* row, int* status) {
   if (P.rec_lanes == 8)
     ok = block_sweep<T, false, 8>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
          block_sweep<T, true, 8>(P.n, P.Urec, pp, v, row, status, P.trace);
-  else
+  else if (P.rec_lanes == 4)
     ok = block_sweep<T, false, 4>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
          block_sweep<T, true, 4>(P.n, P.Urec, pp, v, row, status, P.trace);
+  else
+    ok = block_sweep<T, false, 2>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
+         block_sweep<T, true, 2>(P.n, P.Urec, pp, v, row, status, P.trace);
   pc.stop(2);
   return ok;
 }
