@@ -172,7 +172,7 @@ typedef enum {
   IGM_PH_ILUT_WAIT = 8,   /* ILUT: waits for streamed factor records */
   IGM_PH_ILUT_OFF = 9,    /* ILUT: off-block products of a grid row */
   IGM_PH_ILUT_DIAG = 10,  /* ILUT: dense diagonal-block products */
-  IGM_PH_GS_WAIT = 11,    /* Gauss--Seidel: waits for streamed coefficient rows */
+  IGM_PH_GS_WAIT = 11,    /* reserved (Gauss--Seidel rows are staged by cp.async) */
   IGM_PH_GS_ROW = 12,     /* Gauss--Seidel: couplings to neighbouring rows */
   IGM_PH_GS_SCAN = 13,    /* Gauss--Seidel: in-row recurrence (warp scan) and stores */
   IGM_PH_COUNT = 14

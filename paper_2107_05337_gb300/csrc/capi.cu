@@ -561,7 +561,9 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     d.h[k].G.bytes = rec_bytes;
     gs_max = std::max(gs_max, rec_bytes);
   }
-  d.slot_bytes = (std::max(d.slot_bytes, gs_max) + 127) & ~127;
+  // Gauss--Seidel rows are staged 4 at a time in the ring (see gs_rows_warp)
+  d.slot_bytes = (d.slot_bytes + 127) & ~127;
+  const int gs_stage = 4 * gs_max;
   d.Cinv = up.put(Cinv);
   std::vector<int> wops;
   gen_wcycle(0, d.nh - 1, wops);
@@ -607,9 +609,12 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.arena_smem = 0;
   d.nstage = 0;
   for (int st = kMaxStage; st >= 2 && !d.nstage; --st)
-    if (ring_of(st) + h->arena_bytes <= optin) { d.nstage = st; d.arena_smem = 1; }
+    if (ring_of(st) + h->arena_bytes <= optin && (long)st * d.slot_bytes >= gs_stage) {
+      d.nstage = st;
+      d.arena_smem = 1;
+    }
   for (int st = kMaxStage; st >= 1 && !d.nstage; --st)
-    if (ring_of(st) <= optin) d.nstage = st;
+    if (ring_of(st) <= optin && (long)st * d.slot_bytes >= gs_stage) d.nstage = st;
   if (!d.nstage) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
   d.ring_bytes = ring_of(d.nstage);
   h->arena_smem = d.arena_smem != 0;

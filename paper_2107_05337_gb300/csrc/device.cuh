@@ -549,42 +549,46 @@ __device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int*
   return true;
 }
 
-// One forward lexicographic Gauss--Seidel sweep on a 9-point operator.  Warp 0
-// does the work; each grid row's coefficients arrive in the record ring ahead
-// of use.  Grid row by: every lane forms t_r = b_r - (E, S-row, N-row
-// couplings) x for its E consecutive unknowns; the in-row recurrence
+// Warp-level asynchronous copies (cp.async, 16 bytes per lane per instruction)
+// with group accounting: used to stage Gauss--Seidel coefficient rows.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// One forward lexicographic Gauss--Seidel sweep on a 9-point operator, run by
+// warp 0 (the caller synchronises the CTA afterwards).  The coefficient row of
+// grid row by+D is copied into a 4-slot staging area while row by is solved.
+// Grid row by: every lane forms t_r = b_r - (E, S-row, N-row couplings) x
+// for its E consecutive unknowns; the in-row recurrence
 // x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha = -a_W/a_C) is an affine map per
-// unknown, composed by a warp-wide scan.  All threads keep the ring's phase
-// bits in step; returns false (CTA-uniformly) after a wait timed out.
+// unknown, composed by a warp-wide scan.
 template <typename T, int EMAX>
-__device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status,
+__device__ void gs_rows_warp(int n, const RecSet& R, char* stage, const T* b, T* x,
                              unsigned long long* trace) {
+  constexpr int D = 3;            // rows in flight ahead of the one being solved
+  constexpr int E = EMAX;         // unknowns per lane (the host packs rows for this width)
   const int lane = threadIdx.x & 31;
-  constexpr int E = EMAX;  // unknowns per lane (the host packs rows for this width)
   const int r0 = lane * E;
-  const int S = pp.nstage < n ? pp.nstage : n;
-  if (threadIdx.x == 0)
-    for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
+  const int chunks = R.bytes / 16;
+  auto copy_row = [&](int row) {
+    const char* src = R.recs + (size_t)row * R.bytes;
+    char* dst = stage + (size_t)(row % (D + 1)) * R.bytes;
+    for (int i = lane; i < chunks; i += 32) cp_async16(dst + 16 * i, src + 16 * i);
+  };
+  for (int k = 0; k < D; ++k) {
+    if (k < n) copy_row(k);
+    cp_async_commit();
+  }
   for (int by = 0; by < n; ++by) {
-    const int s = by % pp.nstage;
-    PhaseClock pw(trace);
-    if (!mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u)) {
-      if (status && lane == 0) atomicMin(status, ST_TIMEOUT);
-      pp.dead = true;
-    }
-    pp.phase ^= 1u << s;
-    if (__any_sync(0xffffffffu, pp.dead)) {
-      pp.dead = true;
-      for (int j = by + 1; j < by + S && j < n; ++j) {
-        const int sj = j % pp.nstage;
-        mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
-        pp.phase ^= 1u << sj;
-      }
-      return;
-    }
-    pw.stop(11);
+    if (by + D < n) copy_row(by + D);
+    cp_async_commit();
+    cp_async_wait<D>();           // the group of row `by` has landed
+    __syncwarp();
     PhaseClock pt(trace);
-    const T* cf = (const T*)(pp.ring + (size_t)s * pp.slot);
+    const T* cf = (const T*)(stage + (size_t)(by % (D + 1)) * R.bytes);
     T beta[EMAX], alpha[EMAX];
     T A = 1, B = 0;
 #pragma unroll
@@ -640,29 +644,22 @@ __device__ void gs_rows_warp(int n, const RecSet& R, Pipe& pp, const T* b, T* x,
     }
     __syncwarp();
     ps.stop(13);
-    if (threadIdx.x == 0 && by + pp.nstage < n) {
-      fence_proxy_async();
-      pipe_issue(pp, R, by + pp.nstage, s);
-    }
   }
+  cp_async_wait<0>();
 }
 
+// A Gauss--Seidel sweep staged through the (idle) record ring.
 template <typename T>
 __device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status,
                          unsigned long long* trace = nullptr) {
   if (pp.dead) return false;
   if (threadIdx.x < 32) {
-    if (n <= 32) gs_rows_warp<T, 1>(n, R, pp, b, x, status, trace);
-    else if (n <= 64) gs_rows_warp<T, 2>(n, R, pp, b, x, status, trace);
-    else gs_rows_warp<T, 4>(n, R, pp, b, x, status, trace);
-  } else {
-    // keep this thread's copy of the ring parities in step with warp 0
-    for (int by = 0; by < n; ++by) pp.phase ^= 1u << (by % pp.nstage);
+    if (n <= 32) gs_rows_warp<T, 1>(n, R, pp.ring, b, x, trace);
+    else if (n <= 64) gs_rows_warp<T, 2>(n, R, pp.ring, b, x, trace);
+    else gs_rows_warp<T, 4>(n, R, pp.ring, b, x, trace);
   }
-  // warp 0's phase bits and dead flag are the CTA's
-  const bool dead = __syncthreads_or(pp.dead);
-  pp.dead = dead;
-  return !dead;
+  __syncthreads();
+  return true;
 }
 
 // Tensor-product transfer on the affine map, stage along xi then eta:
