@@ -169,9 +169,11 @@ typedef enum {
   IGM_PH_PROLONG = 5,     /* prolongation 1 -> p (Sec. 4, step 4) */
   IGM_PH_RHS = 6,         /* MGRIT step right-hand side M u + dt f */
   IGM_PH_GS = 7,          /* Gauss--Seidel sweeps inside the W-cycle */
-  IGM_PH_ILUT_WAIT = 8,   /* ILUT: waits for streamed factor records */
-  IGM_PH_ILUT_OFF = 9,    /* ILUT: off-block products of a grid row */
-  IGM_PH_ILUT_DIAG = 10,  /* ILUT: dense diagonal-block products */
+  IGM_PH_ILUT_WAIT = 8,   /* ILUT, first sweep team: waits for its records and for the
+                             preceding grid rows */
+  IGM_PH_ILUT_OFF = 9,    /* ILUT, first sweep team: off-block couplings of its grid rows */
+  IGM_PH_ILUT_DIAG = 10,  /* ILUT, first sweep team: diagonal-block products and row
+                             completion */
   IGM_PH_GS_WAIT = 11,    /* reserved (Gauss--Seidel rows are staged by cp.async) */
   IGM_PH_GS_ROW = 12,     /* Gauss--Seidel: couplings to neighbouring rows */
   IGM_PH_GS_SCAN = 13,    /* Gauss--Seidel: in-row recurrence (warp scan) and stores */

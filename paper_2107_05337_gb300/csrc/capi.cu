@@ -327,12 +327,12 @@ static void gen_wcycle(int k, int last, std::vector<int>& ops) {
 
 static int align4(int x) { return (x + 3) & ~3; }
 
-// Pack the block-row records of one triangular factor for G lanes per row
-// (layout: RecLayout in device.cuh).  Record k covers grid row k (lower) or
+// Pack the block-row records of one triangular factor for the wavefront
+// sweep (layout: RecLayout in device.cuh).  Record k covers grid row k (lower) or
 // n-1-k (upper); every record is padded to the same size (a multiple of 128
 // bytes) so that record k starts at k * rec_bytes.
 template <typename T>
-static std::string pack_records(const BlockTri& B, bool upper, int G, std::vector<char>& out,
+static std::string pack_records(const BlockTri& B, bool upper, int team, std::vector<char>& out,
                                 int& rec_bytes) {
   const int n = B.n;
   const int N = n * n;
@@ -341,38 +341,79 @@ static std::string pack_records(const BlockTri& B, bool upper, int G, std::vecto
   int max_bytes = 0;
   for (int k = 0; k < n; ++k) {
     const int by = upper ? n - 1 - k : k;
+    const int nb = upper ? by + 1 : by - 1;  // grid row one step back in the sweep
     const int* rp = &B.off.ptr[(size_t)by * n];
-    int K = 0;
-    for (int r = 0; r < n; ++r) K = std::max(K, rp[r + 1] - rp[r]);
-    const int KL = (K + G - 1) / G;
-    const RecLayout<T> lay(n, KL, G, upper);
-    std::vector<char> rec(lay.bytes, 0);
-    int* hdr = (int*)rec.data();
-    hdr[0] = KL; hdr[1] = by; hdr[2] = G; hdr[3] = 0;
-    RecEntry<T>* ent = (RecEntry<T>*)(rec.data() + lay.o_ent);
-    for (int r = 0; r < n; ++r)
+    int KF = 0, KN = 0;
+    for (int r = 0; r < n; ++r) {
+      int f = 0, m = 0;
       for (int e = rp[r]; e < rp[r + 1]; ++e) {
-        const int slot = e - rp[r];
         const int col = B.off.col[e];
         if (col < 0 || col >= N) return "factor column out of range";
-        RecEntry<T>& x = ent[((size_t)(slot / G) * n + r) * G + slot % G];
-        x.val = (T)B.off.val[e];
-        x.off = col * (int)sizeof(T);
+        const int g = col / n;
+        if (upper ? g <= by : g >= by) return "factor entry not behind its grid row in the sweep";
+        (g == nb ? m : f) += 1;
       }
-    // dense inverse by rows in 16-byte chunks (zero outside the triangle)
-    constexpr int V = 16 / (int)sizeof(T);
-    const double* src = &B.inv[(size_t)by * blk];
+      KF = std::max(KF, f);
+      KN = std::max(KN, m);
+    }
+    const RecLayout<T> lay(n, KF, KN, upper, team);
+    if (lay.o_inv % 16 || lay.o_desc % 16) return "factor record parts not 16-byte aligned";
+    std::vector<char> rec(lay.bytes, 0);
+    int* hdr = (int*)rec.data();
+    hdr[0] = KF; hdr[1] = KN; hdr[2] = by; hdr[3] = 0;
+    T* fv = (T*)(rec.data() + lay.o_fv);
+    uint16_t* fi = (uint16_t*)(rec.data() + lay.o_fi);
+    T* nv = (T*)(rec.data() + lay.o_nv);
+    uint16_t* ni = (uint16_t*)(rec.data() + lay.o_ni);
     for (int r = 0; r < n; ++r) {
-      T* dst = (T*)(rec.data() + lay.o_inv + 16 * (size_t)RecLayout<T>::rec_inv_row(r, n, upper));
-      const int j0 = upper ? r - r % V : 0;
-      const int jend = upper ? ((n + V - 1) / V) * V : (r / V + 1) * V;
-      for (int j = j0; j < jend; ++j) {
-        double vv = 0.0;
-        if (!upper && j <= r) vv = src[(size_t)r * (r + 1) / 2 + j];
-        if (upper && j >= r && j < n) vv = src[(size_t)r * n - (size_t)r * (r - 1) / 2 + (j - r)];
-        dst[j - j0] = (T)vv;
+      int f = 0, m = 0;
+      for (int e = rp[r]; e < rp[r + 1]; ++e) {
+        const int col = B.off.col[e];
+        if (col > 0xffff) return "factor column beyond 16-bit indices";
+        const size_t pos = (size_t)((col / n == nb) ? m++ : f++) * n + r;
+        (col / n == nb ? nv : fv)[pos] = (T)B.off.val[e];
+        (col / n == nb ? ni : fi)[pos] = (uint16_t)col;
       }
     }
+    // dense inverse in 16-byte chunks (zero outside the triangle): the flat
+    // row-major chunk list, then stored lane-step-major with descriptors
+    constexpr int V = 16 / (int)sizeof(T);
+    const double* src = &B.inv[(size_t)by * blk];
+    const int total = RecLayout<T>::rec_inv_row(n, n, upper);
+    const int S = RecLayout<T>::wave_steps(n, upper, team);
+    std::vector<T> flat((size_t)total * V, (T)0);
+    std::vector<int> crow(total), cq(total);
+    for (int r = 0; r < n; ++r) {
+      const int c0 = RecLayout<T>::rec_inv_row(r, n, upper);
+      const int c1 = RecLayout<T>::rec_inv_row(r + 1, n, upper);
+      const int j0 = upper ? r - r % V : 0;
+      for (int c = c0; c < c1; ++c) {
+        crow[c] = r;
+        cq[c] = c - c0;
+        for (int u = 0; u < V; ++u) {
+          const int j = j0 + (c - c0) * V + u;
+          double vv = 0.0;
+          if (!upper && j <= r) vv = src[(size_t)r * (r + 1) / 2 + j];
+          if (upper && j >= r && j < n) vv = src[(size_t)r * n - (size_t)r * (r - 1) / 2 + (j - r)];
+          flat[(size_t)c * V + u] = (T)vv;
+        }
+      }
+    }
+    T* inv = (T*)(rec.data() + lay.o_inv);
+    int* desc = (int*)(rec.data() + lay.o_desc);
+    for (int l = 0; l < team; ++l)
+      for (int st = 0; st < S; ++st) {
+        const int c = l * S + st;
+        if (c >= total) continue;
+        const int r = crow[c];
+        const int tq = (upper ? r / V : 0) + cq[c];
+        const int end = std::min((l + 1) * S, total);
+        const bool flush = c + 1 == end || c + 1 == RecLayout<T>::rec_inv_row(r + 1, n, upper);
+        if (tq > 0xff || r + l > 0x3ff) return "diagonal block too large for the sweep schedule";
+        const size_t pos = (size_t)st * team + l;
+        std::copy(&flat[(size_t)c * V], &flat[(size_t)c * V] + V, inv + pos * V);
+        desc[pos] = tq | ((r + l) << 8) | (flush ? (int)0x80000000u : 0);
+      }
     max_bytes = std::max(max_bytes, lay.bytes);
     recs.push_back(std::move(rec));
   }
@@ -491,22 +532,24 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.sA64 = up.put(A.val);
   d.sA32 = up.put32(A.val);
   d.sM64 = ops->sM64;
-  // ILUT records in the smoothing precision
-  std::vector<char> recL, recU;
-  int maxL = 0, maxU = 0;
-  d.rec_lanes = (8 * n <= kBlock) ? 8 : (4 * n <= kBlock ? 4 : 2);
-  if (2 * n > kBlock) return fail(IGM_ERR_ARG, "grid rows longer than 256 unknowns are not supported");
-  if (o.precision == 0) {
-    e = pack_records<double>(BL, false, d.rec_lanes, recL, maxL);
-    if (e.empty()) e = pack_records<double>(BU, true, d.rec_lanes, recU, maxU);
-  } else {
-    e = pack_records<float>(BL, false, d.rec_lanes, recL, maxL);
-    if (e.empty()) e = pack_records<float>(BU, true, d.rec_lanes, recU, maxU);
-  }
+  // ILUT records in the smoothing precision, packed for the sweep teams
+  // (uploaded once the shared-memory layout is chosen below)
+  if (n > 256) return fail(IGM_ERR_ARG, "grid rows longer than 256 unknowns are not supported");
+  struct Packed {
+    std::vector<char> L, U;
+    int maxL = 0, maxU = 0;
+  };
+  auto pack = [&](int team, Packed& pk) {
+    std::string err = o.precision == 0 ? pack_records<double>(BL, false, team, pk.L, pk.maxL)
+                                       : pack_records<float>(BL, false, team, pk.L, pk.maxL);
+    if (err.empty())
+      err = o.precision == 0 ? pack_records<double>(BU, true, team, pk.U, pk.maxU)
+                             : pack_records<float>(BU, true, team, pk.U, pk.maxU);
+    return err;
+  };
+  Packed pk128;
+  e = pack(kSweepTeam, pk128);
   if (!e.empty()) return fail(IGM_ERR_ARG, e);
-  d.Lrec.recs = up.put(recL); d.Lrec.bytes = maxL;
-  d.Urec.recs = up.put(recU); d.Urec.bytes = maxU;
-  d.slot_bytes = std::max(maxL, maxU);
   // transfers: CSR always (curved), tensor-product bands on the affine map
   d.N1 = lo.N;
   d.n1 = lo.n;
@@ -562,7 +605,6 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     gs_max = std::max(gs_max, rec_bytes);
   }
   // Gauss--Seidel rows are staged 4 at a time in the ring (see gs_rows_warp)
-  d.slot_bytes = (d.slot_bytes + 127) & ~127;
   const int gs_stage = 4 * gs_max;
   d.Cinv = up.put(Cinv);
   std::vector<int> wops;
@@ -579,7 +621,7 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.max_cycles = o.max_cycles;
   d.tol = o.tol;
   // arena layout, in elements of the smoothing precision:
-  // [r][d] (mixed only) [t] [U: FP32/64 SpMM temporaries | h-level vectors + transfer temp] [row]
+  // [r][d] (mixed only) [t] [U: FP32/64 SpMM temporaries | h-level vectors + transfer temp]
   // The mixed form's FP64 residual temporaries (2N doubles) alias d, t and U.
   const int es = o.precision == 0 ? 8 : 4;
   int off = 0;
@@ -597,26 +639,51 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   }
   d.o_tr = d.o_u + hsum;
   off += std::max(align4(2 * N) + align4(N), hsum + align4(n * lo.n));
-  d.o_row = off;
-  off = align4(off + std::max(n, lo.n) + 4);
   h->arena_bytes = (long)off * es;
   d.arena_bytes = h->arena_bytes;
   if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
-  // shared memory: record ring (2..4 stages) + mbarriers, then the arena if it fits
+  // shared memory: record ring (as many stages as fit, 4 at most; one sweep
+  // team per stage) + mbarriers + the sweep teams' scratch, then the arena if
+  // it fits, else a staged copy of the swept vector if that fits
   const long optin = dev_smem_optin() - 1024;
-  const long bars = 8 * kMaxStage;
-  auto ring_of = [&](int st) { return (long)st * d.slot_bytes + bars; };
-  d.arena_smem = 0;
-  d.nstage = 0;
-  for (int st = kMaxStage; st >= 2 && !d.nstage; --st)
-    if (ring_of(st) + h->arena_bytes <= optin && (long)st * d.slot_bytes >= gs_stage) {
-      d.nstage = st;
-      d.arena_smem = 1;
-    }
-  for (int st = kMaxStage; st >= 1 && !d.nstage; --st)
-    if (ring_of(st) <= optin && (long)st * d.slot_bytes >= gs_stage) d.nstage = st;
-  if (!d.nstage) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
-  d.ring_bytes = ring_of(d.nstage);
+  const long bars = 8 * (kMaxStage + kRowBars);
+  const long vst = ((long)N * es + 15) & ~15L;
+  // preference (measured on the unit square, nel = 64, p = 2..5): the arena
+  // in shared memory with at least 3 stages, else with 2; else the most
+  // stages with a staged copy of the swept vector; else the arena in shared
+  // memory with one stage; else the most stages with everything in global
+  // memory.  Returns the byte offset of the arena (0: nothing fits).
+  auto place = [&](int slot, int team) -> long {
+    const long sweep = ((long)wave_scratch_bytes(n, es, team) + 15) & ~15L;
+    d.arena_smem = 0;
+    d.nstage = 0;
+    d.o_vstage = -1;
+    for (int pass = 0; pass < 5; ++pass)
+      for (int st = kMaxStage; st >= 1; --st) {
+        if ((long)st * slot < gs_stage) continue;
+        const long base = (long)st * slot + bars + sweep;
+        const bool arena = base + h->arena_bytes <= optin;
+        if (pass == 0 && st >= 3 && arena) d.arena_smem = 1;
+        else if (pass == 1 && st == 2 && arena) d.arena_smem = 1;
+        else if (pass == 2 && base + vst <= optin) d.o_vstage = (int)base;
+        else if (pass == 3 && arena) d.arena_smem = 1;
+        else if (pass == 4 && base <= optin) {}
+        else continue;
+        d.nstage = st;
+        d.slot_bytes = slot;
+        d.o_sweep = (int)((long)st * slot + bars);
+        return base + (d.o_vstage >= 0 ? vst : 0);
+      }
+    return 0;
+  };
+  auto slot_of = [&](const Packed& pk) { return (std::max(std::max(pk.maxL, pk.maxU), gs_max) + 127) & ~127; };
+  const long arena_off = place(slot_of(pk128), kSweepTeam);
+  if (!arena_off) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
+  const Packed* chosen = &pk128;
+  d.Lrec.recs = up.put(chosen->L); d.Lrec.bytes = chosen->maxL;
+  d.Urec.recs = up.put(chosen->U); d.Urec.bytes = chosen->maxU;
+  if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
+  d.ring_bytes = arena_off;
   h->arena_smem = d.arena_smem != 0;
   h->smem_bytes = d.ring_bytes + (d.arena_smem ? h->arena_bytes : 0);
   static bool attr_done = false;

@@ -17,6 +17,7 @@ constexpr int kBlock = 512;       // threads per CTA of the solve kernels
 constexpr int kGroup = 4;         // lanes cooperating on one matrix row
 constexpr int kMaxH = 8;          // max h-multigrid levels at p = 1
 constexpr int kMaxStage = 4;      // max depth of the record ring
+constexpr int kRowBars = 8;       // grid-row completion barriers of the wavefront sweeps
 constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier polls (~1 s), then IGM_ERR_TIMEOUT
 
 enum WOp : int { W_GS = 0, W_RESTRICT = 1, W_COARSE = 2, W_PROLONG = 3 };
@@ -29,7 +30,7 @@ enum GsCoef : int { G_SW = 0, G_S, G_SE, G_E, G_NW, G_N, G_NE, G_ALPHA, G_INVC, 
 
 // Block-row records of one triangular factor (or of Gauss--Seidel rows),
 // streamed into shared memory: record k is grid row k (L, Gauss--Seidel) or
-// n-1-k (U); the layout is described at RecLayout.
+// n-1-k (U); the factor layout is described at RecLayout.
 struct RecSet {
   const char* recs;        // record k at recs + k * bytes (every record padded to `bytes`)
   int bytes;
@@ -57,7 +58,6 @@ struct PmgD {
   const float* sA32;
   // ILUT factors as block-row records in the smoothing precision
   RecSet Lrec, Urec;
-  int rec_lanes;               // lanes per row G of the factor records (4 or 8)
   int nstage, slot_bytes;      // record ring: nstage slots of slot_bytes
   // L2 transfers between order p and order 1 (Sec. 4, Eq. (prolongation))
   int N1, n1, wP, tp;          // tp: tensor-product transfers with 1D bands of width wP
@@ -79,12 +79,16 @@ struct PmgD {
   int inner, nu1, nu2, max_cycles;
   double tol;
   // arena layout (element offsets in the smoothing precision)
-  int o_r, o_d, o_t, o_u, o_row, o_tr;  // o_tr: transfer temporary
+  int o_r, o_d, o_t, o_u, o_tr;  // o_tr: transfer temporary
   long arena_bytes;
-  // dynamic shared memory: [record ring: nstage * slot_bytes][mbarriers: 8 * kMaxStage]
-  // followed by the arena when arena_smem
+  // dynamic shared memory: [record ring: nstage * slot_bytes][mbarriers: ring slots
+  // (kMaxStage), sweep row completion (kRowBars)]
+  // [ILUT sweep teams' scratch at o_sweep][staged copy of the vector being
+  // swept at o_vstage, when the arena is in global memory and it fits]
+  // followed by the arena (at ring_bytes) when arena_smem
   long ring_bytes;
   int arena_smem;
+  int o_sweep, o_vstage;       // byte offsets; o_vstage < 0: no staged copy
 };
 
 // ---------------------------------------------------------------------------
@@ -127,22 +131,49 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long lim
   return false;
 }
 
+constexpr long long kWaitCycles = 1LL << 31;  // ~1 s of SM clocks: bound of a sleeping wait
+
+// Wait for the phase of the given parity with the thread suspended in
+// hardware between checks (mbarrier.try_wait with a suspend-time hint), so a
+// waiting warp takes no issue slots.  Gives up after kWaitCycles SM clocks or
+// once *abort_flag is set; returns false then.
+__device__ __forceinline__ bool mbar_sleep_wait(uint64_t* b, uint32_t parity, const int* abort_flag) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok) : "r"(smem_u32(b)), "r"(parity), "r"(20000u) : "memory");
+    if (ok) return true;
+    if ((abort_flag && *(const volatile int*)abort_flag) || clock64() - t0 > kWaitCycles) return false;
+  }
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
+}
+
 // Per-CTA state of the record ring: the expected parity of every stage.
 struct Pipe {
   char* ring;
-  uint64_t* bar;
+  uint64_t* bar;      // ring slot barriers [kMaxStage]
+  uint64_t* rowbar;   // grid-row completion barriers of the sweeps [kRowBars]
   int nstage, slot;
-  uint32_t phase;
+  uint32_t phase;     // bit s: parity of the next phase of ring slot s
+  uint32_t rowphase;  // bit b: parity of the next phase of row barrier b
   bool dead;      // set (CTA-uniformly) after a wait timed out: no further copies
 };
 
-// Initialise the ring's mbarriers (whole CTA; once per kernel).
+// Initialise the ring's and the sweeps' mbarriers (whole CTA; once per kernel).
 __device__ __forceinline__ void pipe_init(Pipe& pp) {
+  pp.rowbar = pp.bar + kMaxStage;
   if (threadIdx.x == 0) {
     for (int s = 0; s < pp.nstage; ++s) mbar_init(&pp.bar[s], 1);
+    for (int b = 0; b < kRowBars; ++b) mbar_init(&pp.rowbar[b], 1);
     fence_mbar_init();
   }
   pp.phase = 0;
+  pp.rowphase = 0;
   pp.dead = false;
   __syncthreads();
 }
@@ -387,32 +418,38 @@ __device__ __forceinline__ size_t upper_off(int i, int n) {
 
 __device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
 
-// One off-block entry of a factor record: the value and the byte offset of
-// the coupled unknown in the vector being solved.
-template <typename T>
-struct alignas(sizeof(T) == 4 ? 8 : 16) RecEntry {
-  T val;
-  int off;
-};
-
 // Byte offsets inside a factor record (must match the host packing in
-// capi.cu).  Record of grid row `by` for G lanes per row: int header[4] =
-// {KL, by, G, 0}; RecEntry ent[KL][n][G]: the off-block entries of the grid
-// row's n rows, entry k of row r at ((k / G) * n + r) * G + k % G, KL =
-// ceil(max entries per row / G), padding entries (0, 0); then the dense
-// inverse of the diagonal block stored by rows in 16-byte chunks of
-// V = 16/sizeof(T) columns: row r covers the chunks of columns [0, r]
-// (lower) or [r - r % V, n) (upper), zero-padded, at chunk offset
-// rec_inv_row(r).  Every part 16-byte aligned.
+// capi.cu).  Record of grid row `by`: int header[4] = {KF, KN, by, 0}; the
+// off-block entries coupling to grid rows two or more steps back in the sweep
+// order ("far", KF per row) and to the grid row one step back ("near", KN
+// per row) as T fv[KF][n], uint16 fi[KF][n], T nv[KN][n], uint16 ni[KN][n]:
+// entry k of row r has value fv[k * n + r] and couples to unknown
+// fi[k * n + r] of the swept vector (KF, KN = max entries per row, padding
+// entries (0, 0)).  Then the dense inverse of the diagonal block in 16-byte
+// chunks of V = 16/sizeof(T) columns: row r covers the chunks of columns
+// [0, r] (lower) or [r - r % V, n) (upper), zero-padded; in row order these
+// chunks form a flat list of rec_inv_row(n) chunks, of which lane l of a
+// sweep team of `team` threads takes [l * S, (l + 1) * S), S = wave_steps.
+// The record stores them lane-step-major: Vec inv[S][team] (step s of lane l
+// at s * team + l, zero past the list), then int desc[S][team]: bits 0-7 the
+// chunk index of the right-hand side t, bits 8-17 the partial-sum slot r + l
+// of the row r the chunk belongs to, bit 31 set where the lane's piece of row
+// r ends (0 past the list).  Every part 16-byte aligned.
 template <typename T>
 struct RecLayout {
-  int o_ent, o_inv, bytes;
-  __host__ __device__ RecLayout(int n, int KL, int G, bool upper) {
-    o_ent = 16;
-    o_inv = o_ent + (((int)sizeof(RecEntry<T>) * KL * n * G + 15) & ~15);
-    bytes = o_inv + 16 * rec_inv_row(n, n, upper);
+  int o_fv, o_fi, o_nv, o_ni, o_inv, o_desc, bytes;
+  __host__ __device__ RecLayout(int n, int KF, int KN, bool upper, int team) {
+    const int S = wave_steps(n, upper, team);
+    auto a16 = [](int b) { return (b + 15) & ~15; };
+    o_fv = 16;
+    o_fi = o_fv + a16((int)sizeof(T) * KF * n);
+    o_nv = o_fi + a16(2 * KF * n);
+    o_ni = o_nv + a16((int)sizeof(T) * KN * n);
+    o_inv = o_ni + a16(2 * KN * n);
+    o_desc = o_inv + 16 * S * team;
+    bytes = o_desc + 4 * S * team;
   }
-  // chunk offset of row r (r = n gives the total number of chunks)
+  // chunk offset of row r in the flat list (r = n gives its length)
   __host__ __device__ static int rec_inv_row(int r, int n, bool upper) {
     constexpr int V = 16 / (int)sizeof(T);
     const int nc = (n + V - 1) / V;  // chunks in a full row
@@ -420,9 +457,13 @@ struct RecLayout {
     if (!upper) return V * q * (q + 1) / 2 + rem * (q + 1);   // row i: floor(i/V)+1 chunks
     return V * (q * nc - q * (q - 1) / 2) + rem * (nc - q);   // row i: nc-floor(i/V) chunks
   }
+  // steps (chunks per lane) of the diagonal-block product
+  __host__ __device__ static int wave_steps(int n, bool upper, int team) {
+    return (rec_inv_row(n, n, upper) + team - 1) / team;
+  }
 };
 
-// Issue the bulk copy of record k of a set into ring slot s (thread 0 only).
+// Issue the bulk copy of record k of a set into ring slot s (one thread).
 // Records have a fixed size so that no offset needs to be loaded here (a
 // global load at this point would sit on every row's critical path).
 __device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int s) {
@@ -430,122 +471,269 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int
             &pp.bar[s]);
 }
 
-// Block-row triangular sweep v <- D^{-1}-weighted substitution over the n
-// grid rows of a record set (L: grid rows 0..n-1; U: n-1..0).  Per grid row:
-// phase 1 forms t_r = v_i - sum_k val_k v_{base+col_k} over the off-block
-// entries in parallel (kGroup lanes per row); phase 2 writes
-// v_row = inv(D_row) t (packed dense, lower for L, upper for U).  Record k+S
-// is in flight while record k is used.  Returns false after a wait timeout.
-template <typename T, bool UPPER, int G>
-__device__ bool block_sweep(int n, const RecSet& R, Pipe& pp, T* v, T* row, int* status,
-                            unsigned long long* trace = nullptr) {
-  if (pp.dead) return false;
-  const int S = pp.nstage < n ? pp.nstage : n;
-  if (threadIdx.x == 0)
-    for (int s = 0; s < S; ++s) pipe_issue(pp, R, s, s);
-  // the vector loads of phase 2 read t up to the next 16-byte boundary past n
-  if (threadIdx.x < 16 / sizeof(T)) row[n + threadIdx.x] = (T)0;
-  for (int k = 0; k < n; ++k) {
-    const int s = k % pp.nstage;
-    PhaseClock pw(trace);
-    // warp 0 observes the copy's completion (acquire); the barrier then
-    // orders the record's contents before every thread's reads
-    const bool got = threadIdx.x < 32 ? mbar_wait(&pp.bar[s], (pp.phase >> s) & 1u) : true;
-    pp.phase ^= 1u << s;
-    const bool timeout = __syncthreads_or(!got);
-    pw.stop(8);
-    if (timeout) {
-      if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
-      // drain the copies still in flight (bounded) before giving up
-      for (int j = k + 1; j < k + S && j < n; ++j) {
-        const int sj = j % pp.nstage;
-        if (threadIdx.x < 32) mbar_wait(&pp.bar[sj], (pp.phase >> sj) & 1u);
-        pp.phase ^= 1u << sj;
-      }
-      pp.dead = true;
-      return false;
+// ---------------------------------------------------------------------------
+// wavefront block-row triangular sweeps
+// ---------------------------------------------------------------------------
+constexpr int kSweepTeam = 128;  // threads per ILUT sweep team (4 warps, one per SM sub-partition)
+
+// Scratch of a sweep in shared memory: int pieces[n] (per row r: first lane
+// of its pieces | count << 16), then per team (kBlock / team of them) the
+// grid row's right-hand side t (padded with zeros to whole 16-byte chunks)
+// and the partial sums of the diagonal-block product (slot r + lane for the
+// piece of row r that a lane computes), in elements of T.
+__host__ __device__ inline int wave_tb(int n) { return (n + 16 + 3) & ~3; }
+__host__ __device__ inline int wave_team_elems(int n, int team) {
+  return wave_tb(n) + ((n + team + 3) & ~3);
+}
+__host__ __device__ inline int wave_scratch_bytes(int n, int es, int team) {
+  return ((4 * n + 15) & ~15) + (kBlock / team) * wave_team_elems(n, team) * es;
+}
+
+// Barrier of the `nthreads` threads of sweep team `team` (named barrier
+// team + 1); the _or form also returns the OR of a predicate over the team.
+__device__ __forceinline__ void team_bar(int team, int nthreads) {
+  asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(nthreads) : "memory");
+}
+__device__ __forceinline__ bool team_bar_or(int team, int nthreads, bool pred) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 q, %1, 0;\n bar.red.or.pred p, %2, %3, q;\n"
+      " selp.s32 %0, 1, 0, p;\n}"
+      : "=r"(r) : "r"((int)pred), "r"(team + 1), "r"(nthreads) : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+
+// Completion of the sweep's grid rows: row j completes phase j / kRowBars
+// (counted from the sweep's start) of row barrier j % kRowBars (arrival
+// count 1).  A team waits on rows at most two steps back and starts a row
+// only after its previous row (at most kBlock / team <= 4 steps back) is
+// complete, so with kRowBars >= 4 the parity of the awaited phase is
+// unambiguous.
+
+// Bounded sleeping wait until grid row j of the sweep is complete (j < 0:
+// nothing to wait for).  On failure the sweep is marked abandoned.
+__device__ __forceinline__ bool wait_row(const Pipe& pp, int* abort_flag, int j) {
+  if (j < 0) return true;
+  const int b = j % kRowBars;
+  const uint32_t par = ((pp.rowphase >> b) ^ (uint32_t)(j / kRowBars)) & 1u;
+  if (mbar_sleep_wait(&pp.rowbar[b], par, abort_flag)) return true;
+  *(volatile int*)abort_flag = 1;
+  return false;
+}
+
+// acc += sum over e < K of val[e * n + r] * v[idx[e * n + r]] for one row r,
+// in e order.  The entries are fetched in batches of B independent loads,
+// then the B gathers, so that a warp keeps several shared-memory loads in
+// flight instead of waiting on each entry in turn.
+template <typename T>
+__device__ __forceinline__ T couple(const T* val, const uint16_t* idx, int K, int n, int r,
+                                    const T* v, T acc) {
+  constexpr int B = 8;
+  for (int e0 = 0; e0 < K; e0 += B) {
+    T a[B];
+    int c[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      const int e = (e0 + j < K ? e0 + j : 0) * n + r;
+      a[j] = val[e];
+      c[j] = idx[e];
     }
-    const char* rec = pp.ring + (size_t)s * pp.slot;
+    T y[B];
+#pragma unroll
+    for (int j = 0; j < B; ++j) y[j] = v[c[j]];
+#pragma unroll
+    for (int j = 0; j < B; ++j)
+      if (e0 + j < K) acc += a[j] * y[j];
+  }
+  return acc;
+}
+
+// Sum of p[l0 + j] for j < np in j order (np <= 8 in one batch of loads).
+template <typename T>
+__device__ __forceinline__ T sum_pieces(const T* p, int l0, int np) {
+  T s = 0;
+  for (int j0 = 0; j0 < np; j0 += 8) {
+    T y[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) y[j] = p[l0 + (j0 + j < np ? j0 + j : 0)];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      if (j0 + j < np) s += y[j];
+  }
+  return s;
+}
+
+// Block-row triangular sweep over the n grid rows of a record set (L: grid
+// rows 0..n-1; U: n-1..0): per grid row, t = v_row - sum over the
+// off-block entries of val * v[off], then v_row = inv(D_row) t with the dense
+// inverse of the diagonal block (lower for L, upper for U).
+//
+// Wavefront schedule: the CTA's threads form NT = min(kBlock / TEAM, ring
+// slots) teams of TEAM threads; team j takes the grid rows k = j, j + NT, ...
+// of the sweep, row k's record arrives in ring slot k % S (S slots) and the
+// team that completes row k streams in record k + S.  A team waits for its
+// row's record, accumulates the couplings to rows at least two steps back as
+// soon as those rows are complete, then the couplings to the row one step
+// back, then applies the inverse (the flat chunk list of the packed inverse
+// is cut into equal ranges, one per lane; the pieces of a row are summed in
+// lane order) and signals the row's completion on a row barrier.  One thread
+// per team waits (suspended in hardware) for records and rows and shares the
+// outcome at a team barrier; every wait is bounded.  Returns false after a
+// timeout (status gets ST_TIMEOUT; the copies in flight are drained).
+template <typename T, bool UPPER, int TEAM>
+__device__ bool wave_sweep(int n, const RecSet& R, Pipe& pp, T* v, char* scr, int* status,
+                           unsigned long long* trace = nullptr) {
+  __shared__ int s_abort, s_done;
+  if (pp.dead) return false;
+  using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  constexpr int NTM = kBlock / TEAM;
+  const int S = pp.nstage;
+  const int NT = S < NTM ? S : NTM;
+  const int team = (int)threadIdx.x / TEAM, tl = (int)threadIdx.x % TEAM;
+  const bool member = team < NT;
+  const int TB = wave_tb(n);
+  int* pieces = (int*)scr;
+  T* tb = (T*)(scr + ((4 * n + 15) & ~15)) + (size_t)(member ? team : 0) * wave_team_elems(n, TEAM);
+  T* part = tb + TB;
+  auto C = [&](int r) { return RecLayout<T>::rec_inv_row(r, n, UPPER); };
+  const int L = RecLayout<T>::wave_steps(n, UPPER, TEAM);
+  IGM_FOR_CTA(r, n) {
+    const int l0 = C(r) / L;
+    pieces[r] = l0 | (((C(r + 1) - 1) / L - l0 + 1) << 16);
+  }
+  if (threadIdx.x == 0) {
+    s_abort = 0;
+    s_done = 0;
+  }
+  if (member)
+    for (int i = n + tl; i < TB; i += TEAM) tb[i] = (T)0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    fence_proxy_async();  // earlier generic accesses of the ring before the copies
+    for (int k = 0; k < S && k < n; ++k) pipe_issue(pp, R, k, k);
+  }
+  unsigned long long t_wait = 0, t_off = 0, t_diag = 0;
+  for (int k = team; member && k < n; k += NT) {
+    const long long ta = (trace && threadIdx.x == 0) ? clock64() : 0;
+    const int sl = k % S;
+    const char* rec = pp.ring + (size_t)sl * pp.slot;
+    bool ok = true;
+    if (tl == 0) {
+      ok = mbar_sleep_wait(&pp.bar[sl], ((pp.phase >> sl) ^ (uint32_t)(k / S)) & 1u, &s_abort);
+      if (!ok) *(volatile int*)&s_abort = 1;
+      // couplings to rows at least two steps back need rows <= k-2
+      else if (((const int*)rec)[0] > 0) ok = wait_row(pp, &s_abort, k - 2);
+    }
+    if (team_bar_or(team, TEAM, !ok)) break;
+    const long long t1 = (trace && threadIdx.x == 0) ? clock64() : 0;
     const int* hdr = (const int*)rec;
-    const int KL = hdr[0], by = hdr[1];
-    const RecLayout<T> lay(n, KL, G, UPPER);
-    const RecEntry<T>* ent = (const RecEntry<T>*)(rec + lay.o_ent);
-    const char* inv = rec + lay.o_inv;
-    const char* vbytes = (const char*)v;
-    PhaseClock p1(trace);
-    // phase 1: t_r = v_i - sum over the row's off-block entries of val * v[off];
-    // a warp covers 32/G rows x G lanes and reads 32 consecutive entries per
-    // step; KL is the same for every lane (padding entries are (0, 0))
-    for_rows_g<G>(n, [&](int r, bool act, int c) {
-      const RecEntry<T>* ep = ent + (size_t)(act ? r : 0) * G + c;
-      const int stride = n * G;
-      T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-      int u = 0;
-      for (; u + 4 <= KL; u += 4) {
-        const RecEntry<T> e0 = ep[(u + 0) * stride], e1 = ep[(u + 1) * stride];
-        const RecEntry<T> e2 = ep[(u + 2) * stride], e3 = ep[(u + 3) * stride];
-        s0 += e0.val * *(const T*)(vbytes + e0.off);
-        s1 += e1.val * *(const T*)(vbytes + e1.off);
-        s2 += e2.val * *(const T*)(vbytes + e2.off);
-        s3 += e3.val * *(const T*)(vbytes + e3.off);
-      }
-      for (; u < KL; ++u) {
-        const RecEntry<T> e0 = ep[u * stride];
-        s0 += e0.val * *(const T*)(vbytes + e0.off);
-      }
-      const T sacc = group_sum_g<G>((s0 + s1) + (s2 + s3));
-      if (act && c == 0) row[r] = v[by * n + r] - sacc;
-    });
-    __syncthreads();
-    p1.stop(9);
-    PhaseClock p2(trace);
-    // phase 2: v_row = inv(D) t.  Lane c of row r takes the 16-byte chunks
-    // c, c+G, ... of the row's stored column range (one vector load of the
-    // inverse and one broadcast load of t per V columns); the trip count is
-    // the warp's maximum, out-of-range chunks are skipped by a predicate
-    for_rows_g<G>(n, [&](int r, bool act, int c) {
-      constexpr int V = 16 / (int)sizeof(T);
-      using Vec = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
-      const int rr = act ? r : 0;
-      const int j0 = UPPER ? rr - rr % V : 0;
-      const int nch = UPPER ? (n - j0 + V - 1) / V : rr / V + 1;
-      constexpr int RW = 32 / G;  // rows per warp
-      const int rw = r & ~(RW - 1);
-      const int rl = rw + RW - 1 < n ? rw + RW - 1 : n - 1;
-      const int nch_w = UPPER ? (n - (rw - rw % V) + V - 1) / V : rl / V + 1;
-      const Vec* ip = (const Vec*)(inv + 16 * RecLayout<T>::rec_inv_row(rr, n, UPPER));
-      const Vec* tp = (const Vec*)(row + j0);
+    const int KF = hdr[0], KN = hdr[1], by = hdr[2];
+    const RecLayout<T> lay(n, KF, KN, UPPER, TEAM);
+    const T* fv = (const T*)(rec + lay.o_fv);
+    const uint16_t* fi = (const uint16_t*)(rec + lay.o_fi);
+    const T* nv = (const T*)(rec + lay.o_nv);
+    const uint16_t* ni = (const uint16_t*)(rec + lay.o_ni);
+    T* vr = v + (size_t)by * n;
+    for (int r = tl; r < n; r += TEAM) tb[r] = vr[r] - couple<T>(fv, fi, KF, n, r, v, (T)0);
+    // couplings to the row one step back
+    const long long tw = (trace && threadIdx.x == 0) ? clock64() : 0;
+    if (tl == 0 && KN > 0) ok = wait_row(pp, &s_abort, k - 1);
+    if (team_bar_or(team, TEAM, !ok)) break;
+    const long long tw2 = (trace && threadIdx.x == 0) ? clock64() : 0;
+    for (int r = tl; r < n; r += TEAM) tb[r] -= couple<T>(nv, ni, KN, n, r, v, (T)0);
+    team_bar(team, TEAM);
+    const long long t4 = (trace && threadIdx.x == 0) ? clock64() : 0;
+    // diagonal block: partial products over this lane's chunk range, in
+    // batches of DB steps (all loads of a batch issued before the products)
+    {
+      constexpr int DB = sizeof(T) == 4 ? 8 : 4;
+      const Vec* inv = (const Vec*)(rec + lay.o_inv) + tl;
+      const int* desc = (const int*)(rec + lay.o_desc) + tl;
+      const Vec* tv = (const Vec*)tb;
       T s0 = 0, s1 = 0;
-      const int steps = (nch_w + G - 1) / G;
-      for (int st = 0; st < steps; ++st) {
-        const int q = c + st * G;
-        const bool ok = act && q < nch;
-        const int qq = ok ? q : 0;
-        const Vec a = ip[qq], t = tp[qq];
-        if (sizeof(T) == 4) {
-          const float4& af = reinterpret_cast<const float4&>(a);
-          const float4& tf = reinterpret_cast<const float4&>(t);
-          const T w = ok ? (T)1 : (T)0;
-          s0 += w * (af.x * tf.x + af.y * tf.y);
-          s1 += w * (af.z * tf.z + af.w * tf.w);
-        } else {
-          const double2& ad = reinterpret_cast<const double2&>(a);
-          const double2& td = reinterpret_cast<const double2&>(t);
-          const T w = ok ? (T)1 : (T)0;
-          s0 += w * (ad.x * td.x);
-          s1 += w * (ad.y * td.y);
+      for (int b0 = 0; b0 < L; b0 += DB) {
+        int d[DB];
+        Vec a[DB], x[DB];
+#pragma unroll
+        for (int jj = 0; jj < DB; ++jj) {
+          const int st = b0 + jj < L ? b0 + jj : 0;
+          d[jj] = b0 + jj < L ? desc[st * TEAM] : 0;
+          a[jj] = inv[st * TEAM];
+        }
+#pragma unroll
+        for (int jj = 0; jj < DB; ++jj) x[jj] = tv[d[jj] & 0xff];
+#pragma unroll
+        for (int jj = 0; jj < DB; ++jj) {
+          if (b0 + jj < L) {
+            if (sizeof(T) == 4) {
+              const float4& af = reinterpret_cast<const float4&>(a[jj]);
+              const float4& xf = reinterpret_cast<const float4&>(x[jj]);
+              s0 += af.x * xf.x + af.y * xf.y;
+              s1 += af.z * xf.z + af.w * xf.w;
+            } else {
+              const double2& ad = reinterpret_cast<const double2&>(a[jj]);
+              const double2& xd = reinterpret_cast<const double2&>(x[jj]);
+              s0 += ad.x * xd.x;
+              s1 += ad.y * xd.y;
+            }
+            if (d[jj] < 0) {
+              part[(d[jj] >> 8) & 0x3ff] = s0 + s1;
+              s0 = 0;
+              s1 = 0;
+            }
+          }
         }
       }
-      const T sacc = group_sum_g<G>(s0 + s1);
-      if (act && c == 0) v[by * n + r] = sacc;
-    });
-    __syncthreads();
-    p2.stop(10);
-    if (threadIdx.x == 0 && k + pp.nstage < n) {
-      fence_proxy_async();
-      pipe_issue(pp, R, k + pp.nstage, s);
+    }
+    team_bar(team, TEAM);
+    // v_row = sum of the pieces of each row, in lane order
+    for (int r = tl; r < n; r += TEAM) {
+      const int e = pieces[r];
+      vr[r] = sum_pieces<T>(part + r, e & 0xffff, e >> 16);
+    }
+    if (team_bar_or(team, TEAM, tl == 0 && ld_volatile(&s_abort))) break;
+    if (tl == 0) {
+      mbar_arrive(&pp.rowbar[k % kRowBars]);  // release: this row's values are complete
+      *(volatile int*)&s_done = k + 1;
+      if (k + S < n) {
+        fence_proxy_async();
+        pipe_issue(pp, R, k + S, sl);
+      }
+    }
+    if (trace && threadIdx.x == 0) {
+      const long long te = clock64();
+      t_wait += (unsigned long long)((t1 - ta) + (tw2 - tw));
+      t_off += (unsigned long long)((tw - t1) + (t4 - tw2));
+      t_diag += (unsigned long long)(te - t4);
     }
   }
+  __syncthreads();
+  const bool okall = ld_volatile(&s_abort) == 0;
+  if (trace && threadIdx.x == 0) {
+    atomicAdd(&trace[8], t_wait);
+    atomicAdd(&trace[9], t_off);
+    atomicAdd(&trace[10], t_diag);
+  }
+  if (!okall) {
+    // records [0, min(n, D + S)) were issued (D rows complete); drain them
+    if (threadIdx.x == 0) {
+      const int D = ld_volatile(&s_done);
+      for (int k = D; k < n && k < D + S; ++k)
+        mbar_sleep_wait(&pp.bar[k % S], ((pp.phase >> (k % S)) ^ (uint32_t)(k / S)) & 1u, nullptr);
+      if (status) atomicMin(status, ST_TIMEOUT);
+    }
+    __syncthreads();
+    pp.dead = true;
+    return false;
+  }
+  __syncthreads();
+  // slot j completed one phase per row k = j, j + S, ... < n; row barrier b
+  // one per row k = b, b + kRowBars, ... < n
+  for (int j = 0; j < S; ++j)
+    if (j < n && (((n - j + S - 1) / S) & 1)) pp.phase ^= 1u << j;
+  for (int b = 0; b < kRowBars; ++b)
+    if (b < n && (((n - b + kRowBars - 1) / kRowBars) & 1)) pp.rowphase ^= 1u << b;
   return true;
 }
 

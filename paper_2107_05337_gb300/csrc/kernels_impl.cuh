@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kBlock) k_ilut_apply(PmgD P, const double* r, 
   T* t = A + P.o_t;
   IGM_FOR_CTA(i, P.N) t[i] = (T)rc[i];
   __syncthreads();
-  ilut_apply<T>(P, pp, t, A + P.o_row, status);
+  ilut_apply<T>(P, pp, t, status);
   IGM_FOR_CTA(i, P.N) zc[i] = (double)t[i];
 }
 

@@ -61,20 +61,26 @@ template <> struct Prec<double> {
 };
 
 // v <- U^{-1} L^{-1} v (the ILUT smoother S = (LU)^{-1} applied to v, Sec. 4).
-// The factor records are in the handle's smoothing precision T.
+// The factor records are in the handle's smoothing precision T.  When the
+// arena is in global memory and shared memory has room, both sweeps run on a
+// staged shared-memory copy of v.
 template <typename T>
-__device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, T* row, int* status) {
+__device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, int* status) {
+  extern __shared__ __align__(128) char dyn_smem[];
   PhaseClock pc(P.trace);
-  bool ok;
-  if (P.rec_lanes == 8)
-    ok = block_sweep<T, false, 8>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
-         block_sweep<T, true, 8>(P.n, P.Urec, pp, v, row, status, P.trace);
-  else if (P.rec_lanes == 4)
-    ok = block_sweep<T, false, 4>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
-         block_sweep<T, true, 4>(P.n, P.Urec, pp, v, row, status, P.trace);
-  else
-    ok = block_sweep<T, false, 2>(P.n, P.Lrec, pp, v, row, status, P.trace) &&
-         block_sweep<T, true, 2>(P.n, P.Urec, pp, v, row, status, P.trace);
+  char* scr = dyn_smem + P.o_sweep;
+  T* w = v;
+  if (P.o_vstage >= 0) {
+    w = (T*)(dyn_smem + P.o_vstage);
+    IGM_FOR_CTA(i, P.N) w[i] = v[i];
+    __syncthreads();
+  }
+  const bool ok = wave_sweep<T, false, kSweepTeam>(P.n, P.Lrec, pp, w, scr, status, P.trace) &&
+                  wave_sweep<T, true, kSweepTeam>(P.n, P.Urec, pp, w, scr, status, P.trace);
+  if (P.o_vstage >= 0) {
+    IGM_FOR_CTA(i, P.N) v[i] = w[i];
+    __syncthreads();
+  }
   pc.stop(2);
   return ok;
 }
@@ -161,7 +167,6 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
   T* t = A + P.o_t;
   T* tm = A + P.o_u;
   T* tk = tm + N;
-  T* row = A + P.o_row;
   for (int s = 0; s < P.nu1; ++s) {
     const bool zero = x_is_zero && s == 0;
     if (zero) {
@@ -172,7 +177,7 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
       residualT<T>(P, b, x, t, tm, tk);
       pc.stop(1);
     }
-    if (!ilut_apply<T>(P, pp, t, row, status)) return false;
+    if (!ilut_apply<T>(P, pp, t, status)) return false;
     IGM_FOR_CTA(i, N) x[i] = zero ? t[i] : x[i] + t[i];
     __syncthreads();
   }
@@ -211,7 +216,7 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
       residualT<T>(P, b, x, t, tm, tk);
       pc.stop(1);
     }
-    if (!ilut_apply<T>(P, pp, t, row, status)) return false;
+    if (!ilut_apply<T>(P, pp, t, status)) return false;
     IGM_FOR_CTA(i, N) x[i] += t[i];
     __syncthreads();
   }
