@@ -174,9 +174,10 @@ typedef enum {
   IGM_PH_ILUT_OFF = 9,    /* ILUT, first sweep team: off-block couplings of its grid rows */
   IGM_PH_ILUT_DIAG = 10,  /* ILUT, first sweep team: diagonal-block products and row
                              completion */
-  IGM_PH_GS_WAIT = 11,    /* reserved (Gauss--Seidel rows are staged by cp.async) */
-  IGM_PH_GS_ROW = 12,     /* Gauss--Seidel: couplings to neighbouring rows */
-  IGM_PH_GS_SCAN = 13,    /* Gauss--Seidel: in-row recurrence (warp scan) and stores */
+  IGM_PH_GS_WAIT = 11,    /* Gauss--Seidel, warp 0: waits for the preceding grid row */
+  IGM_PH_GS_ROW = 12,     /* Gauss--Seidel: couplings to later unknowns (all threads) */
+  IGM_PH_GS_SCAN = 13,    /* Gauss--Seidel, warp 0: couplings to the preceding row, in-row
+                             recurrence (warp scan) and stores */
   IGM_PH_COUNT = 14
 } igm_phase;
 

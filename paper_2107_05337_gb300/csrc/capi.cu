@@ -572,10 +572,9 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   }
   // h-levels: 9-point stencils and Gauss--Seidel row records (lane-interleaved)
   d.nh = (int)H.size();
-  int gs_max = 0;
   for (int k = 0; k < d.nh; ++k) {
     const int nk = H[k].n;
-    const int E = nk <= 32 ? 1 : (nk <= 64 ? 2 : 4);  // lanes' width in gs_sweep
+    const int E = nk <= 32 ? 1 : (nk <= 64 ? 2 : (nk <= 128 ? 4 : 8));  // lanes' width in gs_sweep
     const int es_g = o.precision == 0 ? 8 : 4;
     const int rec_bytes = G_NCOEF * E * 32 * es_g;  // multiple of 128
     std::vector<char> recs((size_t)rec_bytes * nk, 0);
@@ -602,10 +601,7 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     d.h[k].A32 = up.put32(H[k].val);
     d.h[k].G.recs = up.put(recs);
     d.h[k].G.bytes = rec_bytes;
-    gs_max = std::max(gs_max, rec_bytes);
   }
-  // Gauss--Seidel rows are staged 4 at a time in the ring (see gs_rows_warp)
-  const int gs_stage = 4 * gs_max;
   d.Cinv = up.put(Cinv);
   std::vector<int> wops;
   gen_wcycle(0, d.nh - 1, wops);
@@ -660,7 +656,6 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
     d.o_vstage = -1;
     for (int pass = 0; pass < 5; ++pass)
       for (int st = kMaxStage; st >= 1; --st) {
-        if ((long)st * slot < gs_stage) continue;
         const long base = (long)st * slot + bars + sweep;
         const bool arena = base + h->arena_bytes <= optin;
         if (pass == 0 && st >= 3 && arena) d.arena_smem = 1;
@@ -676,7 +671,7 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
       }
     return 0;
   };
-  auto slot_of = [&](const Packed& pk) { return (std::max(std::max(pk.maxL, pk.maxU), gs_max) + 127) & ~127; };
+  auto slot_of = [&](const Packed& pk) { return (std::max(pk.maxL, pk.maxU) + 127) & ~127; };
   const long arena_off = place(slot_of(pk128), kSweepTeam);
   if (!arena_off) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
   const Packed* chosen = &pk128;

@@ -17,7 +17,7 @@ constexpr int kBlock = 512;       // threads per CTA of the solve kernels
 constexpr int kGroup = 4;         // lanes cooperating on one matrix row
 constexpr int kMaxH = 8;          // max h-multigrid levels at p = 1
 constexpr int kMaxStage = 4;      // max depth of the record ring
-constexpr int kRowBars = 8;       // grid-row completion barriers of the wavefront sweeps
+constexpr int kRowBars = 16;      // grid-row completion barriers of the wavefront sweeps
 constexpr long kSpinLimit = 1L << 26;  // bounded mbarrier polls (~1 s), then IGM_ERR_TIMEOUT
 
 enum WOp : int { W_GS = 0, W_RESTRICT = 1, W_COARSE = 2, W_PROLONG = 3 };
@@ -148,6 +148,17 @@ __device__ __forceinline__ bool mbar_sleep_wait(uint64_t* b, uint32_t parity, co
     if (ok) return true;
     if ((abort_flag && *(const volatile int*)abort_flag) || clock64() - t0 > kWaitCycles) return false;
   }
+}
+// Wait for the phase of the given parity by polling (test_wait); reacts
+// faster than a suspended wait but takes issue slots, so it is meant for the
+// one waiter whose turn comes next.  Gives up after kSpinLimit polls or once
+// *abort_flag is set (checked every 256 polls); returns false then.
+__device__ __forceinline__ bool mbar_spin_wait(uint64_t* b, uint32_t parity, const int* abort_flag) {
+  for (long k = 0; k < kSpinLimit; ++k) {
+    if (mbar_try_wait(b, parity)) return true;
+    if ((k & 255) == 255 && abort_flag && *(const volatile int*)abort_flag) return false;
+  }
+  return false;
 }
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b)) : "memory");
@@ -506,18 +517,21 @@ __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volati
 
 // Completion of the sweep's grid rows: row j completes phase j / kRowBars
 // (counted from the sweep's start) of row barrier j % kRowBars (arrival
-// count 1).  A team waits on rows at most two steps back and starts a row
-// only after its previous row (at most kBlock / team <= 4 steps back) is
-// complete, so with kRowBars >= 4 the parity of the awaited phase is
+// count 1).  A waiter waits on rows at most two steps back and starts a row
+// only after its previous row (at most kBlock / 32 = 16 steps back) is
+// complete, so with kRowBars >= 16 the parity of the awaited phase is
 // unambiguous.
 
-// Bounded sleeping wait until grid row j of the sweep is complete (j < 0:
-// nothing to wait for).  On failure the sweep is marked abandoned.
-__device__ __forceinline__ bool wait_row(const Pipe& pp, int* abort_flag, int j) {
+// Bounded wait until grid row j of the sweep is complete (j < 0: nothing to
+// wait for), suspended in hardware or (spin) polling.  On failure the sweep
+// is marked abandoned.
+__device__ __forceinline__ bool wait_row(const Pipe& pp, int* abort_flag, int j, bool spin = false) {
   if (j < 0) return true;
   const int b = j % kRowBars;
   const uint32_t par = ((pp.rowphase >> b) ^ (uint32_t)(j / kRowBars)) & 1u;
-  if (mbar_sleep_wait(&pp.rowbar[b], par, abort_flag)) return true;
+  if (spin ? mbar_spin_wait(&pp.rowbar[b], par, abort_flag)
+           : mbar_sleep_wait(&pp.rowbar[b], par, abort_flag))
+    return true;
   *(volatile int*)abort_flag = 1;
   return false;
 }
@@ -638,7 +652,7 @@ __device__ bool wave_sweep(int n, const RecSet& R, Pipe& pp, T* v, char* scr, in
     for (int r = tl; r < n; r += TEAM) tb[r] = vr[r] - couple<T>(fv, fi, KF, n, r, v, (T)0);
     // couplings to the row one step back
     const long long tw = (trace && threadIdx.x == 0) ? clock64() : 0;
-    if (tl == 0 && KN > 0) ok = wait_row(pp, &s_abort, k - 1);
+    if (tl == 0 && KN > 0) ok = wait_row(pp, &s_abort, k - 1, true);
     if (team_bar_or(team, TEAM, !ok)) break;
     const long long tw2 = (trace && threadIdx.x == 0) ? clock64() : 0;
     for (int r = tl; r < n; r += TEAM) tb[r] -= couple<T>(nv, ni, KN, n, r, v, (T)0);
@@ -737,78 +751,93 @@ __device__ bool wave_sweep(int n, const RecSet& R, Pipe& pp, T* v, char* scr, in
   return true;
 }
 
-// Warp-level asynchronous copies (cp.async, 16 bytes per lane per instruction)
-// with group accounting: used to stage Gauss--Seidel coefficient rows.
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
-// One forward lexicographic Gauss--Seidel sweep on a 9-point operator, run by
-// warp 0 (the caller synchronises the CTA afterwards).  The coefficient row of
-// grid row by+D is copied into a 4-slot staging area while row by is solved.
-// Grid row by: every lane forms t_r = b_r - (E, S-row, N-row couplings) x
-// for its E consecutive unknowns; the in-row recurrence
-// x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha = -a_W/a_C) is an affine map per
-// unknown, composed by a warp-wide scan.
-template <typename T, int EMAX>
-__device__ void gs_rows_warp(int n, const RecSet& R, char* stage, const T* b, T* x,
-                             unsigned long long* trace) {
-  constexpr int D = 3;            // rows in flight ahead of the one being solved
-  constexpr int E = EMAX;         // unknowns per lane (the host packs rows for this width)
-  const int lane = threadIdx.x & 31;
-  const int r0 = lane * E;
-  const int chunks = R.bytes / 16;
-  auto copy_row = [&](int row) {
-    const char* src = R.recs + (size_t)row * R.bytes;
-    char* dst = stage + (size_t)(row % (D + 1)) * R.bytes;
-    for (int i = lane; i < chunks; i += 32) cp_async16(dst + 16 * i, src + 16 * i);
+// One forward lexicographic Gauss--Seidel sweep on a 9-point operator (the
+// smoother of the h-multigrid at p = 1, Sec. 4) in two passes.  Pass 1 (all
+// threads): pre_i = b_i - (E, NW, N, NE couplings) x with the values before
+// the sweep, i.e. the couplings to unknowns that come later in the
+// lexicographic order.  Pass 2: the grid rows in order, warp w taking rows
+// w, w + 16, ...; a warp loads its row's coefficients and pre, waits for the
+// preceding row (row barrier), forms t_r = pre_r - (SW, S, SE couplings) x
+// with that row's new values, and solves the in-row recurrence
+// x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha = -a_W/a_C) as a warp-wide scan
+// of affine maps, E consecutive unknowns per lane.  Row records hold
+// coefficient q of unknown r = lane * E + e at (q * E + e) * 32 + lane.
+// Returns false after a timeout (status gets ST_TIMEOUT).
+template <typename T, int E>
+__device__ bool gs_wave(int n, const RecSet& R, Pipe& pp, const T* b, T* x, T* pre, int* status,
+                        unsigned long long* trace) {
+  __shared__ int s_abort;
+  const int N = n * n;
+  auto coef = [&](int by, int r, int q) -> T {
+    const T* cf = (const T*)(R.recs + (size_t)by * R.bytes);
+    return cf[(q * E + r % E) * 32 + r / E];
   };
-  for (int k = 0; k < D; ++k) {
-    if (k < n) copy_row(k);
-    cp_async_commit();
+  PhaseClock p0(trace);
+  IGM_FOR_CTA(i, N) {
+    const int by = i / n, r = i % n;
+    const bool hasE = r + 1 < n, hasW = r > 0, hasN = by + 1 < n;
+    T s = 0;
+    if (hasE) s += coef(by, r, G_E) * x[i + 1];
+    if (hasN) {
+      const int iN = i + n;
+      if (hasW) s += coef(by, r, G_NW) * x[iN - 1];
+      s += coef(by, r, G_N) * x[iN];
+      if (hasE) s += coef(by, r, G_NE) * x[iN + 1];
+    }
+    pre[i] = b[i] - s;
   }
-  for (int by = 0; by < n; ++by) {
-    if (by + D < n) copy_row(by + D);
-    cp_async_commit();
-    cp_async_wait<D>();           // the group of row `by` has landed
-    __syncwarp();
-    PhaseClock pt(trace);
-    const T* cf = (const T*)(stage + (size_t)(by % (D + 1)) * R.bytes);
-    T beta[EMAX], alpha[EMAX];
+  if (threadIdx.x == 0) s_abort = 0;
+  __syncthreads();
+  p0.stop(12);
+  const int w = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31, NW = (int)blockDim.x >> 5;
+  const int r0 = lane * E;
+  unsigned long long t_wait = 0, t_row = 0;
+  for (int by = w; by < n; by += NW) {
+    const long long ta = (trace && threadIdx.x == 0) ? clock64() : 0;
+    // everything that does not depend on the preceding row
+    const T* cf = (const T*)(R.recs + (size_t)by * R.bytes);
+    T cSW[E], cS[E], cSE[E], al[E], ic[E], pr[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int r = r0 + e;
+      const bool in = r < n;
+      auto c = [&](int q) { return in ? cf[(q * E + e) * 32 + lane] : (T)0; };
+      cSW[e] = c(G_SW);
+      cS[e] = c(G_S);
+      cSE[e] = c(G_SE);
+      al[e] = c(G_ALPHA);
+      ic[e] = c(G_INVC);
+      pr[e] = in ? pre[by * n + r] : (T)0;
+    }
+    bool ok = true;
+    // suspended until the row two back is complete, then polling for the
+    // preceding one (at most one warp polls at a time)
+    if (lane == 0 && by > 0) ok = wait_row(pp, &s_abort, by - 2) && wait_row(pp, &s_abort, by - 1, true);
+    __syncwarp();  // lane 0's acquire of the preceding row, for the whole warp
+    if (!__shfl_sync(0xffffffffu, ok, 0)) break;
+    const long long tw = (trace && threadIdx.x == 0) ? clock64() : 0;
+    T alpha[E], beta[E];
     T A = 1, B = 0;
 #pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
-      beta[e] = 0;
+    for (int e = 0; e < E; ++e) {
       alpha[e] = 0;
+      beta[e] = 0;
       const int r = r0 + e;
       if (r < n) {
-        const int i = by * n + r;
-        auto c = [&](int q) { return cf[(q * E + e) * 32 + lane]; };
-        // neighbours outside the grid have coefficient 0: clamp their index
-        const bool hasE = r + 1 < n, hasW = r > 0, hasS = by > 0, hasN = by + 1 < n;
-        const int iE = hasE ? i + 1 : i;
-        const int iS = hasS ? i - n : i, iN = hasN ? i + n : i;
-        const T xE = x[iE];
-        const T xSW = x[hasW ? iS - 1 : iS], xS = x[iS], xSE = x[hasE ? iS + 1 : iS];
-        const T xNW = x[hasW ? iN - 1 : iN], xN = x[iN], xNE = x[hasE ? iN + 1 : iN];
-        const T cE = hasE ? c(G_E) : (T)0;
-        const T cSW = (hasS && hasW) ? c(G_SW) : (T)0, cS = hasS ? c(G_S) : (T)0;
-        const T cSE = (hasS && hasE) ? c(G_SE) : (T)0;
-        const T cNW = (hasN && hasW) ? c(G_NW) : (T)0, cN = hasN ? c(G_N) : (T)0;
-        const T cNE = (hasN && hasE) ? c(G_NE) : (T)0;
-        const T t = b[i] - (((cE * xE + cSW * xSW) + (cS * xS + cSE * xSE)) +
-                            ((cNW * xNW + cN * xN) + cNE * xNE));
-        alpha[e] = c(G_ALPHA);
-        beta[e] = c(G_INVC) * t;
+        T t = pr[e];
+        if (by > 0) {
+          // neighbours outside the grid have coefficient 0: clamp their index
+          const int iS = (by - 1) * n + r;
+          const T xSW = x[r > 0 ? iS - 1 : iS], xS = x[iS], xSE = x[r + 1 < n ? iS + 1 : iS];
+          const T sw = r > 0 ? cSW[e] : (T)0, se = r + 1 < n ? cSE[e] : (T)0;
+          t -= (sw * xSW + cS[e] * xS) + se * xSE;
+        }
+        alpha[e] = al[e];
+        beta[e] = ic[e] * t;
         B = alpha[e] * B + beta[e];
         A = alpha[e] * A;
       }
     }
-    pt.stop(12);
-    PhaseClock ps(trace);
     // inclusive scan of the lanes' affine maps x_out = A x_in + B
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -821,9 +850,8 @@ __device__ void gs_rows_warp(int n, const RecSet& R, char* stage, const T* b, T*
     }
     T xin = __shfl_up_sync(0xffffffffu, B, 1);
     if (lane == 0) xin = 0;
-    __syncwarp();
 #pragma unroll
-    for (int e = 0; e < EMAX; ++e) {
+    for (int e = 0; e < E; ++e) {
       const int r = r0 + e;
       if (r < n) {
         xin = alpha[e] * xin + beta[e];
@@ -831,23 +859,39 @@ __device__ void gs_rows_warp(int n, const RecSet& R, char* stage, const T* b, T*
       }
     }
     __syncwarp();
-    ps.stop(13);
-  }
-  cp_async_wait<0>();
-}
-
-// A Gauss--Seidel sweep staged through the (idle) record ring.
-template <typename T>
-__device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, int* status,
-                         unsigned long long* trace = nullptr) {
-  if (pp.dead) return false;
-  if (threadIdx.x < 32) {
-    if (n <= 32) gs_rows_warp<T, 1>(n, R, pp.ring, b, x, trace);
-    else if (n <= 64) gs_rows_warp<T, 2>(n, R, pp.ring, b, x, trace);
-    else gs_rows_warp<T, 4>(n, R, pp.ring, b, x, trace);
+    if (lane == 0) mbar_arrive(&pp.rowbar[by % kRowBars]);  // release: the row is complete
+    if (trace && threadIdx.x == 0) {
+      const long long te = clock64();
+      t_wait += (unsigned long long)(tw - ta);
+      t_row += (unsigned long long)(te - tw);
+    }
   }
   __syncthreads();
+  const bool okall = ld_volatile(&s_abort) == 0;
+  __syncthreads();
+  if (trace && threadIdx.x == 0) {
+    atomicAdd(&trace[11], t_wait);
+    atomicAdd(&trace[13], t_row);
+  }
+  if (!okall) {
+    if (threadIdx.x == 0 && status) atomicMin(status, ST_TIMEOUT);
+    pp.dead = true;
+    return false;
+  }
+  for (int bb = 0; bb < kRowBars; ++bb)
+    if (bb < n && (((n - bb + kRowBars - 1) / kRowBars) & 1)) pp.rowphase ^= 1u << bb;
   return true;
+}
+
+// A Gauss--Seidel sweep (pre: scratch of n * n).
+template <typename T>
+__device__ bool gs_sweep(int n, const RecSet& R, Pipe& pp, const T* b, T* x, T* pre, int* status,
+                         unsigned long long* trace = nullptr) {
+  if (pp.dead) return false;
+  if (n <= 32) return gs_wave<T, 1>(n, R, pp, b, x, pre, status, trace);
+  if (n <= 64) return gs_wave<T, 2>(n, R, pp, b, x, pre, status, trace);
+  if (n <= 128) return gs_wave<T, 4>(n, R, pp, b, x, pre, status, trace);
+  return gs_wave<T, 8>(n, R, pp, b, x, pre, status, trace);
 }
 
 // Tensor-product transfer on the affine map, stage along xi then eta:

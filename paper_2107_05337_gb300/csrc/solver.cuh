@@ -112,7 +112,7 @@ __device__ bool wcycle(const PmgD& P, Pipe& pp, T* A, int* status) {
     switch (op) {
       case W_GS: {
         PhaseClock pc(P.trace);
-        const bool ok = gs_sweep<T>(H.n, H.G, pp, bk, xk, status, P.trace);
+        const bool ok = gs_sweep<T>(H.n, H.G, pp, bk, xk, tk, status, P.trace);
         pc.stop(7);
         if (!ok) return false;
         break;
