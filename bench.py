@@ -54,6 +54,12 @@ def manufactured():
     return S, C
 
 
+# DRAM bytes per V-cycle and unknown measured by ncu on k_mgrit_sweep (p = 4,
+# 64 x 64 elements, fine-level relaxation launch; profiles/
+# k_mgrit_sweep_heat_c2_p4_wavefront.md); re-measure whenever the kernel changes.
+DRAM_BYTES_PER_VCYCLE_DOF = 24.7
+
+
 def bytes_per_vcycle_dof(p, B):
     """Algorithmic bytes of one V(1,1) per DOF per right-hand side (8-byte
     values; matrices amortised over the B right-hand sides of a launch):
@@ -215,8 +221,16 @@ def main():
             stats.update(out)
 
     if args.profile_only:
-        step(chosen)
+        step(chosen, concurrent=False)
         torch.cuda.synchronize()
+        # per-launch V-cycle counts of the same solves (same order of launches),
+        # to relate a captured launch's DRAM counters to its units of work
+        for p in orders:
+            hp = B.MGRIT(probs[p], **opts, pmg=dict(precision=1, tol=1e-10), profile=1, graphs=0)
+            hp.run(u0s[p], fhats[p], fcoef, Us[p])
+            pr = hp.profile()
+            print(json.dumps({"order": p, "N": int(probs[p].N), "grid": [int(g) for g in pr["grid"]],
+                              "cycles": [int(c) for c in pr["cycles"]]}))
         return
 
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
@@ -299,13 +313,14 @@ def main():
 
     # roofline of the dominant kernel (k_mgrit_sweep), one profiled solve per order
     roof = None
-    prof_tot_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
+    prof_tot_ms, prof_bytes, prof_launches, prof_units = 0.0, 0.0, 0, 0
     for p in orders:
         hp = B.MGRIT(probs[p], **opts, pmg=dict(precision=1, tol=1e-10), profile=1, graphs=0)
         hp.run(u0s[p], fhats[p], fcoef, Us[p])
         pr = hp.profile()
         for g, c, t in zip(pr["grid"], pr["cycles"], pr["ms"]):
             prof_bytes += c * probs[p].N * bytes_per_vcycle_dof(p, g)
+            prof_units += c * probs[p].N
             prof_tot_ms += t
             prof_launches += 1
         del hp
@@ -314,7 +329,8 @@ def main():
         achieved = prof_bytes / (prof_tot_ms * 1e-3) / 1e9
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 5), "traffic": None,
+                "frac": round(achieved / peak, 5),
+                "traffic": round(DRAM_BYTES_PER_VCYCLE_DOF * prof_units / prof_launches),
                 "kernel": "k_mgrit_sweep", "launches_profiled": prof_launches,
                 "mean_launch_ms": round(prof_tot_ms / prof_launches, 4),
                 "peak_source": "measured" if peaks else "fallback"}
