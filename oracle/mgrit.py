@@ -1,4 +1,5 @@
-"""Two-level and multilevel MGRIT for backward Euler (Sec. 3), plain FP64.
+"""Two-level and multilevel MGRIT for theta-scheme time stepping (Sec. 3,
+with the theta of Sec. 2 Eq. (los)), plain FP64.
 
 Test infrastructure (see ``oracle/__init__``).  Pinned by
 ``tests/test_oracle_mgrit.py``:
@@ -18,17 +19,21 @@ Test infrastructure (see ``oracle/__init__``).  Pinned by
 
 The method (Sec. 3, the MGRIT algorithm box; ideal interpolation P):
   level l has time step dt_l = m^l dt and N_l = N_t / m^l steps; on level l
-  the step is  u_n = Phi_l(u_{n-1}) + g_n,  Phi_l = Psi_l M,
-  Psi_l = (M + kappa dt_l K)^{-1} (rediscretised on every level).  On the
-  fine level the source enters the solve: Phi_0(u) + g_n = Psi_0 (M u + dt f_n),
+  the step is  u_n = Phi_l(u_{n-1}) + g_n,  Phi_l = Psi_l R_l,
+  Psi_l = (M + theta kappa dt_l K)^{-1}, R_l = M - (1-theta) kappa dt_l K
+  (rediscretised on every level; theta = 1 is backward Euler, Sec. 3).  On the
+  fine level the source enters the solve:
+  Phi_0(u) + g_n = Psi_0 (R_0 u + dt (theta c(t_n) + (1-theta) c(t_{n-1})) fhat),
   u_0 = g_0 = the projected initial condition.
 
-  cycle(l):  if l is the coarsest level: solve A^(l) u = g^(l) by forward
-             stepping; else
+  cycle(l, kind):  if l is the coarsest level: solve A^(l) u = g^(l) by
+             forward stepping; else
              FCF-relaxation on A^(l) u = g^(l);
              inject the C-point residual  r_j = g_{jm} + Phi_l(u_{jm-1}) - u_{jm}
              as the right-hand side g^(l+1)_j of the next level (u^(l+1) = 0);
-             cycle(l+1);
+             visit level l+1: once (V-cycle), as an F-cycle then a V-cycle
+             (F-cycle), or twice with the same kind (W-cycle); the second
+             visit starts from the first one's result;
              correct u_{jm} += u^(l+1)_j and F-relax (= ideal interpolation
              P = [-A_FF^{-1} A_FC; I_C]).
 
@@ -50,6 +55,9 @@ Readings of points the paper leaves open or prints garbled (also in the design doc):
     the spatial solves are exact or run to a tolerance from a warm start).
   * Each spatial solve is warm-started from the current value at that time
     point of the part of u that the solve produces (u_n - g_n).
+  * F- and W-cycles (named, not defined, in Sec. 5): the standard multigrid
+    recursions above.  A repeated visit of the coarsest level (an exact
+    forward solve of an unchanged system) is skipped.
 """
 import numpy as np
 
@@ -63,21 +71,28 @@ def level_sizes(Nt, m, max_levels=30, min_coarse=4):
 
 
 class MGRIT:
-    """MGRIT for (M + kappa dt K) u^{n} = M u^{n-1} + dt c(t_n) fhat.
+    """MGRIT for (M + theta kappa dt K) u^{n} = (M - (1-theta) kappa dt K) u^{n-1}
+    + dt (theta c(t_n) + (1-theta) c(t_{n-1})) fhat.
 
     solver_factory(level, c) must return a callable
-    solve(rhs, guess) -> (x, cycles) for the matrix M + c K."""
+    solve(rhs, guess) -> (x, cycles) for the matrix M + c K.
+    cycle: "V", "F" or "W" (the hierarchy of Sec. 5)."""
 
     def __init__(self, M, K, kappa, T, Nt, m, solver_factory, u0, fhat=None, fcoef=None,
-                 max_levels=30, min_coarse=4, relax="FCF", skip_redundant_F=True):
+                 max_levels=30, min_coarse=4, relax="FCF", skip_redundant_F=True, theta=1.0,
+                 cycle="V"):
+        assert cycle in ("V", "F", "W")
         self.M = M.tocsr()
+        self.K = K.tocsr()
+        self.theta = theta
+        self.kind = cycle
         self.kappa = kappa
         self.Nt = Nt
         self.m = m
         self.sizes = level_sizes(Nt, m, max_levels, min_coarse)
         self.L = len(self.sizes) - 1
         self.dt = [T / Nt * m ** l for l in range(len(self.sizes))]
-        self.solve = [solver_factory(l, kappa * self.dt[l]) for l in range(len(self.sizes))]
+        self.solve = [solver_factory(l, theta * kappa * self.dt[l]) for l in range(len(self.sizes))]
         self.fhat = fhat
         self.fcoef = fcoef
         self.relax = relax
@@ -97,9 +112,13 @@ class MGRIT:
 
     def phi(self, l, n):
         """Solve part of the step into point n of level l (warm start W_n)."""
-        rhs = self.M @ self.u(l, n - 1)
+        u = self.u(l, n - 1)
+        rhs = self.M @ u
+        if self.theta != 1.0:
+            rhs = rhs - (1.0 - self.theta) * self.kappa * self.dt[l] * (self.K @ u)
         if l == 0 and self.fhat is not None:
-            rhs = rhs + self.dt[0] * self._c(n) * self.fhat
+            c = self.theta * self._c(n) + (1.0 - self.theta) * self._c(n - 1)
+            rhs = rhs + self.dt[0] * c * self.fhat
         x, cyc = self.solve[l](rhs, self.W[l][n])
         self.cycles.append(cyc)
         return x
@@ -143,14 +162,23 @@ class MGRIT:
             self.W[l][j * m] += self.u(l + 1, j)
         self.f_relax(l)
 
-    def cycle(self, l):
+    def cycle(self, l, kind=None):
+        kind = kind or self.kind
         if l == self.L:
             for n in range(1, self.sizes[l] + 1):
                 self.W[l][n] = self.phi(l, n)
             return
         self.down(l, fresh=True)
-        self.cycle(l + 1)
+        self.visit(l + 1, kind)
         self.up(l)
+
+    def visit(self, l, kind):
+        """The coarse-level visits of one cycle of the given kind."""
+        visits = {"V": ["V"], "F": ["F", "V"], "W": ["W", "W"]}[kind]
+        if l == self.L:
+            visits = visits[:1]
+        for k in visits:
+            self.cycle(l, k)
 
     def run(self, tol=1e-10, max_iter=50, callback=None):
         """Returns (U [Nt+1, N], iterations, residual history)."""
@@ -167,7 +195,7 @@ class MGRIT:
                 callback(it, self)
             if rho == 0.0 or rho <= tol * hist[0] or it >= max_iter:
                 break
-            self.cycle(1)
+            self.visit(1, self.kind)
             self.up(0)
             it += 1
         return self.W[0], it, hist

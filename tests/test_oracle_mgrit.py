@@ -123,3 +123,51 @@ def test_mgrit_with_pmg_solves_matches_sequential():
     U, it, hist = mg.run(tol=1e-12)
     assert np.linalg.norm(U - seq) <= 1e-11 * np.linalg.norm(seq)
     assert 0 < np.mean(mg.cycles) < 6
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.0])
+@pytest.mark.parametrize("cycle", ["V", "F", "W"])
+def test_theta_and_cycle_fixed_point_is_sequential(theta, cycle):
+    """MGRIT's fixed point is sequential theta-stepping for every cycle kind
+    (forward Euler on a step small enough to be stable)."""
+    d = assembly.Discretisation(2, 4, geometry.UnitSquare())
+    u0 = d.project(S)
+    fhat = d.load_vector(S)
+    c = lambda t: 2 * np.pi ** 2 * np.cos(t) - np.sin(t)
+    T, Nt = (0.5, 64) if theta > 0 else (0.02, 64)
+    seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, u0, fhat, c, theta=theta)
+    mg = mgrit.MGRIT(d.M, d.K, 1.0, T, Nt, 4, mgrit.direct_factory(d.M, d.K), u0, fhat, c,
+                     theta=theta, cycle=cycle)
+    U, it, hist = mg.run(tol=1e-13, max_iter=60)
+    assert len(mg.sizes) == 3
+    np.testing.assert_allclose(U, seq, rtol=0, atol=1e-11 * np.abs(seq).max())
+
+
+def test_cycle_kinds_coincide_on_two_levels():
+    """With two levels the coarse level is the exact coarsest solve, so V-, F-
+    and W-cycles are the same iteration (the repeated visit is skipped)."""
+    d = assembly.Discretisation(2, 4, geometry.UnitSquare())
+    u0 = d.project(S)
+    out = []
+    for cycle in ("V", "F", "W"):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, 1.0, 32, 4, mgrit.direct_factory(d.M, d.K), u0,
+                         max_levels=2, cycle=cycle)
+        out.append(mg.run(tol=1e-10, max_iter=20))
+    for U, it, hist in out[1:]:
+        np.testing.assert_array_equal(U, out[0][0])
+        assert it == out[0][1] and hist == out[0][2]
+
+
+def test_f_and_w_cycles_need_no_more_iterations_than_v():
+    """More coarse-level work per iteration: on the paper's own problem (f = 1,
+    u0 = 0, T = 0.1, Sec. 5) F- and W-cycles converge in at most the
+    V-cycle's iterations, and the W-cycle in at most the F-cycle's."""
+    d = assembly.Discretisation(2, 8, geometry.UnitSquare())
+    fhat = d.load_vector(lambda xi, eta, x, y: np.ones_like(x))
+    u0 = np.zeros(d.N)
+    its = {}
+    for cycle in ("V", "F", "W"):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, 0.1, 256, 2, mgrit.direct_factory(d.M, d.K), u0, fhat,
+                         lambda t: 1.0, min_coarse=2, cycle=cycle)
+        its[cycle] = mg.run(tol=1e-10, max_iter=50)[1]
+    assert its["W"] <= its["F"] <= its["V"], its

@@ -42,3 +42,51 @@ def test_manufactured_first_order_in_time():
             for Nt in (20, 40, 80)]
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
     assert np.all(np.abs(rates - 1.0) < 0.1), rates
+
+
+def test_theta_eigenvector_decay_exact():
+    """Eq. (los) on K v = mu M v: u_n = ((1-(1-theta) k dt mu)/(1+theta k dt mu))^n v."""
+    d = assembly.Discretisation(2, 5, geometry.UnitSquare())
+    mu, V = sla.eigh(d.K.toarray(), d.M.toarray())
+    kappa, T, Nt = 0.7, 0.05, 10
+    dt = T / Nt
+    for theta in (0.5, 0.0, 0.3):
+        for k in (0, 5, len(mu) - 1):
+            U = timestep.sequential(d.M, d.K, kappa, T, Nt, V[:, k], theta=theta)
+            g = (1 - (1 - theta) * kappa * dt * mu[k]) / (1 + theta * kappa * dt * mu[k])
+            for n in range(Nt + 1):
+                np.testing.assert_allclose(U[n], g ** n * V[:, k], rtol=1e-9,
+                                           atol=1e-11 * max(1.0, abs(g) ** n) * np.abs(V[:, k]).max())
+
+
+def _semidiscrete_exact(d, kappa, T, u0, fhat, c):
+    """Exact solution at T of M u' + kappa K u = c(t) fhat, u(0) = u0, by the
+    generalised eigen-decomposition (V^T M V = I) and composite Gauss-Legendre
+    quadrature of the source integral."""
+    mu, V = sla.eigh(d.K.toarray(), d.M.toarray())
+    a0 = V.T @ (d.M @ u0)
+    b = V.T @ fhat
+    x, w = np.polynomial.legendre.leggauss(20)
+    integ = np.zeros_like(mu)
+    edges = np.linspace(0.0, T, 201)
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        s = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
+        for si, wi in zip(s, w):
+            integ += 0.5 * (hi - lo) * wi * np.exp(-kappa * mu * (T - si)) * c(si)
+    return V @ (np.exp(-kappa * mu * T) * a0 + integ * b)
+
+
+def test_theta_scheme_order_against_semidiscrete_solution():
+    """Backward Euler is first and Crank-Nicolson second order in dt against
+    the exact solution of the semi-discrete system (no spatial error)."""
+    d = assembly.Discretisation(2, 3, geometry.UnitSquare())
+    u0 = d.project(S)
+    fhat = d.load_vector(S)
+    c = lambda t: 2 * np.pi ** 2 * np.cos(t) - np.sin(t)
+    ref = _semidiscrete_exact(d, 1.0, 1.0, u0, fhat, c)
+    for theta, order in ((1.0, 1.0), (0.5, 2.0)):
+        errs = [np.linalg.norm(timestep.sequential(d.M, d.K, 1.0, 1.0, Nt, u0, fhat, c,
+                                                   theta=theta)[-1] - ref)
+                for Nt in (40, 80, 160)]
+        rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+        assert np.all(np.abs(rates - order) < 0.1), (theta, rates)
