@@ -207,6 +207,9 @@ typedef struct {
   int initial_guess; /* 0: u_n = 0 for n >= 1; 1: start from the U passed in */
   int graphs;      /* 1: replay each iteration's launches as CUDA graphs (default 1) */
   int profile;     /* 1: record CUDA events around every sweep launch (mgrit_profile) */
+  double theta;    /* theta-scheme of Sec. 2, Eq. (los): 1 backward Euler (default),
+                      0.5 Crank-Nicolson, 0 forward Euler; in [0, 1] */
+  int cycle;       /* MGRIT hierarchy (Sec. 5): 0 V-cycle (default), 1 F-cycle, 2 W-cycle */
 } mgrit_opts;
 
 typedef struct {
@@ -227,7 +230,8 @@ void mgrit_default_opts(mgrit_opts* o);
 
 /* Set up MGRIT (Sec. 3) for the time grid in opts: the level hierarchy
  * dt_l = m^l dt, one p-multigrid hierarchy per level (rediscretised operator
- * M + kappa dt_l K), and the device work buffers.  Host setup plus uploads;
+ * M + theta kappa dt_l K; the step's right-hand side uses
+ * M - (1 - theta) kappa dt_l K), and the device work buffers.  Host setup plus uploads;
  * no solve.  The handle keeps a pointer to ops, which must outlive it. */
 igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, mgrit_handle** out);
 void mgrit_destroy(mgrit_handle* mg);

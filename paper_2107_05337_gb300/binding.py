@@ -38,7 +38,7 @@ class MgritOpts(ctypes.Structure):
     _fields_ = [("T", c_double), ("Nt", c_int), ("m", c_int), ("max_levels", c_int),
                 ("min_coarse", c_int), ("relax", c_int), ("tol", c_double), ("max_iter", c_int),
                 ("pmg", PmgOpts), ("initial_guess", c_int), ("graphs", c_int),
-                ("profile", c_int)]
+                ("profile", c_int), ("theta", c_double), ("cycle", c_int)]
 
 
 class MgritStats(ctypes.Structure):
@@ -282,10 +282,16 @@ class PMG:
                 sp.csr_matrix((uv, uc, up_), shape=(N, N)))
 
 
+CYCLES = {"V": 0, "F": 1, "W": 2}
+
+
 def mgrit_opts(**kw):
+    """mgrit_opts from keyword arguments; cycle may be given as "V", "F" or "W"."""
     o = MgritOpts()
     lib().mgrit_default_opts(ctypes.byref(o))
     pmg_kw = kw.pop("pmg", {})
+    if isinstance(kw.get("cycle"), str):
+        kw["cycle"] = CYCLES[kw["cycle"]]
     for k, v in kw.items():
         setattr(o, k, v)
     for k, v in pmg_kw.items():

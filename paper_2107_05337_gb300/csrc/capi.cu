@@ -473,8 +473,19 @@ static bool transfer_bands(const Discretisation& hi, const Discretisation& lo, i
   return fill(n, n1, false, js, band) && fill(n1, n, true, is, tband);
 }
 
+// Set-up of one p-multigrid hierarchy for A = M + kappa_dt K; expl_dt != 0
+// also uploads R = M - expl_dt K, the explicit part of a theta-scheme step
+// (Sec. 2, Eq. (los)), for the step right-hand side.
+static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_dt,
+                               const pmg_opts* opts, pmg_handle** out);
+
 extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_opts* opts,
                                 pmg_handle** out) {
+  return pmg_setup_ex(ops, kappa_dt, 0.0, opts, out);
+}
+
+static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_dt,
+                               const pmg_opts* opts, pmg_handle** out) {
   if (!ops || !out) return fail(IGM_ERR_ARG, "null argument");
   auto h = std::make_unique<pmg_handle>();
   h->ops = ops;
@@ -532,6 +543,21 @@ extern "C" igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_o
   d.sA64 = up.put(A.val);
   d.sA32 = up.put32(A.val);
   d.sM64 = ops->sM64;
+  d.expl = expl_dt;
+  if (expl_dt != 0.0) {
+    Stencil R = hi.M;
+    for (size_t i = 0; i < R.val.size(); ++i) R.val[i] = hi.M.val[i] - expl_dt * hi.K.val[i];
+    d.sR64 = up.put(R.val);
+    if (d.affine) {
+      std::vector<double> bR((size_t)n * W), bcR((size_t)n * W);
+      for (size_t i = 0; i < bR.size(); ++i) {
+        bR[i] = hi.M1[i] - expl_dt * hi.K1[i];
+        bcR[i] = -expl_dt * hi.M1[i];
+      }
+      d.bR64 = up.put(bR);
+      d.bcR64 = up.put(bcR);
+    }
+  }
   // ILUT records in the smoothing precision, packed for the sweep teams
   // (uploaded once the shared-memory layout is chosen below)
   if (n > 256) return fail(IGM_ERR_ARG, "grid rows longer than 256 unknowns are not supported");
@@ -893,6 +919,8 @@ extern "C" void mgrit_default_opts(mgrit_opts* o) {
   o->initial_guess = 0;
   o->graphs = 1;
   o->profile = 0;
+  o->theta = 1.0;
+  o->cycle = 0;
 }
 
 struct Level {
@@ -955,6 +983,8 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
       o.max_iter > 255)
     return fail(IGM_ERR_ARG, "bad MGRIT options (Nt >= 1, m >= 2, T > 0, 0 <= max_iter <= 255)");
   if (o.relax != 0 && o.relax != 1) return fail(IGM_ERR_ARG, "relax must be 0 or 1");
+  if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail(IGM_ERR_ARG, "theta must be in [0, 1]");
+  if (o.cycle < 0 || o.cycle > 2) return fail(IGM_ERR_ARG, "cycle must be 0 (V), 1 (F) or 2 (W)");
   auto t0 = std::chrono::steady_clock::now();
   auto mg = std::make_unique<mgrit_handle>();
   mg->ops = ops;
@@ -976,7 +1006,8 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   Uploader& up = mg->up;
   for (int l = 0; l < nlev; ++l) {
     pmg_handle* h = nullptr;
-    igm_status r = pmg_setup(ops, ops->kappa * L[l].dt, &o.pmg, &h);
+    igm_status r = pmg_setup_ex(ops, o.theta * ops->kappa * L[l].dt,
+                                (1.0 - o.theta) * ops->kappa * L[l].dt, &o.pmg, &h);
     if (r != IGM_OK) return r;
     mg->owned.push_back(h);
     L[l].h = h;
@@ -1031,6 +1062,7 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
   a.fhat = (l == 0) ? fhat : nullptr;
   a.fcoef = mg->dfcoef;
   a.dt0 = L[0].dt;
+  a.theta = mg->o.theta;
   a.scratch = mg->scratch;
   a.garena = L[l].h->garena;
   a.ncycles = 0;
@@ -1079,26 +1111,53 @@ static igm_status part_A(mgrit_handle* mg, bool first, double* U, const double* 
   return IGM_OK;
 }
 
-// Part B: the coarse levels (recursive V-cycle, Sec. 3 algorithm box) and the
-// corrections with F-relaxation (ideal interpolation) back to the fine level.
-static igm_status part_B(mgrit_handle* mg, double* U, const double* fhat, cudaStream_t st,
-                         bool profile) {
+// One visit of coarse level l >= 1 with a cycle of the given kind (Sec. 3
+// algorithm box; Sec. 5 names V-, F-cycles): relaxation and residual into
+// g^(l+1), then the visits of level l+1 (V: one V; F: an F then a V; W: two
+// W, the second from the first's result; a repeated visit of the exact
+// coarsest level is skipped), then the correction with F-relaxation.
+static igm_status visit(mgrit_handle* mg, int l, int kind, double* U, const double* fhat,
+                        cudaStream_t st, bool profile) {
   const int nlev = (int)mg->L.size(), N = mg->ops->hi.N;
   std::vector<Level>& L = mg->L;
-  for (int l = 1; l < nlev; ++l) {
-    CU(cudaMemsetAsync(L[l].W, 0, sizeof(double) * (size_t)(L[l].Nl + 1) * N, st));
-    if (l == nlev - 1) {
-      SWEEP(l, MODE_SEQ, 1, nullptr);
-    } else {
-      const int ni = L[l].Nl / mg->o.m;
-      if (mg->o.relax == 1) {
-        SWEEP(l, MODE_F, ni, nullptr);
-        SWEEP(l, MODE_C, ni, nullptr);
-      }
-      SWEEP(l, MODE_FR, ni, nullptr);
-    }
+  if (l == nlev - 1) {
+    SWEEP(l, MODE_SEQ, 1, nullptr);
+    return IGM_OK;
   }
-  for (int l = nlev - 2; l >= 0; --l) SWEEP(l, MODE_CF, L[l].Nl / mg->o.m, nullptr);
+  const int ni = L[l].Nl / mg->o.m;
+  if (mg->o.relax == 1) {
+    SWEEP(l, MODE_F, ni, nullptr);
+    SWEEP(l, MODE_C, ni, nullptr);
+  }
+  SWEEP(l, MODE_FR, ni, nullptr);
+  CU(cudaMemsetAsync(L[l + 1].W, 0, sizeof(double) * (size_t)(L[l + 1].Nl + 1) * N, st));
+  const int sub[3][2] = {{0, -1}, {1, 0}, {2, 2}};
+  for (int v = 0; v < 2; ++v) {
+    const int k = sub[kind][v];
+    if (k < 0 || (v == 1 && l + 1 == nlev - 1)) break;
+    igm_status r = visit(mg, l + 1, k, U, fhat, st, profile);
+    if (r != IGM_OK) return r;
+  }
+  SWEEP(l, MODE_CF, ni, nullptr);
+  return IGM_OK;
+}
+
+// Part B: the coarse levels and the correction with F-relaxation (ideal
+// interpolation) of the fine level.
+static igm_status part_B(mgrit_handle* mg, double* U, const double* fhat, cudaStream_t st,
+                         bool profile) {
+  const int N = mg->ops->hi.N;
+  std::vector<Level>& L = mg->L;
+  CU(cudaMemsetAsync(L[1].W, 0, sizeof(double) * (size_t)(L[1].Nl + 1) * N, st));
+  const int kind = mg->o.cycle;
+  const int nlev = (int)L.size();
+  for (int v = 0; v < 2; ++v) {
+    const int k = v == 0 ? kind : (kind == 1 ? 0 : (kind == 2 ? 2 : -1));
+    if (k < 0 || (v == 1 && nlev == 2)) break;
+    igm_status r = visit(mg, 1, k, U, fhat, st, profile);
+    if (r != IGM_OK) return r;
+  }
+  SWEEP(0, MODE_CF, L[0].Nl / mg->o.m, nullptr);
   return IGM_OK;
 }
 

@@ -53,6 +53,11 @@ struct PmgD {
   // affine operator: 1D interior bands [n][2p+1]; bA = M1 + c K1, bcM = c M1
   const double *bM64, *bK64, *bA64, *bcM64;
   const float *bM32, *bK32, *bA32, *bcM32;
+  // explicit part of a theta-scheme step, R = M - expl K (expl = (1-theta)
+  // kappa dt; 0 for backward Euler): affine y-bands bR = M1 - expl K1,
+  // bcR = -expl M1; curved stencil sR
+  double expl;
+  const double *bR64, *bcR64, *sR64;
   // curved operator: stencils [N][(2p+1)^2]
   const double *sA64, *sM64;
   const float* sA32;

@@ -25,6 +25,7 @@ struct SweepArgs {
   const double* fhat;     // fine level source profile or nullptr
   const double* fcoef;    // device [Nt+1] time factors
   double dt0;
+  double theta;           // theta-scheme weight of the source: theta c(t_n) + (1-theta) c(t_{n-1})
   double* scratch;        // per CTA: 2 N doubles (rhs, residual iterate)
   char* garena;
   int ncycles;

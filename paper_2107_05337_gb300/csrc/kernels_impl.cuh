@@ -62,7 +62,8 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
   double* tm = (PREC == 0) ? (double*)arena + P.o_u : (double*)((float*)arena + P.o_d);
   const double* u = a.W + (size_t)(n - 1) * N;
   const double* ug = a.g ? a.g + (size_t)(n - 1) * N : nullptr;
-  const double scale = a.fhat ? a.dt0 * a.fcoef[n] : 0.0;
+  const double scale =
+      a.fhat ? a.dt0 * (a.theta * a.fcoef[n] + (1.0 - a.theta) * a.fcoef[n - 1]) : 0.0;
   {
     PhaseClock pc(P.trace);
     build_rhs(P, u, ug, scale, a.fhat, rhs, tm);

@@ -295,16 +295,24 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
   return cyc;
 }
 
-// out = M (u + ug) + scale * fhat in FP64 (the right-hand side of one
-// backward-Euler step, Sec. 3: M u^{n-1} + dt f^n).  tm: N doubles scratch.
+// out = R (u + ug) + scale * fhat in FP64 with R = M - expl K (the
+// right-hand side of one theta-scheme step, Sec. 2 Eq. (los) and Sec. 3:
+// R u^{n-1} + dt f; R = M for backward Euler).  tm: 2 N doubles scratch.
 __device__ inline void build_rhs(const PmgD& P, const double* u, const double* ug, double scale,
                           const double* fhat, double* out, double* tm) {
-  if (P.affine)
+  if (P.expl != 0.0) {
+    if (P.affine)
+      apply_A_affine<double>(P.n, P.p, P.bM64, P.bK64, P.bR64, P.bcR64, u, ug,
+                             (const double*)nullptr, out, tm, tm + P.N, (double*)nullptr);
+    else
+      apply_stencil<double>(P.n, P.w, P.sR64, u, ug, (const double*)nullptr, out, (double*)nullptr);
+  } else if (P.affine) {
     apply_A_affine<double>(P.n, P.p, P.bM64, (const double*)nullptr, P.bM64,
                            (const double*)nullptr, u, ug, (const double*)nullptr, out, tm,
                            (double*)nullptr, (double*)nullptr);
-  else
+  } else {
     apply_stencil<double>(P.n, P.w, P.sM64, u, ug, (const double*)nullptr, out, (double*)nullptr);
+  }
   if (fhat && scale != 0.0) {
     IGM_FOR_CTA(i, P.N) out[i] += scale * fhat[i];
     __syncthreads();

@@ -1,0 +1,94 @@
+"""GPU parity of the method variants: the theta-scheme of Sec. 2 Eq. (los)
+(Crank-Nicolson, forward Euler beside backward Euler) and the MGRIT F- and
+W-cycles named in Sec. 5, against the CPU oracle on the same inputs."""
+import numpy as np
+import pytest
+
+from oracle import assembly, geometry, mgrit, timestep
+
+pytestmark = pytest.mark.gpu
+
+S = lambda xi, eta, x, y: np.sin(np.pi * x) * np.sin(np.pi * y)
+C = lambda t: 2 * np.pi ** 2 * np.cos(t) - np.sin(t)
+
+
+@pytest.fixture(scope="module")
+def B():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_2107_05337_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def _gpu(B, p, nel, T, Nt, check=True, geom="unit_square", **opts):
+    prob = B.Problem(p, nel, geom)
+    u0, fhat = prob.project(S), prob.load_vector(S)
+    fc = np.array([C(n * T / Nt) for n in range(Nt + 1)])
+    U, st, status = B.mgrit_solve(prob, u0, fhat, fc, T=T, Nt=Nt, check=check, **opts)
+    return U.cpu().numpy(), st
+
+
+@pytest.mark.parametrize("cycle", ["V", "F", "W"])
+@pytest.mark.parametrize("theta", [1.0, 0.5])
+def test_fixed_iterations_match_oracle(B, theta, cycle):
+    """k MGRIT iterations (FP64 form, tight spatial tolerance) with four time
+    levels: the GPU iterate and residual history equal the oracle's."""
+    p, nel, T, Nt, m = 2, 8, 1.0, 128, 4
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    u0, fhat = d.project(S), d.load_vector(S)
+    for k in (1, 2):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, T, Nt, m, mgrit.direct_factory(d.M, d.K), u0, fhat, C,
+                         theta=theta, cycle=cycle)
+        Uo, it, hist = mg.run(tol=0.0, max_iter=k)
+        assert len(mg.sizes) == 4
+        U, st = _gpu(B, p, nel, T, Nt, check=False, m=m, tol=0.0, max_iter=k, theta=theta,
+                     cycle=cycle, pmg=dict(tol=1e-14, precision=0, max_cycles=60))
+        assert st["iters"] == k and st["levels"] == 4
+        assert _rel(U, Uo) < 1e-10, (theta, cycle, k)
+        np.testing.assert_allclose(st["res_hist"], hist, rtol=1e-8)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("cycle", ["V", "F"])
+def test_crank_nicolson_converges_to_sequential(B, precision, cycle):
+    """Converged MGRIT with Crank-Nicolson steps equals sequential CN stepping."""
+    p, nel, T, Nt = 3, 16, 1.0, 64
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C, theta=0.5)
+    U, st = _gpu(B, p, nel, T, Nt, m=4, tol=1e-12, max_iter=60, theta=0.5, cycle=cycle,
+                 pmg=dict(tol=1e-13, precision=precision))
+    assert st["levels"] == 3
+    assert _rel(U, seq) < 1e-10, st
+
+
+def test_forward_euler_converges_to_sequential(B):
+    """Forward Euler (theta = 0: every step is a mass-matrix solve) on steps
+    small enough for the coarse propagator to be stable too."""
+    p, nel, T, Nt = 2, 8, 8e-4, 32
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C, theta=0.0)
+    U, st = _gpu(B, p, nel, T, Nt, m=4, max_levels=2, tol=1e-12, max_iter=40, theta=0.0,
+                 pmg=dict(tol=1e-13, precision=0))
+    assert _rel(U, seq) < 1e-10, st
+
+
+def test_curved_theta_rhs(B):
+    """The explicit part of the step on the curved map (stencil path)."""
+    p, nel, T, Nt = 2, 8, 0.5, 32
+    d = assembly.Discretisation(p, nel, geometry.QuarterAnnulus())
+    seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C, theta=0.5)
+    U, st = _gpu(B, p, nel, T, Nt, geom="quarter_annulus", m=4, tol=1e-12, max_iter=60,
+                 theta=0.5, pmg=dict(tol=1e-13, precision=0))
+    assert _rel(U, seq) < 1e-10, st
+
+
+def test_invalid_variant_options_rejected(B):
+    prob = B.Problem(2, 8)
+    for bad in (dict(theta=1.5), dict(theta=-0.1), dict(cycle=3)):
+        with pytest.raises(B.IgmError):
+            B.MGRIT(prob, T=1.0, Nt=16, **bad)
