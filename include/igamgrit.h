@@ -110,6 +110,10 @@ typedef struct {
   double tol;             /* spatial stop: ||b - A x||_2 <= tol ||b||_2 (default 1e-10) */
   int max_cycles;         /* cycle limit of one spatial solve (default 50) */
   int trace;              /* 1: accumulate SM clock cycles per solver phase (pmg_trace) */
+  int solver;             /* 0: p-multigrid cycles (default); 1: conjugate gradients with a
+                             diagonal preconditioner (the comparison solver of Sec. 5), always
+                             in FP64 (precision is set to 0), one "cycle" = one CG iteration,
+                             max_cycles = the iteration limit */
 } pmg_opts;
 
 typedef struct pmg_handle pmg_handle;

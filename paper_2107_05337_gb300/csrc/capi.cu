@@ -309,6 +309,7 @@ extern "C" void pmg_default_opts(pmg_opts* o) {
   o->tol = 1e-10;
   o->max_cycles = 50;
   o->trace = 0;
+  o->solver = 0;
 }
 
 static void gen_wcycle(int k, int last, std::vector<int>& ops) {
@@ -496,6 +497,8 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   if (o.inner_cycles < 1) return fail(IGM_ERR_ARG, "inner_cycles must be >= 1");
   if (o.max_cycles < 1) return fail(IGM_ERR_ARG, "max_cycles must be >= 1");
   if (!(o.tol >= 0.0)) return fail(IGM_ERR_ARG, "tol must be >= 0");
+  if (o.solver != 0 && o.solver != 1) return fail(IGM_ERR_ARG, "solver must be 0 or 1");
+  if (o.solver == 1) h->opts.precision = 0;  // CG runs in FP64
   h->c = kappa_dt;
   const Discretisation& hi = ops->hi;
   const Discretisation& lo = ops->lo;
@@ -543,6 +546,17 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   d.sA64 = up.put(A.val);
   d.sA32 = up.put32(A.val);
   d.sM64 = ops->sM64;
+  d.solver = o.solver;
+  if (o.solver == 1) {
+    const int S = (2 * p + 1) * (2 * p + 1);
+    std::vector<double> dinv(N);
+    for (int i = 0; i < N; ++i) {
+      const double a = A.val[(size_t)i * S + S / 2];
+      if (!(a > 0.0)) return fail(IGM_ERR_NUMERIC, "non-positive diagonal for CG");
+      dinv[i] = 1.0 / a;
+    }
+    d.dinv64 = up.put(dinv);
+  }
   d.expl = expl_dt;
   if (expl_dt != 0.0) {
     Stencil R = hi.M;
@@ -660,7 +674,8 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
     d.h[k].ot = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
   }
   d.o_tr = d.o_u + hsum;
-  off += std::max(align4(2 * N) + align4(N), hsum + align4(n * lo.n));
+  off += std::max(std::max(align4(2 * N) + align4(N), hsum + align4(n * lo.n)),
+                  o.solver == 1 ? 4 * align4(N) : 0);  // CG: p, q and two operator temporaries
   h->arena_bytes = (long)off * es;
   d.arena_bytes = h->arena_bytes;
   if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));

@@ -58,6 +58,9 @@ struct PmgD {
   // bcR = -expl M1; curved stencil sR
   double expl;
   const double *bR64, *bcR64, *sR64;
+  // spatial solver: 0 p-multigrid, 1 diagonally preconditioned CG (dinv = 1 / diag A)
+  int solver;
+  const double* dinv64;
   // curved operator: stencils [N][(2p+1)^2]
   const double *sA64, *sM64;
   const float* sA32;

@@ -229,6 +229,67 @@ __device__ __forceinline__ double block_dot(const double* a, int N, double* red)
   return block_sum(s, red);
 }
 
+// Conjugate gradients with the preconditioner D^-1 = diag(A)^-1 on A x = b
+// in FP64 (the comparison solver of Sec. 5), warm start x, on the FP64
+// arena: r at o_t; p, q and the operator's two temporaries at o_u.
+// ncycles > 0: exactly ncycles iterations; else iterate until
+// ||b - A x|| <= tol ||b|| or max_cycles.  Returns the iterations done.
+__device__ inline int cg_solve(const PmgD& P, const double* b, double* x, double* A, double* red,
+                               double nb2, int ncycles, int* status) {
+  const int N = P.N;
+  double* r = A + P.o_t;
+  double* pv = A + P.o_u;
+  double* q = pv + N;
+  double* tm = q + N;
+  double* tk = tm + N;
+  const double tol2 = P.tol * P.tol * nb2;
+  double rr = residual64<double>(P, b, x, r, tm, tk, red);
+  if (ncycles == 0 && rr <= tol2) return 0;
+  double rz = 0.0;
+  IGM_FOR_CTA(i, N) {
+    const double z = P.dinv64[i] * r[i];
+    pv[i] = z;
+    rz += r[i] * z;
+  }
+  rz = block_sum(rz, red);
+  int it = 0;
+  while (true) {
+    if (P.affine)
+      apply_A_affine<double>(P.n, P.p, P.bM64, P.bK64, P.bA64, P.bcM64, pv, (const double*)nullptr,
+                             (const double*)nullptr, q, tm, tk, (double*)nullptr);
+    else
+      apply_stencil<double>(P.n, P.w, P.sA64, pv, (const double*)nullptr, (const double*)nullptr,
+                            q, (double*)nullptr);
+    double pq = 0.0;
+    IGM_FOR_CTA(i, N) pq += pv[i] * q[i];
+    pq = block_sum(pq, red);
+    const double alpha = rz / pq;
+    double rr2 = 0.0, rz2 = 0.0;
+    IGM_FOR_CTA(i, N) {
+      x[i] += alpha * pv[i];
+      const double ri = r[i] - alpha * q[i];
+      r[i] = ri;
+      rr2 += ri * ri;
+      rz2 += ri * P.dinv64[i] * ri;
+    }
+    rr2 = block_sum(rr2, red);
+    rz2 = block_sum(rz2, red);
+    ++it;
+    if (!(rr2 == rr2)) { record_status(status, ST_NUMERIC); break; }
+    if (ncycles > 0) {
+      if (it >= ncycles) break;
+    } else {
+      if (rr2 <= tol2) break;
+      if (it >= P.max_cycles) { record_status(status, ST_NOT_CONVERGED); break; }
+    }
+    const double beta = rz2 / rz;
+    rz = rz2;
+    IGM_FOR_CTA(i, N) pv[i] = P.dinv64[i] * r[i] + beta * pv[i];
+    __syncthreads();
+  }
+  return it;
+}
+
 // Spatial solve of A x = b (b, x FP64 in global memory), warm start x.
 // ncycles > 0: exactly ncycles cycles; else cycle until
 // ||b - A x|| <= tol ||b|| (checked before each cycle) or max_cycles.
@@ -246,6 +307,8 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
     __syncthreads();
     return 0;
   }
+  if (PREC == 0 && P.solver == 1)
+    return cg_solve(P, b, x, (double*)arena, red, nb2, ncycles, status);
   const double tol2 = P.tol * P.tol * nb2;
   int cyc = 0;
   if (PREC == 0) {

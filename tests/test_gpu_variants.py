@@ -92,3 +92,57 @@ def test_invalid_variant_options_rejected(B):
     for bad in (dict(theta=1.5), dict(theta=-0.1), dict(cycle=3)):
         with pytest.raises(B.IgmError):
             B.MGRIT(prob, T=1.0, Nt=16, **bad)
+
+
+def _cuda(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+@pytest.mark.parametrize("geom", ["unit_square", "quarter_annulus"])
+def test_cg_fixed_iterations_match_oracle(B, geom):
+    """k iterations of the diagonally preconditioned CG (pmg_opts.solver = 1)
+    from a random start equal the oracle's PCG iterates (several columns)."""
+    from oracle import cg
+    p, nel, c = 3, 16, 1.0 / 256
+    d = assembly.Discretisation(p, nel, geometry.get(geom))
+    A = (d.M + c * d.K).tocsr()
+    rng = np.random.default_rng(11)
+    b = rng.standard_normal((3, d.N))
+    x0 = rng.standard_normal((3, d.N))
+    prob = B.Problem(p, nel, geom)
+    g = B.PMG(prob, c, solver=1, precision=1)   # CG always runs in FP64
+    for k in (1, 5, 20):
+        X = _cuda(x0)
+        cyc, _ = g.solve(_cuda(b), X, ncycles=k, check=False)
+        assert list(cyc) == [k] * 3
+        for j in range(3):
+            want, _ = cg.pcg_jacobi(A, b[j], x0[j], niter=k)
+            assert _rel(X[j].cpu().numpy(), want) < 1e-9, (k, j)
+
+
+def test_cg_converged_vs_direct_and_iterations_grow_with_p(B):
+    from scipy.sparse.linalg import spsolve
+    its = []
+    for p in (2, 3, 4, 5):
+        d = assembly.Discretisation(p, 16, geometry.UnitSquare())
+        A = (d.M + d.K / 256.0).tocsc()
+        b = d.load_vector(lambda xi, eta, x, y: np.ones_like(x))
+        g = B.PMG(B.Problem(p, 16), 1.0 / 256, solver=1, tol=1e-12, max_cycles=5000)
+        X = _cuda(np.zeros((1, d.N)))
+        cyc, _ = g.solve(_cuda(b[None, :]), X)
+        assert _rel(X[0].cpu().numpy(), spsolve(A, b)) < 1e-10
+        its.append(int(cyc[0]))
+    assert all(b > a for a, b in zip(its, its[1:])), its
+
+
+def test_mgrit_with_cg_spatial_solves(B):
+    """MGRIT whose every step is solved by CG reaches sequential backward Euler."""
+    p, nel, T, Nt = 3, 16, 1.0, 64
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C)
+    U, st = _gpu(B, p, nel, T, Nt, m=4, tol=1e-12, max_iter=60,
+                 pmg=dict(solver=1, tol=1e-13, max_cycles=5000))
+    assert st["levels"] == 3
+    assert _rel(U, seq) < 1e-10, st
+    assert st["vcyc_mean"] > 5   # CG iterations per solve, not p-multigrid cycles
