@@ -250,6 +250,24 @@ void mgrit_destroy(mgrit_handle* mg);
 igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double* fhat, const double* fcoef,
                      double* U, mgrit_stats* stats, igm_stream s);
 
+/* Run nprob independent MGRIT solves (each as mgrit_run on its own handle,
+ * with its own problem size, order, time grid and kappa) concurrently: every
+ * handle works on its own internal stream, replaying its iteration graphs,
+ * and one host thread advances whichever problem's fine-level relaxation has
+ * finished (the stopping test of Sec. 3 needs one norm read-back per
+ * iteration).  Arrays of length nprob: mgs (distinct handles), u0, U (DEVICE
+ * pointers as in mgrit_run), fhat and fcoef (either array pointer may be NULL
+ * for no sources; entries as in mgrit_run), stats (HOST, may be NULL),
+ * latency_ms (HOST, may be NULL): per problem the time from the start of the
+ * batch on stream s to the end of that problem's solve, measured with CUDA
+ * events (-1 for a problem that failed).  All problems run to the end;
+ * returns the first non-OK status in problem order.  There is no counterpart
+ * in the paper: it schedules several of the paper's solves on one GPU. */
+igm_status mgrit_run_batched(int nprob, mgrit_handle* const* mgs, const double* const* u0,
+                             const double* const* fhat, const double* const* fcoef,
+                             double* const* U, mgrit_stats* stats, float* latency_ms,
+                             igm_stream s);
+
 /* One-shot convenience: mgrit_create + mgrit_run + mgrit_destroy. */
 igm_status mgrit_solve(const iga_ops* ops, const mgrit_opts* opts, const double* u0,
                        const double* fhat, const double* fcoef, double* U, mgrit_stats* stats,

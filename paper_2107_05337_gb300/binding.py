@@ -72,6 +72,9 @@ EXPORTS = {
     "mgrit_destroy": (None, [c_void_p]),
     "mgrit_run": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p,
                           POINTER(MgritStats), c_void_p]),
+    "mgrit_run_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                                  POINTER(c_void_p), POINTER(c_void_p), c_void_p,
+                                  POINTER(ctypes.c_float), c_void_p]),
     "mgrit_solve": (c_int, [c_void_p, POINTER(MgritOpts), c_void_p, c_void_p, POINTER(c_double),
                             c_void_p, POINTER(MgritStats), c_void_p]),
     "mgrit_profile": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -345,6 +348,34 @@ class MGRIT:
         k = cnt.value
         return dict(level=np.array(lv[:k]), grid=np.array(gr[:k]), mode=np.array(md[:k]),
                     ms=np.array(ms[:k], dtype=np.float64), cycles=np.array(cy[:k]))
+
+
+def mgrit_run_batched(handles, u0s, fhats=None, fcoefs=None, Us=None, check=True):
+    """Concurrent MGRIT solves of independent problems (mgrit_run_batched).
+    handles: MGRIT objects; u0s, fhats: CUDA float64 [N_i] (fhats entries may
+    be None); fcoefs: host arrays [Nt_i+1] or None.  Returns (Us, stats list,
+    latencies in ms, status)."""
+    torch = _torch()
+    k = len(handles)
+    if Us is None:
+        Us = [torch.empty((h.Nt + 1, h.problem.N), dtype=torch.float64, device="cuda")
+              for h in handles]
+    arr = lambda xs: (c_void_p * k)(*[x if isinstance(x, int) or x is None else x for x in xs])
+    hs = arr([h.h.value for h in handles])
+    u0p = arr([u.data_ptr() for u in u0s])
+    Up = arr([U.data_ptr() for U in Us])
+    fh = None if fhats is None else arr([None if f is None else f.data_ptr() for f in fhats])
+    keep = None
+    fc = None
+    if fcoefs is not None:
+        keep = [None if f is None else np.ascontiguousarray(f, dtype=np.float64) for f in fcoefs]
+        fc = arr([None if f is None else f.ctypes.data for f in keep])
+    st = (MgritStats * k)()
+    lat = (ctypes.c_float * k)()
+    status = lib().mgrit_run_batched(k, hs, u0p, fh, fc, Up, st, lat, _stream())
+    if check:
+        _check(status)
+    return Us, [_stats(x) for x in st], np.array(lat[:], dtype=np.float64), status
 
 
 def mgrit_solve(problem, u0, fhat=None, fcoef=None, U=None, check=True, **opts):

@@ -11,6 +11,7 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/igamgrit.h"
@@ -979,7 +980,21 @@ struct mgrit_handle {
   std::vector<unsigned long long> prof_cyc;  // counter snapshots after each launch
   unsigned long long* dlog = nullptr;
   int dlog_cap = 0;
+  // state of the run in progress (mgrit_run, mgrit_run_batched)
+  struct Run {
+    double* U = nullptr;
+    const double* fhat = nullptr;
+    cudaStream_t user = nullptr;
+    bool profile = false, graphs = false, done = false;
+    int it = 0;
+    std::vector<double> hist;
+    long launches0 = 0;
+    std::chrono::steady_clock::time_point t0;
+    igm_status status = IGM_OK;
+    cudaEvent_t evA = nullptr;      // completion of the fine-level part of an iteration
+  } run;
   ~mgrit_handle() {
+    if (run.evA) cudaEventDestroy(run.evA);
     if (gA) cudaGraphExecDestroy(gA);
     if (gB) cudaGraphExecDestroy(gB);
     for (auto& r : prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -1190,33 +1205,67 @@ static igm_status capture(mgrit_handle* mg, bool partA, double* U, const double*
   return IGM_OK;
 }
 
-extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double* fhat,
-                                const double* fcoef, double* U, mgrit_stats* stats, igm_stream s) {
+// Launch the fine-level part of iteration it (relaxation, residual, norms to
+// the host) and record run.evA after it.
+static igm_status launch_A(mgrit_handle* mg) {
+  auto& R = mg->run;
+  cudaStream_t st = mg->own;
+  double* U = R.U;
+  const double* fhat = R.fhat;
+  const bool profile = R.profile;
+  if (R.graphs && R.it > 0) {
+    if (!mg->gA) {
+      igm_status r = capture(mg, true, U, fhat, st, &mg->gA);
+      if (r != IGM_OK) return r;
+    }
+    CU(cudaGraphLaunch(mg->gA, st));
+    g_launches += (mg->o.relax == 1) ? 2 : 1;
+  } else {
+    igm_status r = part_A(mg, R.it == 0, U, fhat, st, profile);
+    if (r != IGM_OK) return r;
+  }
+  CU(cudaEventRecord(R.evA, st));
+  return IGM_OK;
+}
+
+// Start a run: ordering after the caller's stream, the source factors, the
+// initial guess, and the first fine-level part (or the whole sequential
+// solve for a single time level).
+static igm_status run_begin(mgrit_handle* mg, const double* u0, const double* fhat,
+                            const double* fcoef, double* U, cudaStream_t user) {
   if (!mg || !u0 || !U) return fail(IGM_ERR_ARG, "null argument");
   const mgrit_opts& o = mg->o;
-  cudaStream_t user = (cudaStream_t)s;
+  auto& R = mg->run;
   cudaStream_t st = mg->own;
+  if (!R.evA) CU(cudaEventCreateWithFlags(&R.evA, cudaEventDisableTiming));
   CU(cudaEventRecord(mg->ev_in, user));
   CU(cudaStreamWaitEvent(st, mg->ev_in, 0));
   const int N = mg->ops->hi.N;
   const int nlev = (int)mg->L.size();
-  const bool profile = o.profile != 0;
-  const bool use_graphs = o.graphs != 0 && !profile && nlev > 1;
   if (fhat && !fcoef) return fail(IGM_ERR_ARG, "fhat given without fcoef");
   if (!fcoef) fhat = nullptr;
-  const long launches0 = g_launches.load();
+  R.U = U;
+  R.fhat = fhat;
+  R.user = user;
+  R.profile = o.profile != 0;
+  R.graphs = o.graphs != 0 && !R.profile && nlev > 1;
+  R.done = false;
+  R.it = 0;
+  R.hist.clear();
+  R.status = IGM_OK;
+  R.launches0 = g_launches.load();
   if (fhat)
     CU(cudaMemcpyAsync(mg->dfcoef, fcoef, sizeof(double) * (o.Nt + 1), cudaMemcpyHostToDevice, st));
   CU(cudaMemsetAsync(mg->counters, 0, 2 * sizeof(unsigned long long), st));
   CU(cudaMemsetAsync(mg->status, 0, sizeof(int), st));
   for (auto& r : mg->prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
   mg->prof.clear();
-  if (profile && !mg->dlog) {
+  if (R.profile && !mg->dlog) {
     mg->dlog_cap = 4096;
     mg->dlog = (unsigned long long*)mg->up.raw(sizeof(unsigned long long) * 2 * mg->dlog_cap);
     if (mg->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(mg->up.err));
   }
-  if (use_graphs && (mg->g_U != U || mg->g_fhat != fhat)) {
+  if (R.graphs && (mg->g_U != U || mg->g_fhat != fhat)) {
     if (mg->gA) cudaGraphExecDestroy(mg->gA);
     if (mg->gB) cudaGraphExecDestroy(mg->gB);
     mg->gA = mg->gB = nullptr;
@@ -1224,84 +1273,175 @@ extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double
   // initial guess: U[0] = u0, U[n>=1] = 0 unless the caller's U is to be kept
   CU(cudaMemcpyAsync(U, u0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
   if (!o.initial_guess) CU(cudaMemsetAsync(U + N, 0, sizeof(double) * (size_t)o.Nt * N, st));
-  auto t0 = std::chrono::steady_clock::now();
-  std::vector<double> hist;
-  int it = 0;
+  R.t0 = std::chrono::steady_clock::now();
   if (nlev == 1) {
+    const bool profile = R.profile;
     SWEEP(0, MODE_SEQ, 1, nullptr);
-  } else {
-    const int nint0 = mg->L[0].Nl / o.m;
-    while (true) {
-      if (use_graphs && it > 0) {
-        if (!mg->gA) {
-          igm_status r = capture(mg, true, U, fhat, st, &mg->gA);
-          if (r != IGM_OK) return r;
-        }
-        CU(cudaGraphLaunch(mg->gA, st));
-        g_launches += (o.relax == 1) ? 2 : 1;
-      } else {
-        igm_status r = part_A(mg, it == 0, U, fhat, st, profile);
-        if (r != IGM_OK) return r;
-      }
-      CU(cudaStreamSynchronize(st));
-      double rr = 0.0;
-      for (int j = 0; j < nint0; ++j) rr += mg->hnorms[j];
-      const double rho = std::sqrt(rr);
-      hist.push_back(rho);
-      if (!(rho == rho)) return fail(IGM_ERR_NUMERIC, "NaN in the MGRIT residual");
-      if (rho == 0.0 || rho <= o.tol * hist[0] || it >= o.max_iter) break;
-      if (use_graphs) {
-        if (!mg->gB) {
-          igm_status r = capture(mg, false, U, fhat, st, &mg->gB);
-          if (r != IGM_OK) return r;
-        }
-        CU(cudaGraphLaunch(mg->gB, st));
-        int nb = 0;
-        for (int l = 1; l < nlev; ++l)
-          nb += (l == nlev - 1) ? 1 : (o.relax == 1 ? 3 : 1);
-        g_launches += nb + (nlev - 1);
-      } else {
-        igm_status r = part_B(mg, U, fhat, st, profile);
-        if (r != IGM_OK) return r;
-      }
-      ++it;
-    }
-    if (use_graphs) {
+    R.done = true;
+    return IGM_OK;
+  }
+  return launch_A(mg);
+}
+
+// After the fine-level part of an iteration has completed (run.evA): the
+// stopping test on the C-point residual norms, then either the end of the
+// run or the coarse levels, the correction and the next fine-level part.
+static igm_status run_advance(mgrit_handle* mg) {
+  const mgrit_opts& o = mg->o;
+  auto& R = mg->run;
+  cudaStream_t st = mg->own;
+  double* U = R.U;
+  const double* fhat = R.fhat;
+  const bool profile = R.profile;
+  const int nlev = (int)mg->L.size();
+  const int nint0 = mg->L[0].Nl / o.m;
+  double rr = 0.0;
+  for (int j = 0; j < nint0; ++j) rr += mg->hnorms[j];
+  const double rho = std::sqrt(rr);
+  R.hist.push_back(rho);
+  if (!(rho == rho)) return fail(IGM_ERR_NUMERIC, "NaN in the MGRIT residual");
+  if (rho == 0.0 || rho <= o.tol * R.hist[0] || R.it >= o.max_iter) {
+    R.done = true;
+    if (R.graphs) {
       mg->g_U = U;
       mg->g_fhat = fhat;
     }
+    return IGM_OK;
   }
+  if (R.graphs) {
+    if (!mg->gB) {
+      igm_status r = capture(mg, false, U, fhat, st, &mg->gB);
+      if (r != IGM_OK) return r;
+    }
+    CU(cudaGraphLaunch(mg->gB, st));
+    int nb = 0;
+    for (int l = 1; l < nlev; ++l) nb += (l == nlev - 1) ? 1 : (o.relax == 1 ? 3 : 1);
+    g_launches += nb + (nlev - 1);
+  } else {
+    igm_status r = part_B(mg, U, fhat, st, profile);
+    if (r != IGM_OK) return r;
+  }
+  ++R.it;
+  return launch_A(mg);
+}
+
+// End of a run: order the caller's stream after it, collect the counters and
+// fill stats; the status reflects spatial-solve failures and convergence.
+static igm_status run_finish(mgrit_handle* mg, mgrit_stats* stats) {
+  const mgrit_opts& o = mg->o;
+  auto& R = mg->run;
+  cudaStream_t st = mg->own;
+  const int nlev = (int)mg->L.size();
   CU(cudaEventRecord(mg->ev_out, st));
-  CU(cudaStreamWaitEvent(user, mg->ev_out, 0));
+  CU(cudaStreamWaitEvent(R.user, mg->ev_out, 0));
   CU(cudaStreamSynchronize(st));
   auto t1 = std::chrono::steady_clock::now();
   unsigned long long hc[2] = {0, 0};
   int hstat = 0;
   CU(cudaMemcpy(hc, mg->counters, sizeof(hc), cudaMemcpyDeviceToHost));
   CU(cudaMemcpy(&hstat, mg->status, sizeof(int), cudaMemcpyDeviceToHost));
-  if (profile) {
+  if (R.profile) {
     const int k = std::min((int)mg->prof.size(), mg->dlog_cap);
     mg->prof_cyc.assign(2 * (size_t)k, 0);
     if (k) CU(cudaMemcpy(mg->prof_cyc.data(), mg->dlog, sizeof(unsigned long long) * 2 * k,
                          cudaMemcpyDeviceToHost));
   }
+  const auto& hist = R.hist;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->iters = it;
+    stats->iters = R.it;
     stats->levels = nlev;
     for (size_t k = 0; k < hist.size() && k < 256; ++k) stats->res_hist[k] = hist[k];
     stats->solves = (long)hc[0];
     stats->vcycles = (long)hc[1];
     stats->vcyc_mean = hc[0] ? (double)hc[1] / (double)hc[0] : 0.0;
-    stats->seconds = std::chrono::duration<double>(t1 - t0).count();
+    stats->seconds = std::chrono::duration<double>(t1 - R.t0).count();
     stats->setup_seconds = mg->setup_seconds;
-    stats->launches = g_launches.load() - launches0;
+    stats->launches = g_launches.load() - R.launches0;
   }
   if (hstat == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
   if (hstat == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "a spatial solve hit max_cycles");
   if (nlev > 1 && !hist.empty() && !(hist.back() <= o.tol * hist[0]) && hist.back() != 0.0)
     return fail(IGM_ERR_NOT_CONVERGED, "MGRIT hit max_iter");
   return IGM_OK;
+}
+
+extern "C" igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double* fhat,
+                                const double* fcoef, double* U, mgrit_stats* stats, igm_stream s) {
+  igm_status r = run_begin(mg, u0, fhat, fcoef, U, (cudaStream_t)s);
+  while (r == IGM_OK && !mg->run.done) {
+    CU(cudaEventSynchronize(mg->run.evA));
+    r = run_advance(mg);
+  }
+  if (r != IGM_OK) {
+    cudaStreamSynchronize(mg->own);
+    return r;
+  }
+  return run_finish(mg, stats);
+}
+
+extern "C" igm_status mgrit_run_batched(int nprob, mgrit_handle* const* mgs,
+                                        const double* const* u0, const double* const* fhat,
+                                        const double* const* fcoef, double* const* U,
+                                        mgrit_stats* stats, float* latency_ms, igm_stream s) {
+  if (nprob < 0 || (nprob > 0 && (!mgs || !u0 || !U))) return fail(IGM_ERR_ARG, "null argument");
+  if (nprob == 0) return IGM_OK;
+  for (int i = 0; i < nprob; ++i)
+    for (int k = 0; k < i; ++k)
+      if (mgs[i] == mgs[k]) return fail(IGM_ERR_ARG, "a handle appears twice in the batch");
+  cudaStream_t user = (cudaStream_t)s;
+  cudaEvent_t start = nullptr;
+  std::vector<cudaEvent_t> ends(nprob, nullptr);
+  CU(cudaEventCreate(&start));
+  for (auto& e : ends) CU(cudaEventCreate(&e));
+  CU(cudaEventRecord(start, user));
+  std::vector<igm_status> st(nprob, IGM_OK);
+  std::vector<char> active(nprob, 1);
+  int left = nprob;
+  for (int i = 0; i < nprob; ++i) {
+    st[i] = run_begin(mgs[i], u0[i], fhat ? fhat[i] : nullptr, fcoef ? fcoef[i] : nullptr, U[i],
+                      user);
+    if (st[i] != IGM_OK || mgs[i]->run.done) {
+      if (st[i] == IGM_OK) CU(cudaEventRecord(ends[i], mgs[i]->own));
+      active[i] = 0;
+      --left;
+    }
+  }
+  // host scheduler: advance whichever problem's fine-level part has finished
+  while (left > 0) {
+    bool progressed = false;
+    for (int i = 0; i < nprob; ++i) {
+      if (!active[i]) continue;
+      const cudaError_t q = cudaEventQuery(mgs[i]->run.evA);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) {
+        st[i] = fail(IGM_ERR_CUDA, cudaGetErrorString(q));
+      } else {
+        st[i] = run_advance(mgs[i]);
+        if (st[i] == IGM_OK && mgs[i]->run.done) CU(cudaEventRecord(ends[i], mgs[i]->own));
+      }
+      progressed = true;
+      if (st[i] != IGM_OK || mgs[i]->run.done) {
+        active[i] = 0;
+        --left;
+      }
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  igm_status first = IGM_OK;
+  for (int i = 0; i < nprob; ++i) {
+    if (st[i] == IGM_OK) st[i] = run_finish(mgs[i], stats ? &stats[i] : nullptr);
+    else cudaStreamSynchronize(mgs[i]->own);
+    if (latency_ms) {
+      float ms = -1.0f;
+      if (st[i] == IGM_OK || st[i] == IGM_ERR_NOT_CONVERGED) cudaEventElapsedTime(&ms, start, ends[i]);
+      latency_ms[i] = ms;
+    }
+    if (first == IGM_OK && st[i] != IGM_OK) first = st[i];
+  }
+  cudaEventDestroy(start);
+  for (auto& e : ends) cudaEventDestroy(e);
+  return first;
 }
 
 extern "C" igm_status mgrit_profile(const mgrit_handle* mg, int cap, int* count, int* level,
