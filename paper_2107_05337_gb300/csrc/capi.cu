@@ -723,12 +723,11 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   d.ring_bytes = arena_off;
   h->arena_smem = d.arena_smem != 0;
   h->smem_bytes = d.ring_bytes + (d.arena_smem ? h->arena_bytes : 0);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t ce = set_solver_smem(optin);
-    if (ce != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(ce));
-    attr_done = true;
-  }
+  // kernel attributes once per process (handles may be set up from several threads)
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] { attr_err = set_solver_smem(optin); });
+  if (attr_err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(attr_err));
   *out = h.release();
   return IGM_OK;
 }

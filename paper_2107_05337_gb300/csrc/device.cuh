@@ -234,6 +234,21 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Maximum of one non-negative double per thread over the CTA, returned to
+// every thread.
+__device__ __forceinline__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double m = 0.0;
+  const int nw = blockDim.x >> 5;
+  for (int k = 0; k < nw; ++k) m = fmax(m, red[k]);
+  __syncthreads();
+  return m;
+}
+
 // Strided CTA loop whose trip count is the same for every thread; the bound
 // test is a predicate inside the body.  (A loop whose trip count differs
 // between the lanes of a warp needs a reconvergence point and makes the next
@@ -329,9 +344,12 @@ __device__ void sf_stage1_w(int n, const T* bM, const T* bK, const S* x, const S
   }
 }
 
+// With b: out = (b - y) * oscale and the return value is sum ((b - y) *
+// nscale)^2 (power-of-two scales keep FP32 copies and squared norms of tiny
+// residuals in range without changing any rounding).
 template <typename T, int W, typename B, typename O>
 __device__ double sf_stage2_w(int n, const T* bA, const T* bcM, const T* tm, const T* tk,
-                              const B* b, O* out) {
+                              const B* b, O* out, double oscale = 1.0, double nscale = 1.0) {
   constexpr int p = (W - 1) / 2;
   const int R = blockDim.x / n;
   double acc = 0.0;
@@ -359,8 +377,9 @@ __device__ double sf_stage2_w(int n, const T* bA, const T* bcM, const T* tm, con
     const int i = iy * n + ix;
     if (b) {
       const T r = (T)b[i] - y;
-      out[i] = (O)r;
-      acc += (double)r * (double)r;
+      out[i] = (O)((double)r * oscale);
+      const double rs = (double)r * nscale;
+      acc += rs * rs;
     } else {
       out[i] = (O)y;
     }
@@ -371,10 +390,10 @@ __device__ double sf_stage2_w(int n, const T* bA, const T* bcM, const T* tm, con
 template <typename T, int W, typename S, typename B, typename O>
 __device__ double apply_A_affine_w(int n, const T* bM, const T* bK, const T* bA, const T* bcM,
                                    const S* x, const S* x2, const B* b, O* out, T* tm, T* tk,
-                                   double* red) {
+                                   double* red, double oscale = 1.0, double nscale = 1.0) {
   sf_stage1_w<T, W>(n, bM, bK, x, x2, tm, tk);
   __syncthreads();
-  const double acc = sf_stage2_w<T, W>(n, bA, bcM, tm, tk, b, out);
+  const double acc = sf_stage2_w<T, W>(n, bA, bcM, tm, tk, b, out, oscale, nscale);
   if (b && red) return block_sum(acc, red);
   __syncthreads();
   return 0.0;
@@ -383,22 +402,23 @@ __device__ double apply_A_affine_w(int n, const T* bM, const T* bK, const T* bA,
 template <typename T, typename S, typename B, typename O>
 __device__ double apply_A_affine(int n, int p, const T* bM, const T* bK, const T* bA,
                                  const T* bcM, const S* x, const S* x2, const B* b, O* out, T* tm,
-                                 T* tk, double* red) {
+                                 T* tk, double* red, double oscale = 1.0,
+                                 double nscale = 1.0) {
   switch (p) {
-    case 2: return apply_A_affine_w<T, 5>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
-    case 3: return apply_A_affine_w<T, 7>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
-    case 4: return apply_A_affine_w<T, 9>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
-    case 5: return apply_A_affine_w<T, 11>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
-    case 6: return apply_A_affine_w<T, 13>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
-    case 7: return apply_A_affine_w<T, 15>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
-    default: return apply_A_affine_w<T, 17>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red);
+    case 2: return apply_A_affine_w<T, 5>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
+    case 3: return apply_A_affine_w<T, 7>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
+    case 4: return apply_A_affine_w<T, 9>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
+    case 5: return apply_A_affine_w<T, 11>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
+    case 6: return apply_A_affine_w<T, 13>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
+    case 7: return apply_A_affine_w<T, 15>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
+    default: return apply_A_affine_w<T, 17>(n, bM, bK, bA, bcM, x, x2, b, out, tm, tk, red, oscale, nscale);
   }
 }
 
 // Curved: y = A x from the (2p+1)^2 stencil; same out/b convention.
 template <typename T, typename S, typename B, typename O>
 __device__ double apply_stencil(int n, int w, const T* sA, const S* x, const S* x2, const B* b,
-                                O* out, double* red) {
+                                O* out, double* red, double oscale = 1.0, double nscale = 1.0) {
   const int W = 2 * w + 1, N = n * n;
   double acc = 0.0;
   IGM_FOR_CTA(i, N) {
@@ -416,8 +436,9 @@ __device__ double apply_stencil(int n, int w, const T* sA, const S* x, const S* 
     }
     if (b) {
       const T r = (T)b[i] - y;
-      out[i] = (O)r;
-      acc += (double)r * (double)r;
+      out[i] = (O)((double)r * oscale);
+      const double rs = (double)r * nscale;
+      acc += rs * rs;
     } else {
       out[i] = (O)y;
     }

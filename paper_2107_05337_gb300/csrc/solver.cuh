@@ -9,15 +9,16 @@ __device__ __forceinline__ void record_status(int* status, int code) {
   if (status && threadIdx.x == 0) atomicMin(status, code);
 }
 
-// FP64 residual out = b - A x (out may be float: the mixed form's r32);
-// returns ||b - A x||_2^2 computed in FP64.
+// FP64 residual out = (b - A x) * oscale (out may be float: the mixed form's
+// r32); returns ||(b - A x) * nscale||_2^2 computed in FP64.
 template <typename O>
 __device__ double residual64(const PmgD& P, const double* b, const double* x, O* out, double* tm,
-                             double* tk, double* red) {
+                             double* tk, double* red, double oscale = 1.0, double nscale = 1.0) {
   if (P.affine)
     return apply_A_affine<double>(P.n, P.p, P.bM64, P.bK64, P.bA64, P.bcM64, x,
-                                  (const double*)nullptr, b, out, tm, tk, red);
-  return apply_stencil<double>(P.n, P.w, P.sA64, x, (const double*)nullptr, b, out, red);
+                                  (const double*)nullptr, b, out, tm, tk, red, oscale, nscale);
+  return apply_stencil<double>(P.n, P.w, P.sA64, x, (const double*)nullptr, b, out, red, oscale,
+                               nscale);
 }
 
 // t = b - A x in the smoothing precision (no norm).
@@ -235,15 +236,18 @@ __device__ __forceinline__ double block_dot(const double* a, int N, double* red)
 // ncycles > 0: exactly ncycles iterations; else iterate until
 // ||b - A x|| <= tol ||b|| or max_cycles.  Returns the iterations done.
 __device__ inline int cg_solve(const PmgD& P, const double* b, double* x, double* A, double* red,
-                               double nb2, int ncycles, int* status) {
+                               double nb2, double sc, int ncycles, int* status) {
   const int N = P.N;
   double* r = A + P.o_t;
   double* pv = A + P.o_u;
   double* q = pv + N;
   double* tm = q + N;
   double* tk = tm + N;
+  // r, p, q are carried scaled by the power of two sc (alpha and beta do
+  // not depend on it); x is updated with alpha p / sc
+  const double isc = 1.0 / sc;
   const double tol2 = P.tol * P.tol * nb2;
-  double rr = residual64<double>(P, b, x, r, tm, tk, red);
+  double rr = residual64<double>(P, b, x, r, tm, tk, red, sc, sc);
   if (ncycles == 0 && rr <= tol2) return 0;
   double rz = 0.0;
   IGM_FOR_CTA(i, N) {
@@ -266,7 +270,7 @@ __device__ inline int cg_solve(const PmgD& P, const double* b, double* x, double
     const double alpha = rz / pq;
     double rr2 = 0.0, rz2 = 0.0;
     IGM_FOR_CTA(i, N) {
-      x[i] += alpha * pv[i];
+      x[i] += alpha * pv[i] * isc;
       const double ri = r[i] - alpha * q[i];
       r[i] = ri;
       rr2 += ri * ri;
@@ -301,14 +305,26 @@ template <int PREC>
 __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, char* arena,
                          double* red, int ncycles, int* status) {
   const int N = P.N;
-  const double nb2 = block_dot(b, N, red);
-  if (nb2 == 0.0) {
+  // power of two sc with max |b| sc in [1/2, 1): norms are taken of scaled
+  // vectors and the mixed form's FP32 residual is b - A x scaled by sc, so
+  // tiny right-hand sides (decayed solutions) neither underflow in FP32 nor
+  // in the squared norms; the scaling is exact, results are unchanged
+  double bmax = 0.0;
+  IGM_FOR_CTA(i, N) bmax = fmax(bmax, fabs(b[i]));
+  bmax = block_max(bmax, red);
+  if (bmax == 0.0) {
     IGM_FOR_CTA(i, N) x[i] = 0.0;
     __syncthreads();
     return 0;
   }
+  int ex;
+  frexp(bmax, &ex);
+  const double sc = ldexp(1.0, -ex), isc = ldexp(1.0, ex);
+  double nb2 = 0.0;
+  IGM_FOR_CTA(i, N) nb2 += (b[i] * sc) * (b[i] * sc);
+  nb2 = block_sum(nb2, red);
   if (PREC == 0 && P.solver == 1)
-    return cg_solve(P, b, x, (double*)arena, red, nb2, ncycles, status);
+    return cg_solve(P, b, x, (double*)arena, red, nb2, sc, ncycles, status);
   const double tol2 = P.tol * P.tol * nb2;
   int cyc = 0;
   if (PREC == 0) {
@@ -318,7 +334,7 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
     double* tk = tm + N;
     while (true) {
       PhaseClock pc(P.trace);
-      const double rr = residual64<double>(P, b, x, t, tm, tk, red);
+      const double rr = residual64<double>(P, b, x, t, tm, tk, red, 1.0, sc);
       pc.stop(0);
       if (!(rr == rr)) { record_status(status, ST_NUMERIC); break; }
       if (ncycles > 0) {
@@ -339,7 +355,7 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
     while (true) {
       if (ncycles > 0 && cyc >= ncycles) break;
       PhaseClock pc(P.trace);
-      const double rr = residual64<float>(P, b, x, r, tm64, tk64, red);
+      const double rr = residual64<float>(P, b, x, r, tm64, tk64, red, sc, sc);
       pc.stop(0);
       if (!(rr == rr)) { record_status(status, ST_NUMERIC); break; }
       if (ncycles == 0) {
@@ -350,7 +366,7 @@ __device__ int pmg_solve(const PmgD& P, Pipe& pp, const double* b, double* x, ch
       for (int k = 0; k < P.inner && ok; ++k)
         ok = pmg_cycle<float>(P, pp, r, d, A, false, k == 0, status);
       if (!ok) break;
-      IGM_FOR_CTA(i, N) x[i] += (double)d[i];
+      IGM_FOR_CTA(i, N) x[i] += (double)d[i] * isc;
       __syncthreads();
       ++cyc;
     }

@@ -18,6 +18,7 @@ with kappa = 1, so f = (2 kappa pi^2 cos t - sin t) sin(pi x) sin(pi y).
 import numpy as np
 
 SEED_ANNULUS = 20210712
+SEED_BATCH = 20210714
 
 
 def fourier_modes(seed=SEED_ANNULUS, count=8, kmax=8):
@@ -48,4 +49,23 @@ WORKLOADS = {
                     max_levels=30, min_coarse=4, kappa=1.0, source="manufactured"),
     "annulus_c3": dict(geom="quarter_annulus", p=[4], nel=128, T=1.0, Nt=1024, m=8,
                        max_levels=30, min_coarse=4, kappa=1.0, source="none"),
+    "batch_c5": dict(members="batch_members()", source="none"),
 }
+
+
+def batch_members(seed=SEED_BATCH, count=64):
+    """The uneven multi-problem batch: ``count`` independent heat problems on the
+    unit square with h drawn from {1/32, 1/64, 1/128}, p from {2, 3, 4, 5}, N_t
+    from {128, 256, 512, 1024, 2048}, kappa log-uniform on [0.1, 10], T = 1,
+    f = 0, m = 4, and an initial condition of 16 random Fourier modes
+    (``fourier_modes`` with a per-member seed).  Returns a list of dicts."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        nel = int(rng.choice([32, 64, 128]))
+        p = int(rng.integers(2, 6))
+        Nt = int(rng.choice([128, 256, 512, 1024, 2048]))
+        kappa = float(10.0 ** rng.uniform(-1.0, 1.0))
+        modes_seed = int(rng.integers(0, 2 ** 31 - 1))
+        out.append(dict(p=p, nel=nel, Nt=Nt, kappa=kappa, T=1.0, m=4, modes_seed=modes_seed))
+    return out

@@ -146,3 +146,22 @@ def test_mgrit_with_cg_spatial_solves(B):
     assert st["levels"] == 3
     assert _rel(U, seq) < 1e-10, st
     assert st["vcyc_mean"] > 5   # CG iterations per solve, not p-multigrid cycles
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("solver", [0, 1])
+def test_tiny_right_hand_side_scales_exactly(B, precision, solver):
+    """A right-hand side 2^-200 times smaller (far below FP32's range, as a
+    decayed solution produces) gives exactly 2^-200 times the solution: the
+    solves scale by powers of two internally."""
+    import torch
+    d = assembly.Discretisation(3, 16, geometry.UnitSquare())
+    b = np.random.default_rng(4).standard_normal((2, d.N))
+    g = B.PMG(B.Problem(3, 16), 1.0 / 64, precision=precision, solver=solver, tol=1e-10,
+              max_cycles=2000)
+    X1 = torch.zeros((2, d.N), dtype=torch.float64, device="cuda")
+    X2 = torch.zeros_like(X1)
+    c1, _ = g.solve(torch.as_tensor(b, device="cuda"), X1)
+    c2, _ = g.solve(torch.as_tensor(np.ldexp(b, -200), device="cuda"), X2)
+    assert list(c1) == list(c2) and min(c1) > 0
+    np.testing.assert_array_equal(np.ldexp(X1.cpu().numpy(), -200), X2.cpu().numpy())
