@@ -72,6 +72,23 @@ def bytes_per_vcycle_dof(p, B):
     return (3 * 8 * q + 2 * 12 * q + 2 * 8 * (p + 2) ** 2) / max(B, 1) + 300.0
 
 
+def job_time_ms(local_total_ms, world, device="cpu"):
+    """Length of a timed region for the whole job: the maximum over ranks (every
+    rank's steps must have finished)."""
+    if world > 1:
+        import torch
+        t = torch.tensor([float(local_total_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+    return float(local_total_ms)
+
+
+def job_throughput(units_per_rank, world, steps, total_ms):
+    """Whole-job throughput: every rank processed units_per_rank per step (the
+    ranks run independent replicas of the workload, weak scaling)."""
+    return world * units_per_rank * steps / (total_ms * 1e-3)
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -318,15 +335,11 @@ def main():
                 torch.cuda.synchronize()
                 ms.append(e0.elapsed_time(e1))
         launches = B.kernel_launches() - l0
-        total = sum(ms)
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            total = float(t.item())
+        total = job_time_ms(sum(ms), world, "cuda")
         return total, ms, stats, ck.summary(), launches
 
     total, ms, stats, clocks, launches = timed(chosen, args.steps, args.warmup)
-    value = world * units * args.steps / (total * 1e-3)
+    value = job_throughput(units, world, args.steps, total)
 
     # plain FP64 form, same workload
     plain = None
@@ -370,7 +383,8 @@ def main():
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
     h2d = sum(2 * probs[p].N * 8 + (Nt + 1) * 8 for p in orders)
     d2h = sum(probs[p].N * 8 for p in orders)
-    e2e = {"value": world * units * len(e2e_ms) / (sum(e2e_ms) * 1e-3), "unit": UNIT,
+    e2e = {"value": job_throughput(units, world, len(e2e_ms), job_time_ms(sum(e2e_ms), world, "cuda")),
+           "unit": UNIT,
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel (k_mgrit_sweep), one profiled solve per order
