@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--sjf", type=int, default=1,
+                    help="--batch: 1 = shortest-job-first stream priorities (default), 0 = equal")
     ap.add_argument("--batch", action="store_true",
                     help="the uneven 64-problem batch (batch_c5): per-problem latency p50/p99 "
                          "and batch throughput, one JSON line (not the headline metric)")
@@ -206,9 +208,17 @@ def run_batch(args):
             a[s] * np.sin(k[s] * np.pi * xi) * np.sin(l[s] * np.pi * eta) for s in range(len(a)))
         probs.append(pr)
         u0s.append(pr.project(fn))
+    # shortest job first: members with less work (N * N_t) get higher stream
+    # priority (six levels by work rank), so small problems finish early
+    work = [pr.N * mb["Nt"] for pr, mb in zip(probs, members)]
+    order = sorted(range(len(members)), key=lambda i: work[i])
+    prio = [0] * len(members)
+    for r, i in enumerate(order):
+        prio[i] = 5 - (6 * r) // len(members) if args.sjf else 0
     t0 = time.perf_counter()
     mk = lambda i: B.MGRIT(probs[i], T=members[i]["T"], Nt=members[i]["Nt"], m=members[i]["m"],
-                           tol=1e-10, max_iter=100, pmg=dict(precision=1, tol=1e-10))
+                           tol=1e-10, max_iter=100, priority=prio[i],
+                           pmg=dict(precision=1, tol=1e-10))
     with ThreadPoolExecutor(max_workers=16) as ex:
         handles = list(ex.map(mk, range(len(members))))
     setup_s = time.perf_counter() - t0
@@ -238,6 +248,7 @@ def run_batch(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "makespan_ms": makespan, "setup_s": round(setup_s, 2),
+            "scheduling": "shortest job first (stream priorities)" if args.sjf else "equal priorities",
             "iters": {"min": int(min(iters)), "max": int(max(iters))}, "members": len(members)}
     print(json.dumps(line))
 

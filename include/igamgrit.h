@@ -214,6 +214,9 @@ typedef struct {
   double theta;    /* theta-scheme of Sec. 2, Eq. (los): 1 backward Euler (default),
                       0.5 Crank-Nicolson, 0 forward Euler; in [0, 1] */
   int cycle;       /* MGRIT hierarchy (Sec. 5): 0 V-cycle (default), 1 F-cycle, 2 W-cycle */
+  int priority;    /* scheduling priority of the handle's work against other work on the
+                      GPU: 0 normal (default), k > 0 k levels more urgent (clamped to the
+                      device's range of stream priorities) */
 } mgrit_opts;
 
 typedef struct {

@@ -38,7 +38,8 @@ class MgritOpts(ctypes.Structure):
     _fields_ = [("T", c_double), ("Nt", c_int), ("m", c_int), ("max_levels", c_int),
                 ("min_coarse", c_int), ("relax", c_int), ("tol", c_double), ("max_iter", c_int),
                 ("pmg", PmgOpts), ("initial_guess", c_int), ("graphs", c_int),
-                ("profile", c_int), ("theta", c_double), ("cycle", c_int)]
+                ("profile", c_int), ("theta", c_double), ("cycle", c_int),
+                ("priority", c_int)]
 
 
 class MgritStats(ctypes.Structure):

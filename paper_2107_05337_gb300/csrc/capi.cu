@@ -936,6 +936,7 @@ extern "C" void mgrit_default_opts(mgrit_opts* o) {
   o->profile = 0;
   o->theta = 1.0;
   o->cycle = 0;
+  o->priority = 0;
 }
 
 struct Level {
@@ -1053,7 +1054,12 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   mg->dfcoef = (double*)up.raw(sizeof(double) * (size_t)(o.Nt + 1));
   if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
   CU(cudaMallocHost(&mg->hnorms, sizeof(double) * mg->max_grid));
-  CU(cudaStreamCreateWithFlags(&mg->own, cudaStreamNonBlocking));
+  {
+    int least = 0, greatest = 0;  // greatest priority = numerically lowest
+    CU(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    const int prio = std::max(greatest, least - std::max(0, o.priority));
+    CU(cudaStreamCreateWithPriority(&mg->own, cudaStreamNonBlocking, prio));
+  }
   CU(cudaEventCreateWithFlags(&mg->ev_in, cudaEventDisableTiming));
   CU(cudaEventCreateWithFlags(&mg->ev_out, cudaEventDisableTiming));
   for (int l = 0; l < nlev; ++l) {
