@@ -217,6 +217,10 @@ typedef struct {
   int priority;    /* scheduling priority of the handle's work against other work on the
                       GPU: 0 normal (default), k > 0 k levels more urgent (clamped to the
                       device's range of stream priorities) */
+  int coarse_cycles; /* spatial solves on the coarse time levels: 0 = to pmg.tol like the
+                        fine level (default); k > 0 = exactly k p-multigrid cycles (an
+                        inexact coarse propagator; the fine level, and with it the
+                        converged answer, is unchanged) */
 } mgrit_opts;
 
 typedef struct {

@@ -210,10 +210,13 @@ def direct_factory(M, K):
     return make
 
 
-def pmg_factory(hi, lo, tol=1e-10, max_cycles=50, ncycles=0, **pmg_kw):
+def pmg_factory(hi, lo, tol=1e-10, max_cycles=50, ncycles=0, coarse_cycles=0, **pmg_kw):
+    """p-multigrid spatial solves; coarse_cycles > 0: exactly that many cycles
+    per solve on the coarse time levels (an inexact coarse propagator)."""
     from .pmg import PMG
 
     def make(level, c):
         P = PMG(hi, lo, c, **pmg_kw)
-        return lambda rhs, guess: P.solve(rhs, guess, tol=tol, max_cycles=max_cycles, ncycles=ncycles)
+        nc = coarse_cycles if (level > 0 and coarse_cycles > 0) else ncycles
+        return lambda rhs, guess: P.solve(rhs, guess, tol=tol, max_cycles=max_cycles, ncycles=nc)
     return make

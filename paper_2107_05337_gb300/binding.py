@@ -39,7 +39,7 @@ class MgritOpts(ctypes.Structure):
                 ("min_coarse", c_int), ("relax", c_int), ("tol", c_double), ("max_iter", c_int),
                 ("pmg", PmgOpts), ("initial_guess", c_int), ("graphs", c_int),
                 ("profile", c_int), ("theta", c_double), ("cycle", c_int),
-                ("priority", c_int)]
+                ("priority", c_int), ("coarse_cycles", c_int)]
 
 
 class MgritStats(ctypes.Structure):

@@ -937,6 +937,7 @@ extern "C" void mgrit_default_opts(mgrit_opts* o) {
   o->theta = 1.0;
   o->cycle = 0;
   o->priority = 0;
+  o->coarse_cycles = 0;
 }
 
 struct Level {
@@ -1015,6 +1016,7 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   if (o.relax != 0 && o.relax != 1) return fail(IGM_ERR_ARG, "relax must be 0 or 1");
   if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail(IGM_ERR_ARG, "theta must be in [0, 1]");
   if (o.cycle < 0 || o.cycle > 2) return fail(IGM_ERR_ARG, "cycle must be 0 (V), 1 (F) or 2 (W)");
+  if (o.coarse_cycles < 0) return fail(IGM_ERR_ARG, "coarse_cycles must be >= 0");
   auto t0 = std::chrono::steady_clock::now();
   auto mg = std::make_unique<mgrit_handle>();
   mg->ops = ops;
@@ -1100,7 +1102,7 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
   a.theta = mg->o.theta;
   a.scratch = mg->scratch;
   a.garena = L[l].h->garena;
-  a.ncycles = 0;
+  a.ncycles = l > 0 ? mg->o.coarse_cycles : 0;
   a.counters = mg->counters;
   a.status = mg->status;
   ProfRec rec{l, grid, mode, nullptr, nullptr};

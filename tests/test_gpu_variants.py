@@ -165,3 +165,33 @@ def test_tiny_right_hand_side_scales_exactly(B, precision, solver):
     c2, _ = g.solve(torch.as_tensor(np.ldexp(b, -200), device="cuda"), X2)
     assert list(c1) == list(c2) and min(c1) > 0
     np.testing.assert_array_equal(np.ldexp(X1.cpu().numpy(), -200), X2.cpu().numpy())
+
+
+def test_coarse_cycles_fixed_iterations_match_oracle(B):
+    """One p-multigrid cycle per coarse-level solve (FP64 form): k MGRIT
+    iterations equal the oracle's with the same inexact coarse propagator."""
+    p, nel, T, Nt, m = 2, 8, 1.0, 64, 4
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    lo = assembly.Discretisation(1, nel, geometry.UnitSquare())
+    u0, fhat = d.project(S), d.load_vector(S)
+    for k in (1, 2):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, T, Nt, m,
+                         mgrit.pmg_factory(d, lo, tol=1e-14, max_cycles=60, coarse_cycles=1),
+                         u0, fhat, C)
+        Uo, it, hist = mg.run(tol=0.0, max_iter=k)
+        U, st = _gpu(B, p, nel, T, Nt, check=False, m=m, tol=0.0, max_iter=k, coarse_cycles=1,
+                     pmg=dict(tol=1e-14, precision=0, max_cycles=60))
+        assert st["iters"] == k and st["levels"] == 3
+        assert _rel(U, Uo) < 1e-9, k
+        np.testing.assert_allclose(st["res_hist"], hist, rtol=1e-7)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_coarse_cycles_converge_to_sequential(B, precision):
+    p, nel, T, Nt = 3, 16, 1.0, 256
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C)
+    U, st = _gpu(B, p, nel, T, Nt, m=4, tol=1e-12, max_iter=60, coarse_cycles=1,
+                 pmg=dict(tol=1e-13, precision=precision))
+    assert st["levels"] == 4
+    assert _rel(U, seq) < 1e-10, st

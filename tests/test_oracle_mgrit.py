@@ -171,3 +171,23 @@ def test_f_and_w_cycles_need_no_more_iterations_than_v():
                          lambda t: 1.0, min_coarse=2, cycle=cycle)
         its[cycle] = mg.run(tol=1e-10, max_iter=50)[1]
     assert its["W"] <= its["F"] <= its["V"], its
+
+
+def test_inexact_coarse_solves_keep_the_fixed_point():
+    """One p-multigrid cycle per coarse-level solve changes the coarse
+    propagator only: the converged MGRIT solution is still sequential
+    stepping, in the same number of iterations on this problem."""
+    from oracle import assembly as asm
+    d = asm.Discretisation(2, 8, geometry.UnitSquare())
+    lo = asm.Discretisation(1, 8, geometry.UnitSquare())
+    u0, fhat = d.project(S), d.load_vector(S)
+    c = lambda t: 2 * np.pi ** 2 * np.cos(t) - np.sin(t)
+    seq = timestep.sequential(d.M, d.K, 1.0, 1.0, 64, u0, fhat, c)
+    its = []
+    for cc in (0, 1):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, 1.0, 64, 4,
+                         mgrit.pmg_factory(d, lo, tol=1e-13, coarse_cycles=cc), u0, fhat, c)
+        U, it, _ = mg.run(tol=1e-12, max_iter=40)
+        np.testing.assert_allclose(U, seq, rtol=0, atol=1e-11 * np.abs(seq).max())
+        its.append(it)
+    assert its[1] <= its[0] + 1, its
