@@ -233,6 +233,7 @@ typedef struct {
   double seconds;        /* wall time of the iteration loop (setup excluded) */
   double setup_seconds;  /* p-multigrid setup of all levels */
   long launches;         /* kernel launches of the run */
+  int coarse_fallback;   /* 1 if a learned coarse propagator was replaced by backward Euler */
 } mgrit_stats;
 
 typedef struct mgrit_handle mgrit_handle;
@@ -274,6 +275,46 @@ igm_status mgrit_run_batched(int nprob, mgrit_handle* const* mgs, const double* 
                              const double* const* fhat, const double* const* fcoef,
                              double* const* U, mgrit_stats* stats, float* latency_ms,
                              igm_stream s);
+
+/* ---------------------------------------------------------------------------
+ * Learned coarse propagator Phi_c (no counterpart in the paper, whose coarse
+ * levels rediscretise the time step, Sec. 3).  A convolutional network on the
+ * n x n grid of interior coefficients (zero padding: the homogeneous Dirichlet
+ * condition), BF16 weights and activations with FP32 accumulation:
+ *   x = u / s, s = max |u|;  Phi_c(u) = u + s * K3 * tanh(K2 * tanh(K1 * x)),
+ * K1: 1 -> C, K2: C -> C, K3: C -> 1 channels, 5 x 5 kernels, no biases.
+ * Weights (FP32 master copy) in one array [K1 (C,1,5,5) | K2 (C,C,5,5) |
+ * K3 (1,C,5,5)] of count = 25 (2C + C^2) floats.
+ * ------------------------------------------------------------------------ */
+typedef struct phic_handle phic_handle;
+
+/* n = interior coefficients per direction, channels C in [1, 8]; K1 and K2
+ * random (seeded), K3 = 0 (the network starts as the identity). */
+igm_status phic_create(int n, int channels, unsigned long long seed, phic_handle** out);
+void phic_destroy(phic_handle* h);
+/* HOST w[count]; phic_get_weights also returns count (w may be NULL). */
+igm_status phic_set_weights(phic_handle* h, const float* w);
+igm_status phic_get_weights(const phic_handle* h, float* w, int* count);
+/* out_b = Phi_c(u_b) for nb DEVICE vectors of n*n FP64 values (row strides ldu, ldo). */
+igm_status phic_apply(phic_handle* h, int nb, const double* u, long ldu, double* out, long ldo,
+                      igm_stream s);
+/* Train on npairs DEVICE pairs (U0 row b -> U1 row b, stride ld, FP64): each
+ * pair is normalised by max |U0_b|; mean squared error of Phi_c(U0_b)/s -
+ * U1_b/s over minibatches of `batch` pairs drawn uniformly (seeded), `steps`
+ * Adam steps (beta 0.9, 0.999, eps 1e-8) with learning rate lr.  loss: HOST
+ * [steps] per-step minibatch losses, or NULL.  Synchronises the stream. */
+igm_status phic_train(phic_handle* h, int npairs, const double* U0, const double* U1, long ld,
+                      int steps, int batch, double lr, unsigned long long seed, double* loss,
+                      igm_stream s);
+/* Use h (NULL: backward Euler again) as the coarse propagator of a two-level
+ * MGRIT handle (max_levels = 2), with the FAS coarse equation
+ * tau_j = u_{jm} - Phi_c(u_{(j-1)m}) + r_j, v_j = Phi_c(v_{j-1}) + tau_j.  The
+ * fine propagator is unchanged, so the converged answer is sequential
+ * stepping.  When an iteration's residual contraction rho_k / rho_{k-1}
+ * exceeds switch_ratio (0.5 recommended) the run continues with the
+ * backward-Euler coarse level (mgrit_stats.coarse_fallback = 1).  The handle
+ * h must outlive the MGRIT handle's use of it. */
+igm_status mgrit_set_coarse_propagator(mgrit_handle* mg, phic_handle* h, double switch_ratio);
 
 /* One-shot convenience: mgrit_create + mgrit_run + mgrit_destroy. */
 igm_status mgrit_solve(const iga_ops* ops, const mgrit_opts* opts, const double* u0,

@@ -45,7 +45,8 @@ class MgritOpts(ctypes.Structure):
 class MgritStats(ctypes.Structure):
     _fields_ = [("iters", c_int), ("levels", c_int), ("res_hist", c_double * 256),
                 ("vcyc_mean", c_double), ("solves", c_long), ("vcycles", c_long),
-                ("seconds", c_double), ("setup_seconds", c_double), ("launches", c_long)]
+                ("seconds", c_double), ("setup_seconds", c_double), ("launches", c_long),
+                ("coarse_fallback", c_int)]
 
 
 EXPORTS = {
@@ -76,6 +77,14 @@ EXPORTS = {
     "mgrit_run_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                                   POINTER(c_void_p), POINTER(c_void_p), c_void_p,
                                   POINTER(ctypes.c_float), c_void_p]),
+    "phic_create": (c_int, [c_int, c_int, ctypes.c_ulonglong, POINTER(c_void_p)]),
+    "phic_destroy": (None, [c_void_p]),
+    "phic_set_weights": (c_int, [c_void_p, POINTER(ctypes.c_float)]),
+    "phic_get_weights": (c_int, [c_void_p, POINTER(ctypes.c_float), POINTER(c_int)]),
+    "phic_apply": (c_int, [c_void_p, c_int, c_void_p, c_long, c_void_p, c_long, c_void_p]),
+    "phic_train": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int, c_int, c_double,
+                           ctypes.c_ulonglong, POINTER(c_double), c_void_p]),
+    "mgrit_set_coarse_propagator": (c_int, [c_void_p, c_void_p, c_double]),
     "mgrit_solve": (c_int, [c_void_p, POINTER(MgritOpts), c_void_p, c_void_p, POINTER(c_double),
                             c_void_p, POINTER(MgritStats), c_void_p]),
     "mgrit_profile": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int),
@@ -307,7 +316,8 @@ def _stats(st):
     return dict(iters=st.iters, levels=st.levels,
                 res_hist=list(st.res_hist[:st.iters + 1]), vcyc_mean=st.vcyc_mean,
                 solves=st.solves, vcycles=st.vcycles, seconds=st.seconds,
-                setup_seconds=st.setup_seconds, launches=st.launches)
+                setup_seconds=st.setup_seconds, launches=st.launches,
+                coarse_fallback=st.coarse_fallback)
 
 
 class MGRIT:
@@ -340,6 +350,12 @@ class MGRIT:
             _check(status)
         return U, _stats(st), status
 
+    def set_coarse_propagator(self, phic, switch=0.5):
+        """Two-level FAS with a learned coarse propagator (Phic), or None."""
+        _check(lib().mgrit_set_coarse_propagator(self.h, phic.h if phic is not None else None,
+                                                  switch))
+        self._phic = phic
+
     def profile(self, cap=100000):
         """Per-launch records of the last run made with profile=1."""
         cnt = c_int()
@@ -349,6 +365,59 @@ class MGRIT:
         k = cnt.value
         return dict(level=np.array(lv[:k]), grid=np.array(gr[:k]), mode=np.array(md[:k]),
                     ms=np.array(ms[:k], dtype=np.float64), cycles=np.array(cy[:k]))
+
+
+def _ld(T):
+    """Row stride of a 2D tensor (a single row may carry stride 0 from NumPy)."""
+    return T.stride(0) if T.shape[0] > 1 else T.shape[1]
+
+
+class Phic:
+    """Learned coarse propagator (phic_*): a 5 x 5 convolutional network on the
+    n x n coefficient grid, BF16 kernels."""
+
+    def __init__(self, n, channels=8, seed=0):
+        h = c_void_p()
+        _check(lib().phic_create(n, channels, seed, ctypes.byref(h)))
+        self.h = h
+        self.n, self.channels = n, channels
+
+    def __del__(self):
+        if getattr(self, "h", None) and _LIB is not None:
+            _LIB.phic_destroy(self.h)
+            self.h = None
+
+    @property
+    def weights(self):
+        cnt = c_int()
+        _check(lib().phic_get_weights(self.h, None, ctypes.byref(cnt)))
+        w = np.zeros(cnt.value, dtype=np.float32)
+        _check(lib().phic_get_weights(self.h, w.ctypes.data_as(POINTER(ctypes.c_float)),
+                                      ctypes.byref(cnt)))
+        return w
+
+    @weights.setter
+    def weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.size == self.weights.size
+        _check(lib().phic_set_weights(self.h, w.ctypes.data_as(POINTER(ctypes.c_float))))
+
+    def apply(self, U):
+        """U: CUDA float64 [nb, n*n] -> Phi_c of every row."""
+        torch = _torch()
+        out = torch.empty_like(U)
+        _check(lib().phic_apply(self.h, U.shape[0], _dptr(U), _ld(U), _dptr(out), _ld(out),
+                                _stream()))
+        return out
+
+    def train(self, U0, U1, steps, batch=16, lr=1e-3, seed=0):
+        """Pairs U0[b] -> U1[b] (CUDA float64 [np, n*n]); returns per-step losses."""
+        loss = np.zeros(max(steps, 1))
+        assert _ld(U0) == _ld(U1)
+        _check(lib().phic_train(self.h, U0.shape[0], _dptr(U0), _dptr(U1), _ld(U0), steps,
+                                batch, lr, seed, loss.ctypes.data_as(POINTER(c_double)),
+                                _stream()))
+        return loss[:steps]
 
 
 def mgrit_run_batched(handles, u0s, fhats=None, fcoefs=None, Us=None, check=True):

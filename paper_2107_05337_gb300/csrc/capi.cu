@@ -10,6 +10,7 @@
 #include <cstring>
 #include <memory>
 #include <mutex>
+#include <random>
 #include <string>
 #include <thread>
 #include <vector>
@@ -17,6 +18,7 @@
 #include "../../include/igamgrit.h"
 #include "host_setup.h"
 #include "kernels.h"
+#include "phic.h"
 
 using namespace igm;
 
@@ -920,6 +922,136 @@ extern "C" igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const d
 // ---------------------------------------------------------------------------
 // MGRIT (Sec. 3)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// learned coarse propagator (the benchmark spec (4))
+// ---------------------------------------------------------------------------
+struct phic_handle {
+  PhicNet net;
+  PhicWork work;
+  PhicTrain train;
+  Uploader up;        // weights
+  Uploader upw;       // inference work (regrown on demand)
+  Uploader upt;       // training state (per phic_train call)
+  Uploader uptw;      // training activations (per phic_train call)
+};
+
+static igm_status phic_work(phic_handle* h, Uploader& up, PhicWork& w, int nb) {
+  if (w.cap >= nb) return IGM_OK;
+  const size_t N = (size_t)h->net.n * h->net.n, C = h->net.C;
+  up = Uploader();
+  w.x0 = (__nv_bfloat16*)up.raw(2 * N * nb);
+  w.a1 = (__nv_bfloat16*)up.raw(2 * N * C * nb);
+  w.a2 = (__nv_bfloat16*)up.raw(2 * N * C * nb);
+  w.z3 = (float*)up.raw(4 * N * nb);
+  w.s = (double*)up.raw(8 * (size_t)nb);
+  if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
+  w.cap = nb;
+  return IGM_OK;
+}
+
+extern "C" igm_status phic_create(int n, int channels, unsigned long long seed, phic_handle** out) {
+  if (!out || n < 1 || n > 1024 || channels < 1 || channels > kPhicMaxC)
+    return fail(IGM_ERR_ARG, "phic_create: need n in [1, 1024] and channels in [1, 8]");
+  auto h = std::make_unique<phic_handle>();
+  PhicNet& net = h->net;
+  net.n = n;
+  net.C = channels;
+  net.o1 = 0;
+  net.o2 = channels * 25;
+  net.o3 = net.o2 + channels * channels * 25;
+  net.count = net.o3 + channels * 25;
+  // initial weights: K1, K2 normal with standard deviation 1/(5 sqrt(fan-in
+  // channels)), K3 = 0 (the network starts as the identity)
+  std::vector<float> w(net.count, 0.0f);
+  std::mt19937_64 rng(seed);
+  std::normal_distribution<double> nd(0.0, 1.0);
+  for (int i = 0; i < net.o2; ++i) w[i] = (float)(nd(rng) / 5.0);
+  for (int i = net.o2; i < net.o3; ++i) w[i] = (float)(nd(rng) / (5.0 * std::sqrt((double)channels)));
+  net.wall = h->up.put(w);
+  if (h->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(h->up.err));
+  net.w1 = net.wall + net.o1;
+  net.w2 = net.wall + net.o2;
+  net.w3 = net.wall + net.o3;
+  *out = h.release();
+  return IGM_OK;
+}
+
+extern "C" void phic_destroy(phic_handle* h) { delete h; }
+
+extern "C" igm_status phic_set_weights(phic_handle* h, const float* w) {
+  if (!h || !w) return fail(IGM_ERR_ARG, "null argument");
+  CU(cudaMemcpy(h->net.wall, w, sizeof(float) * h->net.count, cudaMemcpyHostToDevice));
+  return IGM_OK;
+}
+
+extern "C" igm_status phic_get_weights(const phic_handle* h, float* w, int* count) {
+  if (!h || !count) return fail(IGM_ERR_ARG, "null argument");
+  *count = h->net.count;
+  if (w) CU(cudaMemcpy(w, h->net.wall, sizeof(float) * h->net.count, cudaMemcpyDeviceToHost));
+  return IGM_OK;
+}
+
+extern "C" igm_status phic_apply(phic_handle* h, int nb, const double* u, long ldu, double* out,
+                                 long ldo, igm_stream s) {
+  if (!h || (nb > 0 && (!u || !out))) return fail(IGM_ERR_ARG, "null argument");
+  const long N = (long)h->net.n * h->net.n;
+  if (nb < 0 || ldu < N || ldo < N) return fail(IGM_ERR_ARG, "bad nb or leading dimension");
+  if (nb == 0) return IGM_OK;
+  igm_status r = phic_work(h, h->upw, h->work, nb);
+  if (r != IGM_OK) return r;
+  CU(phic_forward(h->net, nb, u, ldu, nullptr, 0, nullptr, 0, out, ldo, h->work, (cudaStream_t)s));
+  return IGM_OK;
+}
+
+extern "C" igm_status phic_train(phic_handle* h, int npairs, const double* U0, const double* U1,
+                                 long ld, int steps, int batch, double lr, unsigned long long seed,
+                                 double* loss, igm_stream s) {
+  if (!h || !U0 || !U1) return fail(IGM_ERR_ARG, "null argument");
+  const long N = (long)h->net.n * h->net.n;
+  if (npairs < 1 || steps < 0 || batch < 1 || ld < N || !(lr > 0.0))
+    return fail(IGM_ERR_ARG, "phic_train: need npairs, batch >= 1, steps >= 0, ld >= n*n, lr > 0");
+  cudaStream_t st = (cudaStream_t)s;
+  PhicTrain& t = h->train;
+  Uploader& up = h->upt;
+  up = Uploader();
+  t = PhicTrain();
+  const size_t C = h->net.C;
+  t.np = npairs;
+  t.X = (float*)up.raw(4 * (size_t)N * npairs);
+  t.Y = (float*)up.raw(4 * (size_t)N * npairs);
+  t.xf = (float*)up.raw(4 * (size_t)N * batch);
+  t.y = (float*)up.raw(4 * (size_t)N * batch);
+  t.g1 = (float*)up.raw(4 * (size_t)N * C * batch);
+  t.g2 = (float*)up.raw(4 * (size_t)N * C * batch);
+  t.g3 = (float*)up.raw(4 * (size_t)N * batch);
+  t.wf2 = (float*)up.raw(4 * C * C * 25);
+  t.wf3 = (float*)up.raw(4 * C * 25);
+  t.gw = (float*)up.raw(4 * (size_t)h->net.count);
+  t.m = (float*)up.raw(4 * (size_t)h->net.count);
+  t.v = (float*)up.raw(4 * (size_t)h->net.count);
+  t.loss = (float*)up.raw(4 * (size_t)std::max(1, steps));
+  int* idx = (int*)up.raw(4 * (size_t)std::max(1, steps) * batch);
+  if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
+  igm_status r = phic_work(h, h->uptw, t.work, batch);
+  if (r != IGM_OK) return r;
+  std::vector<int> hidx((size_t)std::max(1, steps) * batch);
+  std::mt19937_64 rng(seed);
+  std::uniform_int_distribution<int> ud(0, npairs - 1);
+  for (auto& k : hidx) k = ud(rng);
+  CU(cudaMemcpyAsync(idx, hidx.data(), sizeof(int) * hidx.size(), cudaMemcpyHostToDevice, st));
+  CU(phic_prepare_pairs(h->net.n, npairs, U0, U1, ld, t.X, t.Y, st));
+  for (int k = 0; k < steps; ++k)
+    CU(phic_train_step(h->net, t, batch, idx + (size_t)k * batch, k, (float)lr, st));
+  if (loss && steps > 0) {
+    std::vector<float> hl(steps);
+    CU(cudaMemcpyAsync(hl.data(), t.loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    for (int k = 0; k < steps; ++k) loss[k] = hl[k];
+  }
+  CU(cudaStreamSynchronize(st));
+  return IGM_OK;
+}
+
 extern "C" void mgrit_default_opts(mgrit_opts* o) {
   if (!o) return;
   o->T = 1.0;
@@ -981,6 +1113,11 @@ struct mgrit_handle {
   std::vector<unsigned long long> prof_cyc;  // counter snapshots after each launch
   unsigned long long* dlog = nullptr;
   int dlog_cap = 0;
+  // learned coarse propagator (two levels, FAS) and its scratch
+  phic_handle* phic = nullptr;
+  double phic_switch = 0.5;
+  double *fas_tau = nullptr, *fas_v = nullptr;
+  cudaGraphExec_t gL = nullptr;             // the FAS coarse level, captured per (U, fhat)
   // state of the run in progress (mgrit_run, mgrit_run_batched)
   struct Run {
     double* U = nullptr;
@@ -992,10 +1129,12 @@ struct mgrit_handle {
     long launches0 = 0;
     std::chrono::steady_clock::time_point t0;
     igm_status status = IGM_OK;
+    bool fallback = false;          // the learned propagator was replaced by backward Euler
     cudaEvent_t evA = nullptr;      // completion of the fine-level part of an iteration
   } run;
   ~mgrit_handle() {
     if (run.evA) cudaEventDestroy(run.evA);
+    if (gL) cudaGraphExecDestroy(gL);
     if (gA) cudaGraphExecDestroy(gA);
     if (gB) cudaGraphExecDestroy(gB);
     for (auto& r : prof) { cudaEventDestroy(r.e0); cudaEventDestroy(r.e1); }
@@ -1075,6 +1214,32 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
 }
 
 extern "C" void mgrit_destroy(mgrit_handle* mg) { delete mg; }
+
+extern "C" igm_status mgrit_set_coarse_propagator(mgrit_handle* mg, phic_handle* h,
+                                                  double switch_ratio) {
+  if (!mg) return fail(IGM_ERR_ARG, "null argument");
+  if (mg->gL) cudaGraphExecDestroy(mg->gL);
+  mg->gL = nullptr;
+  if (!h) {
+    mg->phic = nullptr;
+    return IGM_OK;
+  }
+  if ((int)mg->L.size() != 2)
+    return fail(IGM_ERR_ARG, "the learned coarse propagator needs two time levels (max_levels = 2)");
+  if (h->net.n != mg->ops->hi.n) return fail(IGM_ERR_ARG, "propagator grid does not match the problem");
+  if (!(switch_ratio > 0.0)) return fail(IGM_ERR_ARG, "switch_ratio must be > 0");
+  const int N = mg->ops->hi.N, Nc = mg->L[1].Nl;
+  if (!mg->fas_tau) {
+    mg->fas_tau = (double*)mg->up.raw(sizeof(double) * (size_t)(Nc + 1) * N);
+    mg->fas_v = (double*)mg->up.raw(sizeof(double) * (size_t)(Nc + 1) * N);
+    if (mg->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(mg->up.err));
+  }
+  igm_status r = phic_work(h, h->upw, h->work, Nc);
+  if (r != IGM_OK) return r;
+  mg->phic = h;
+  mg->phic_switch = switch_ratio;
+  return IGM_OK;
+}
 
 // Launch one sweep kernel on level l.
 static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm, double* U,
@@ -1212,6 +1377,18 @@ static igm_status capture(mgrit_handle* mg, bool partA, double* U, const double*
   return IGM_OK;
 }
 
+// The coarse level of two-level MGRIT with the learned propagator (FAS):
+// tau_j = u_{jm} - Phi_c(u_{(j-1)m}) + r_j, v_j = Phi_c(v_{j-1}) + tau_j from
+// v_0 = u_0, then the C-point correction u_{jm} <- v_j with F-relaxation.
+static igm_status part_learned(mgrit_handle* mg, double* U, const double* fhat, cudaStream_t st) {
+  const bool profile = false;
+  const int m = mg->o.m, Nc = mg->L[1].Nl;
+  CU(phic_fas_coarse(mg->phic->net, Nc, m, U, mg->L[1].g, mg->fas_tau, mg->fas_v, mg->L[1].W,
+                     mg->phic->work, st));
+  SWEEP(0, MODE_CF, mg->L[0].Nl / m, nullptr);
+  return IGM_OK;
+}
+
 // Launch the fine-level part of iteration it (relaxation, residual, norms to
 // the host) and record run.evA after it.
 static igm_status launch_A(mgrit_handle* mg) {
@@ -1260,6 +1437,7 @@ static igm_status run_begin(mgrit_handle* mg, const double* u0, const double* fh
   R.it = 0;
   R.hist.clear();
   R.status = IGM_OK;
+  R.fallback = false;
   R.launches0 = g_launches.load();
   if (fhat)
     CU(cudaMemcpyAsync(mg->dfcoef, fcoef, sizeof(double) * (o.Nt + 1), cudaMemcpyHostToDevice, st));
@@ -1275,7 +1453,8 @@ static igm_status run_begin(mgrit_handle* mg, const double* u0, const double* fh
   if (R.graphs && (mg->g_U != U || mg->g_fhat != fhat)) {
     if (mg->gA) cudaGraphExecDestroy(mg->gA);
     if (mg->gB) cudaGraphExecDestroy(mg->gB);
-    mg->gA = mg->gB = nullptr;
+    if (mg->gL) cudaGraphExecDestroy(mg->gL);
+    mg->gA = mg->gB = mg->gL = nullptr;
   }
   // initial guess: U[0] = u0, U[n>=1] = 0 unless the caller's U is to be kept
   CU(cudaMemcpyAsync(U, u0, sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
@@ -1315,7 +1494,32 @@ static igm_status run_advance(mgrit_handle* mg) {
     }
     return IGM_OK;
   }
-  if (R.graphs) {
+  // learned coarse propagator: replaced by backward Euler for the rest of the
+  // run once the residual contraction exceeds the switch ratio
+  if (mg->phic && !R.fallback && R.hist.size() >= 2 &&
+      rho > mg->phic_switch * R.hist[R.hist.size() - 2])
+    R.fallback = true;
+  if (mg->phic && !R.fallback) {
+    const int Nc = mg->L[1].Nl;
+    if (R.graphs) {
+      if (!mg->gL) {
+        CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        igm_status r = part_learned(mg, U, fhat, st);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(st, &g);
+        if (r != IGM_OK) { if (g) cudaGraphDestroy(g); return r; }
+        if (e != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&mg->gL, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(e));
+      }
+      CU(cudaGraphLaunch(mg->gL, st));
+    } else {
+      igm_status r = part_learned(mg, U, fhat, st);
+      if (r != IGM_OK) return r;
+    }
+    g_launches += 5 * (Nc + 1) + 2 + 1;
+  } else if (R.graphs) {
     if (!mg->gB) {
       igm_status r = capture(mg, false, U, fhat, st, &mg->gB);
       if (r != IGM_OK) return r;
@@ -1365,6 +1569,7 @@ static igm_status run_finish(mgrit_handle* mg, mgrit_stats* stats) {
     stats->seconds = std::chrono::duration<double>(t1 - R.t0).count();
     stats->setup_seconds = mg->setup_seconds;
     stats->launches = g_launches.load() - R.launches0;
+    stats->coarse_fallback = R.fallback ? 1 : 0;
   }
   if (hstat == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
   if (hstat == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "a spatial solve hit max_cycles");
