@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--sjf", type=int, default=1,
                     help="--batch: 1 = shortest-job-first stream priorities (default), 0 = equal")
+    ap.add_argument("--learned", action="store_true",
+                    help="learned_c4: two-level MGRIT with the learned coarse propagator against "
+                         "backward Euler on the coarse level, one JSON line (not the headline)")
     ap.add_argument("--batch", action="store_true",
                     help="the uneven 64-problem batch (batch_c5): per-problem latency p50/p99 "
                          "and batch throughput, one JSON line (not the headline metric)")
@@ -253,10 +256,112 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_learned(args):
+    """learned_c4: unit square, p = 3, 64 x 64 elements, N_t = 4096, T = 4,
+    two-level MGRIT with m = 8, f = 0.  Training pairs (u_n, u_{n+8}) come from
+    the fine stepper (sequential backward Euler through the library) on five
+    16-mode random initial conditions; the network is trained with the BF16
+    kernels; then the same two-level MGRIT (chosen form) is timed on a sixth
+    initial condition with the learned coarse propagator and with backward
+    Euler on the coarse level, and the plain FP64 form with backward Euler."""
+    import numpy as np
+    import torch
+    from paper_2107_05337_gb300 import binding as B
+    from paper_2107_05337_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["learned_c4"]
+    p, nel, T, Nt, m = w["p"][0], w["nel"], w["T"], w["Nt"], w["m"]
+    prob = B.Problem(p, nel)
+
+    def ic(seed):
+        k, l, a = inputs.fourier_modes(seed=seed, count=w["modes"])
+        return prob.project(lambda xi, eta, x, y: sum(
+            a[s] * np.sin(k[s] * np.pi * xi) * np.sin(l[s] * np.pi * eta) for s in range(len(a))))
+
+    t0 = time.perf_counter()
+    seq = B.MGRIT(prob, T=T, Nt=Nt, m=m, max_levels=1, pmg=dict(precision=1, tol=1e-10))
+    U0s, U1s = [], []
+    for i in range(w["train_ics"] - 1):
+        U, _, _ = seq.run(ic(w["seed"] + i))
+        U0s.append(U[:-m].clone())
+        U1s.append(U[m:].clone())
+    # rough pairs: m fine steps from white noise (all columns solved at once),
+    # so that the network also learns how the fine stepper damps rough modes
+    gen = torch.Generator(device="cuda").manual_seed(w["seed"])
+    X0 = torch.randn((Nt, prob.N), dtype=torch.float64, device="cuda", generator=gen)
+    stepper = B.PMG(prob, T / Nt, precision=1, tol=1e-10)
+    X = X0.clone()
+    for _ in range(m):
+        rhs = prob.apply("M", X)
+        stepper.solve(rhs, X)
+    U0s.append(X0)
+    U1s.append(X)
+    U0, U1 = torch.cat(U0s), torch.cat(U1s)
+    npairs = int(U0.shape[0])
+    gen_s = time.perf_counter() - t0
+    phic = B.Phic(prob.n, 8, seed=w["seed"])
+    t0 = time.perf_counter()
+    steps = 3000
+    loss = phic.train(U0, U1, steps=steps, batch=32, lr=2e-3, seed=1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del U0, U1, U0s, U1s
+    u0 = ic(w["seed"] + 100)
+    Uref, _, _ = seq.run(u0)
+    Uref = Uref.clone()
+    units = prob.N * Nt
+
+    def timed(h):
+        h.run(u0, check=False)
+        torch.cuda.synchronize()
+        ms = []
+        st = None
+        status = 0
+        for _ in range(max(1, args.steps)):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            U, st, status = h.run(u0, check=False)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        err = float(torch.linalg.norm(U - Uref) / torch.linalg.norm(Uref))
+        return float(np.mean(ms)), st, err, status
+
+    common = dict(T=T, Nt=Nt, m=m, max_levels=2, tol=1e-10, max_iter=100)
+    learned = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
+    learned.set_coarse_propagator(phic, 0.5)
+    be = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
+    plain = B.MGRIT(prob, **common, pmg=dict(precision=0, tol=1e-10))
+    res = {}
+    for name, h in (("learned", learned), ("backward_euler", be), ("plain_fp64", plain)):
+        ms, st, err, status = timed(h)
+        hist = st["res_hist"]
+        res[name] = {"value": units / (ms * 1e-3), "ms": ms, "iters": st["iters"],
+                     "status": status, "coarse_fallback": st["coarse_fallback"],
+                     "error_vs_sequential": err,
+                     "contraction": [round(hist[k + 1] / hist[k], 4) for k in range(min(12, len(hist) - 1))]}
+    line = {"metric": "DOF*timesteps/s, two-level MGRIT with a learned coarse propagator",
+            "value": res["learned"]["value"], "unit": "DOF*timesteps/s", "n_gpus": 1,
+            "higher_is_better": True, "dtype": "bf16 (network) + f32/f64 (solves)",
+            "data": "synthetic",
+            "config": {"workload": "learned_c4: unit square, p=3, nel=64, N_t=4096, T=4, m=8, "
+                                   "two levels, f=0, 16-mode random initial conditions"},
+            "runs": res,
+            "speedup_vs_backward_euler_coarse": res["learned"]["value"] / res["backward_euler"]["value"],
+            "speedup_vs_plain_fp64": res["learned"]["value"] / res["plain_fp64"]["value"],
+            "training": {"pairs": npairs, "steps": steps, "batch": 32,
+                         "seconds": round(train_s, 2), "data_seconds": round(gen_s, 2),
+                         "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-20:]))}}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.learned:
+        return run_learned(args)
     if args.batch:
         return run_batch(args)
     import numpy as np

@@ -310,10 +310,12 @@ igm_status phic_train(phic_handle* h, int npairs, const double* U0, const double
  * MGRIT handle (max_levels = 2), with the FAS coarse equation
  * tau_j = u_{jm} - Phi_c(u_{(j-1)m}) + r_j, v_j = Phi_c(v_{j-1}) + tau_j.  The
  * fine propagator is unchanged, so the converged answer is sequential
- * stepping.  When an iteration's residual contraction rho_k / rho_{k-1}
- * exceeds switch_ratio (0.5 recommended) the run continues with the
- * backward-Euler coarse level (mgrit_stats.coarse_fallback = 1).  The handle
- * h must outlive the MGRIT handle's use of it. */
+ * stepping.  When the residual after a learned correction is not finite or
+ * its contraction rho_k / rho_{k-1} exceeds switch_ratio (0.5 recommended),
+ * that correction is undone (the iterate before it is restored and relaxed
+ * again) and the run continues with the backward-Euler coarse level
+ * (mgrit_stats.coarse_fallback = 1).  The handle h must outlive the MGRIT
+ * handle's use of it. */
 igm_status mgrit_set_coarse_propagator(mgrit_handle* mg, phic_handle* h, double switch_ratio);
 
 /* One-shot convenience: mgrit_create + mgrit_run + mgrit_destroy. */

@@ -13,7 +13,8 @@ Test infrastructure (see ``oracle/__init__``).  Pinned by
     because the fine propagator is unchanged (Sec. 3: the fixed point is the
     block forward solve of A u = g);
   * a propagator that does not contract (here -identity) is replaced by the
-    backward-Euler one once the residual contraction exceeds 0.5.
+    backward-Euler one once the residual contraction after a learned
+    correction exceeds 0.5; that correction is undone first.
 
 The network (reading; the paper uses only the rediscretised coarse step): on
 the n x n grid of interior coefficients (zero padding = the homogeneous
@@ -30,6 +31,10 @@ C-point residuals r_j = Phi(u_{jm-1}) + g_{jm} - u_{jm},
     tau_j = u_{jm} - Phi_c(u_{(j-1)m}) + r_j,
     v_0 = u_0,  v_j = Phi_c(v_{j-1}) + tau_j  (sequential),
     u_{jm} <- v_j, then F-relaxation (ideal interpolation).
+If the residual after a learned correction is not finite or contracted by
+more than the switch ratio (0.5), the iterate before the correction is
+restored and relaxed again, and the backward-Euler coarse propagator is used
+from then on.
 """
 import numpy as np
 
@@ -174,6 +179,7 @@ class FASTwoLevel:
         hist = []
         phic = self.phi_c
         it = 0
+        backup = None
         while True:
             if it == 0:
                 self._f_relax()
@@ -181,12 +187,19 @@ class FASTwoLevel:
             self._f_relax()
             r = [self.step(self.U[j * m - 1], j * m) - self.U[j * m] for j in range(1, Nc + 1)]
             rho = np.sqrt(sum(float(x @ x) for x in r))
+            if backup is not None and not (rho <= self.switch * hist[-1]):
+                # the learned correction is undone; backward Euler from here on
+                self.U = backup
+                backup = None
+                phic = self.fallback_c
+                self.used_fallback = True
+                continue
+            backup = None
             hist.append(rho)
             if rho == 0.0 or rho <= tol * hist[0] or it >= max_iter:
                 break
-            if len(hist) > 1 and rho > self.switch * hist[-2] and phic is not self.fallback_c:
-                phic = self.fallback_c
-                self.used_fallback = True
+            if phic is not self.fallback_c:
+                backup = self.U.copy()
             C = [self.U[j * m].copy() for j in range(Nc + 1)]
             tau = [None] + [C[j] - phic(C[j - 1]) + r[j - 1] for j in range(1, Nc + 1)]
             v = C[0].copy()

@@ -1117,6 +1117,7 @@ struct mgrit_handle {
   phic_handle* phic = nullptr;
   double phic_switch = 0.5;
   double *fas_tau = nullptr, *fas_v = nullptr;
+  double* fas_backup = nullptr;             // the iterate before a learned coarse correction
   cudaGraphExec_t gL = nullptr;             // the FAS coarse level, captured per (U, fhat)
   // state of the run in progress (mgrit_run, mgrit_run_batched)
   struct Run {
@@ -1130,6 +1131,7 @@ struct mgrit_handle {
     std::chrono::steady_clock::time_point t0;
     igm_status status = IGM_OK;
     bool fallback = false;          // the learned propagator was replaced by backward Euler
+    bool learned_prev = false;      // the last correction used the learned propagator
     cudaEvent_t evA = nullptr;      // completion of the fine-level part of an iteration
   } run;
   ~mgrit_handle() {
@@ -1232,6 +1234,7 @@ extern "C" igm_status mgrit_set_coarse_propagator(mgrit_handle* mg, phic_handle*
   if (!mg->fas_tau) {
     mg->fas_tau = (double*)mg->up.raw(sizeof(double) * (size_t)(Nc + 1) * N);
     mg->fas_v = (double*)mg->up.raw(sizeof(double) * (size_t)(Nc + 1) * N);
+    mg->fas_backup = (double*)mg->up.raw(sizeof(double) * (size_t)(mg->o.Nt + 1) * N);
     if (mg->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(mg->up.err));
   }
   igm_status r = phic_work(h, h->upw, h->work, Nc);
@@ -1382,7 +1385,9 @@ static igm_status capture(mgrit_handle* mg, bool partA, double* U, const double*
 // v_0 = u_0, then the C-point correction u_{jm} <- v_j with F-relaxation.
 static igm_status part_learned(mgrit_handle* mg, double* U, const double* fhat, cudaStream_t st) {
   const bool profile = false;
-  const int m = mg->o.m, Nc = mg->L[1].Nl;
+  const int m = mg->o.m, Nc = mg->L[1].Nl, N = mg->ops->hi.N;
+  CU(cudaMemcpyAsync(mg->fas_backup, U, sizeof(double) * (size_t)(mg->o.Nt + 1) * N,
+                     cudaMemcpyDeviceToDevice, st));
   CU(phic_fas_coarse(mg->phic->net, Nc, m, U, mg->L[1].g, mg->fas_tau, mg->fas_v, mg->L[1].W,
                      mg->phic->work, st));
   SWEEP(0, MODE_CF, mg->L[0].Nl / m, nullptr);
@@ -1438,6 +1443,7 @@ static igm_status run_begin(mgrit_handle* mg, const double* u0, const double* fh
   R.hist.clear();
   R.status = IGM_OK;
   R.fallback = false;
+  R.learned_prev = false;
   R.launches0 = g_launches.load();
   if (fhat)
     CU(cudaMemcpyAsync(mg->dfcoef, fcoef, sizeof(double) * (o.Nt + 1), cudaMemcpyHostToDevice, st));
@@ -1484,6 +1490,17 @@ static igm_status run_advance(mgrit_handle* mg) {
   double rr = 0.0;
   for (int j = 0; j < nint0; ++j) rr += mg->hnorms[j];
   const double rho = std::sqrt(rr);
+  // a learned coarse correction that made the residual non-finite or did not
+  // contract enough is undone: the iterate before it is restored, relaxed
+  // again, and the run continues with the backward-Euler coarse level
+  if (R.learned_prev && !(rho <= mg->phic_switch * R.hist.back())) {
+    R.learned_prev = false;
+    R.fallback = true;
+    const int N = mg->ops->hi.N;
+    CU(cudaMemcpyAsync(U, mg->fas_backup, sizeof(double) * (size_t)(o.Nt + 1) * N,
+                       cudaMemcpyDeviceToDevice, st));
+    return launch_A(mg);
+  }
   R.hist.push_back(rho);
   if (!(rho == rho)) return fail(IGM_ERR_NUMERIC, "NaN in the MGRIT residual");
   if (rho == 0.0 || rho <= o.tol * R.hist[0] || R.it >= o.max_iter) {
@@ -1494,12 +1511,9 @@ static igm_status run_advance(mgrit_handle* mg) {
     }
     return IGM_OK;
   }
-  // learned coarse propagator: replaced by backward Euler for the rest of the
-  // run once the residual contraction exceeds the switch ratio
-  if (mg->phic && !R.fallback && R.hist.size() >= 2 &&
-      rho > mg->phic_switch * R.hist[R.hist.size() - 2])
-    R.fallback = true;
+  R.learned_prev = false;
   if (mg->phic && !R.fallback) {
+    R.learned_prev = true;
     const int Nc = mg->L[1].Nl;
     if (R.graphs) {
       if (!mg->gL) {

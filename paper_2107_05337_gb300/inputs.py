@@ -19,6 +19,7 @@ import numpy as np
 
 SEED_ANNULUS = 20210712
 SEED_BATCH = 20210714
+SEED_LEARNED = 20210713
 
 
 def fourier_modes(seed=SEED_ANNULUS, count=8, kmax=8):
@@ -50,6 +51,8 @@ WORKLOADS = {
     "annulus_c3": dict(geom="quarter_annulus", p=[4], nel=128, T=1.0, Nt=1024, m=8,
                        max_levels=30, min_coarse=4, kappa=1.0, source="none"),
     "batch_c5": dict(members="batch_members()", source="none"),
+    "learned_c4": dict(geom="unit_square", p=[3], nel=64, T=4.0, Nt=4096, m=8, max_levels=2,
+                       kappa=1.0, source="none", train_ics=5, modes=16, seed=SEED_LEARNED),
 }
 
 
