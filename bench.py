@@ -388,7 +388,8 @@ def main():
     t_setup = time.perf_counter()
     # chosen form: FP32 p-multigrid cycles with FP64 refinement, and one cycle per
     # spatial solve on the coarse time levels (inexact coarse propagator)
-    chosen = {p: B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
+    chosen = {p: B.MGRIT(probs[p], **opts, coarse_cycles=1,
+                         pmg=dict(precision=1, tol=1e-10, autotune=1))
               for p in orders}
     setup_s = time.perf_counter() - t_setup
     units = sum(probs[p].N * Nt for p in orders)
@@ -424,7 +425,7 @@ def main():
         # per-launch V-cycle counts of the same solves (same order of launches),
         # to relate a captured launch's DRAM counters to its units of work
         for p in orders:
-            hp = B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10), profile=1,
+            hp = B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10, autotune=1), profile=1,
                          graphs=0)
             hp.run(u0s[p], fhats[p], fcoef, Us[p])
             pr = hp.profile()
@@ -511,7 +512,7 @@ def main():
     roof = None
     prof_tot_ms, prof_bytes, prof_launches, prof_units = 0.0, 0.0, 0, 0
     for p in orders:
-        hp = B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10), profile=1,
+        hp = B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10, autotune=1), profile=1,
                      graphs=0)
         hp.run(u0s[p], fhats[p], fcoef, Us[p])
         pr = hp.profile()
@@ -569,7 +570,8 @@ def main():
                 "config": {"workload": f"heat_c2: unit square, nel={nel}, p={orders}, N_t={Nt}, T=1, "
                                        "m=4 multilevel FCF MGRIT, p-MG V(1,1) to 1e-10",
                            "chosen_form": "FP32 p-MG cycles with FP64 refinement; one p-MG cycle "
-                                          "per coarse-time-level solve (fine level to 1e-10)",
+                                          "per coarse-time-level solve (fine level to 1e-10); "
+                                          "sweep layouts autotuned at setup",
                            "plain_form": "FP64 p-MG on every level to 1e-10",
                            "orders": "solved concurrently, one stream each",
                            "parallelism": f"replicas{world}" if world > 1 else "single GPU",

@@ -114,6 +114,10 @@ typedef struct {
                              diagonal preconditioner (the comparison solver of Sec. 5), always
                              in FP64 (precision is set to 0), one "cycle" = one CG iteration,
                              max_cycles = the iteration limit */
+  int autotune;           /* 0: the fixed layout policy (default); 1: time the candidate layouts
+                             of the ILUT sweeps (sweep team of 128 or 256 threads; arena in shared
+                             memory, swept vector staged in shared memory, or everything in global
+                             memory) on a probe solve at setup and keep the fastest */
 } pmg_opts;
 
 typedef struct pmg_handle pmg_handle;
@@ -184,6 +188,11 @@ typedef enum {
                              recurrence (warp scan) and stores */
   IGM_PH_COUNT = 14
 } igm_phase;
+
+/* The layout of the ILUT sweeps chosen at setup (HOST out[4]): threads per
+ * sweep team, record ring slots, 1 if the working vectors are in shared
+ * memory, 1 if the swept vector is staged in shared memory. */
+igm_status pmg_layout(const pmg_handle* h, int* out);
 
 /* Copy the accumulated phase clocks (HOST out[IGM_PH_COUNT]); reset = 1
  * zeroes them afterwards.  The handle must have been set up with trace = 1. */

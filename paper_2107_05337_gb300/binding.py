@@ -31,7 +31,7 @@ class PmgOpts(ctypes.Structure):
     _fields_ = [("nu1", c_int), ("nu2", c_int), ("ilut_droptol", c_double),
                 ("ilut_fill", c_double), ("hmg_coarsest_nel", c_int), ("precision", c_int),
                 ("inner_cycles", c_int), ("tol", c_double), ("max_cycles", c_int),
-                ("trace", c_int), ("solver", c_int)]
+                ("trace", c_int), ("solver", c_int), ("autotune", c_int)]
 
 
 class MgritOpts(ctypes.Structure):
@@ -74,6 +74,7 @@ EXPORTS = {
     "mgrit_destroy": (None, [c_void_p]),
     "mgrit_run": (c_int, [c_void_p, c_void_p, c_void_p, POINTER(c_double), c_void_p,
                           POINTER(MgritStats), c_void_p]),
+    "pmg_layout": (c_int, [c_void_p, POINTER(c_int)]),
     "mgrit_run_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                                   POINTER(c_void_p), POINTER(c_void_p), c_void_p,
                                   POINTER(ctypes.c_float), c_void_p]),
@@ -260,6 +261,12 @@ class PMG:
         if check:
             _check(st)
         return np.array(cyc[:], dtype=np.int64), st
+
+    def layout(self):
+        """(threads per sweep team, ring slots, arena in shared memory, staged vector)."""
+        out = (c_int * 4)()
+        _check(lib().pmg_layout(self.h, out))
+        return tuple(out)
 
     def ilut_apply(self, R):
         torch = _torch()

@@ -313,6 +313,7 @@ extern "C" void pmg_default_opts(pmg_opts* o) {
   o->max_cycles = 50;
   o->trace = 0;
   o->solver = 0;
+  o->autotune = 0;
 }
 
 static void gen_wcycle(int k, int last, std::vector<int>& ops) {
@@ -693,12 +694,17 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   // stages with a staged copy of the swept vector; else the arena in shared
   // memory with one stage; else the most stages with everything in global
   // memory.  Returns the byte offset of the arena (0: nothing fits).
-  auto place = [&](int slot, int team) -> long {
+  auto place = [&](int slot, int team, int only) -> long {
     const long sweep = ((long)wave_scratch_bytes(n, es, team) + 15) & ~15L;
     d.arena_smem = 0;
     d.nstage = 0;
     d.o_vstage = -1;
-    for (int pass = 0; pass < 5; ++pass)
+    d.sweep_team = team;
+    for (int pass = 0; pass < 5; ++pass) {
+      // only = 0: arena in shared memory; 1: staged vector; 2: all global
+      if (only == 0 && pass != 0 && pass != 1 && pass != 3) continue;
+      if (only == 1 && pass != 2) continue;
+      if (only == 2 && pass != 4) continue;
       for (int st = kMaxStage; st >= 1; --st) {
         const long base = (long)st * slot + bars + sweep;
         const bool arena = base + h->arena_bytes <= optin;
@@ -713,24 +719,104 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
         d.o_sweep = (int)((long)st * slot + bars);
         return base + (d.o_vstage >= 0 ? vst : 0);
       }
+    }
     return 0;
   };
   auto slot_of = [&](const Packed& pk) { return (std::max(pk.maxL, pk.maxU) + 127) & ~127; };
-  const long arena_off = place(slot_of(pk128), kSweepTeam);
+  // kernel attributes once per process (handles may be set up from several threads)
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, [&] { attr_err = set_solver_smem(optin); });
+  if (attr_err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(attr_err));
+  long arena_off = place(slot_of(pk128), kSweepTeam, -1);
   if (!arena_off) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
+  Packed pk256;
   const Packed* chosen = &pk128;
+  if (o.autotune) {
+    // time every distinct candidate layout on a probe solve (3 cycles, one
+    // right-hand side) and keep the fastest
+    e = pack(256, pk256);
+    if (!e.empty()) return fail(IGM_ERR_ARG, e);
+    std::vector<double> hb(N);
+    std::mt19937_64 rng(12345);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    for (auto& v : hb) v = nd(rng);
+    double *db = nullptr, *dx = nullptr;
+    int *dst = nullptr, *dcy = nullptr;
+    char* garena = nullptr;
+    CU(cudaMalloc(&db, sizeof(double) * N));
+    CU(cudaMalloc(&dx, sizeof(double) * N));
+    CU(cudaMalloc(&dst, sizeof(int)));
+    CU(cudaMalloc(&dcy, sizeof(int)));
+    CU(cudaMalloc(&garena, h->arena_bytes));
+    CU(cudaMemcpy(db, hb.data(), sizeof(double) * N, cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 0.0f;
+    int best_team = kSweepTeam, best_only = -1;
+    for (int team : {128, 256})
+      for (int only : {0, 1, 2}) {
+        const Packed& pk = team == 128 ? pk128 : pk256;
+        const long off = place(slot_of(pk), team, only);
+        if (!off) continue;
+        char *rl = nullptr, *ru = nullptr;
+        CU(cudaMalloc(&rl, pk.L.size()));
+        CU(cudaMalloc(&ru, pk.U.size()));
+        CU(cudaMemcpy(rl, pk.L.data(), pk.L.size(), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(ru, pk.U.data(), pk.U.size(), cudaMemcpyHostToDevice));
+        PmgD t = d;
+        t.Lrec.recs = rl; t.Lrec.bytes = pk.maxL;
+        t.Urec.recs = ru; t.Urec.bytes = pk.maxU;
+        t.ring_bytes = off;
+        const long smem = off + (t.arena_smem ? h->arena_bytes : 0);
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2; ++rep) {
+          CU(cudaMemset(dx, 0, sizeof(double) * N));
+          CU(cudaMemset(dst, 0, sizeof(int)));
+          CU(cudaEventRecord(e0, 0));
+          CU(launch_pmg_solve(t.precision, t, 1, smem, 0, db, dx, N, 3, dcy, dst, garena));
+          CU(cudaEventRecord(e1, 0));
+          CU(cudaEventSynchronize(e1));
+          CU(cudaEventElapsedTime(&ms, e0, e1));
+        }
+        int hst = 0;
+        CU(cudaMemcpy(&hst, dst, sizeof(int), cudaMemcpyDeviceToHost));
+        cudaFree(rl);
+        cudaFree(ru);
+        if (hst != ST_OK) continue;
+        if (best_only < 0 || ms < best) {
+          best = ms;
+          best_team = team;
+          best_only = only;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(db); cudaFree(dx); cudaFree(dst); cudaFree(dcy); cudaFree(garena);
+    if (best_only >= 0) {
+      chosen = best_team == 128 ? &pk128 : &pk256;
+      arena_off = place(slot_of(*chosen), best_team, best_only);
+    } else {
+      arena_off = place(slot_of(pk128), kSweepTeam, -1);
+    }
+  }
   d.Lrec.recs = up.put(chosen->L); d.Lrec.bytes = chosen->maxL;
   d.Urec.recs = up.put(chosen->U); d.Urec.bytes = chosen->maxU;
   if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
   d.ring_bytes = arena_off;
   h->arena_smem = d.arena_smem != 0;
   h->smem_bytes = d.ring_bytes + (d.arena_smem ? h->arena_bytes : 0);
-  // kernel attributes once per process (handles may be set up from several threads)
-  static std::once_flag attr_once;
-  static cudaError_t attr_err = cudaSuccess;
-  std::call_once(attr_once, [&] { attr_err = set_solver_smem(optin); });
-  if (attr_err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(attr_err));
   *out = h.release();
+  return IGM_OK;
+}
+
+extern "C" igm_status pmg_layout(const pmg_handle* h, int* out) {
+  if (!h || !out) return fail(IGM_ERR_ARG, "null argument");
+  out[0] = h->d.sweep_team;
+  out[1] = h->d.nstage;
+  out[2] = h->d.arena_smem;
+  out[3] = h->d.o_vstage >= 0 ? 1 : 0;
   return IGM_OK;
 }
 

@@ -97,6 +97,7 @@ struct PmgD {
   long ring_bytes;
   int arena_smem;
   int o_sweep, o_vstage;       // byte offsets; o_vstage < 0: no staged copy
+  int sweep_team;              // threads per ILUT sweep team: 128 or 256
 };
 
 // ---------------------------------------------------------------------------
@@ -514,7 +515,7 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, const RecSet& R, int k, int
 // ---------------------------------------------------------------------------
 // wavefront block-row triangular sweeps
 // ---------------------------------------------------------------------------
-constexpr int kSweepTeam = 128;  // threads per ILUT sweep team (4 warps, one per SM sub-partition)
+constexpr int kSweepTeam = 128;  // default threads per ILUT sweep team (4 warps, one per SM sub-partition)
 
 // Scratch of a sweep in shared memory: int pieces[n] (per row r: first lane
 // of its pieces | count << 16), then per team (kBlock / team of them) the

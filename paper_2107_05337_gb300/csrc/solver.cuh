@@ -76,8 +76,13 @@ __device__ bool ilut_apply(const PmgD& P, Pipe& pp, T* v, int* status) {
     IGM_FOR_CTA(i, P.N) w[i] = v[i];
     __syncthreads();
   }
-  const bool ok = wave_sweep<T, false, kSweepTeam>(P.n, P.Lrec, pp, w, scr, status, P.trace) &&
-                  wave_sweep<T, true, kSweepTeam>(P.n, P.Urec, pp, w, scr, status, P.trace);
+  bool ok;
+  if (P.sweep_team == 256)
+    ok = wave_sweep<T, false, 256>(P.n, P.Lrec, pp, w, scr, status, P.trace) &&
+         wave_sweep<T, true, 256>(P.n, P.Urec, pp, w, scr, status, P.trace);
+  else
+    ok = wave_sweep<T, false, kSweepTeam>(P.n, P.Lrec, pp, w, scr, status, P.trace) &&
+         wave_sweep<T, true, kSweepTeam>(P.n, P.Urec, pp, w, scr, status, P.trace);
   if (P.o_vstage >= 0) {
     IGM_FOR_CTA(i, P.N) v[i] = w[i];
     __syncthreads();

@@ -195,3 +195,28 @@ def test_coarse_cycles_converge_to_sequential(B, precision):
                  pmg=dict(tol=1e-13, precision=precision))
     assert st["levels"] == 4
     assert _rel(U, seq) < 1e-10, st
+
+
+@pytest.mark.parametrize("p", [2, 5])
+def test_autotuned_layout_gives_the_same_solve(B, p):
+    """pmg_opts.autotune = 1 (layout chosen by timing) solves like the default
+    layout: fixed FP64 cycles equal the oracle's, converged mixed solves agree."""
+    import torch
+    from oracle import pmg as opmg
+    nel, c = 16, 1.0 / 256
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    lo = assembly.Discretisation(1, nel, geometry.UnitSquare())
+    b = np.random.default_rng(8).standard_normal((2, d.N))
+    P = opmg.PMG(d, lo, c)
+    want = np.array([P.solve(bb, np.zeros(d.N), ncycles=2)[0] for bb in b])
+    g = B.PMG(B.Problem(p, nel), c, precision=0, autotune=1)
+    X = torch.zeros((2, d.N), dtype=torch.float64, device="cuda")
+    g.solve(torch.as_tensor(b, device="cuda"), X, ncycles=2, check=False)
+    assert _rel(X.cpu().numpy(), want) < 1e-10
+    sols = []
+    for tune in (0, 1):
+        gm = B.PMG(B.Problem(p, nel), c, precision=1, tol=1e-12, autotune=tune)
+        Y = torch.zeros((2, d.N), dtype=torch.float64, device="cuda")
+        gm.solve(torch.as_tensor(b, device="cuda"), Y)
+        sols.append(Y.cpu().numpy())
+    assert _rel(sols[1], sols[0]) < 1e-10
