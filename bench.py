@@ -220,8 +220,8 @@ def run_batch(args):
         prio[i] = 5 - (6 * r) // len(members) if args.sjf else 0
     t0 = time.perf_counter()
     mk = lambda i: B.MGRIT(probs[i], T=members[i]["T"], Nt=members[i]["Nt"], m=members[i]["m"],
-                           tol=1e-10, max_iter=100, priority=prio[i],
-                           pmg=dict(precision=1, tol=1e-10))
+                           tol=1e-10, max_iter=100, priority=prio[i], coarse_cycles=1,
+                           pmg=dict(precision=1, tol=1e-10, autotune=1))
     with ThreadPoolExecutor(max_workers=16) as ex:
         handles = list(ex.map(mk, range(len(members))))
     setup_s = time.perf_counter() - t0
@@ -252,6 +252,7 @@ def run_batch(args):
                            "max": float(lat.max())},
             "makespan_ms": makespan, "setup_s": round(setup_s, 2),
             "scheduling": "shortest job first (stream priorities)" if args.sjf else "equal priorities",
+            "form": "mixed precision, one p-MG cycle per coarse-level solve, autotuned sweep layouts",
             "iters": {"min": int(min(iters)), "max": int(max(iters))}, "members": len(members)}
     print(json.dumps(line))
 
