@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="learned_c4: two-level MGRIT with the learned coarse propagator against "
                          "backward Euler on the coarse level, one JSON line (not the headline)")
+    ap.add_argument("--spmm", action="store_true",
+                    help="batched FP32 operator apply (iga_apply_f32) on 8192 columns: achieved "
+                         "HBM GB/s against the measured peak, one JSON line per order")
     ap.add_argument("--batch", action="store_true",
                     help="the uneven 64-problem batch (batch_c5): per-problem latency p50/p99 "
                          "and batch throughput, one JSON line (not the headline metric)")
@@ -357,10 +360,49 @@ def run_learned(args):
     print(json.dumps(line))
 
 
+def run_spmm(args):
+    """(M + c K) applied to 8192 FP32 columns of the 64 x 64-element unit square
+    (one column per time point of a long interval), p = 2..5: bytes moved
+    (one read of x, one write of y) over the CUDA-event time, against the
+    measured HBM copy bandwidth.  286 MB in and out per call at p = 4, far above
+    L2; the timed calls alternate between two input blocks.  Columns are padded to
+    a multiple of four floats (the streamed kernel needs 16-byte aligned columns)."""
+    import torch
+    from paper_2107_05337_gb300 import binding as B
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    ncol = 8192
+    for p in (2, 3, 4, 5):
+        prob = B.Problem(p, 64)
+        ld = (prob.N + 3) // 4 * 4   # 16-byte aligned columns: the streamed path
+        X = [torch.randn((ncol, ld), dtype=torch.float32, device="cuda") for _ in range(2)]
+        for _ in range(3):
+            prob.apply_f32("A", X[0], c=1.0 / 256)
+        torch.cuda.synchronize()
+        reps = 10
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for r in range(reps):
+            prob.apply_f32("A", X[r % 2], c=1.0 / 256)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        gbs = 2 * 4 * prob.N * ncol / (ms * 1e-3) / 1e9
+        print(json.dumps({"kernel": "k_spmm32 (iga_apply_f32)", "p": p, "N": prob.N, "columns": ncol,
+                          "ms_per_call": round(ms, 4), "achieved_gbs": round(gbs, 1),
+                          "peak_gbs": peak, "frac": round(gbs / peak, 3),
+                          "peak_source": "measured" if peaks else "fallback",
+                          "flops_per_unknown": 4 * (2 * p + 1) * 2}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.spmm:
+        return run_spmm(args)
     if args.learned:
         return run_learned(args)
     if args.batch:

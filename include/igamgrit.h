@@ -95,6 +95,15 @@ igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_st
 igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, double* y,
                      long ld, igm_stream s);
 
+/* Batched FP32 apply on the affine map (the unit square): y_b = M x_b
+ * (which = 0), K x_b (1) or (M + c K) x_b (2) for b < nrhs, x, y DEVICE
+ * [nrhs][ld] FP32, ld >= N, by sum factorisation in shared memory (one
+ * persistent CTA per column at a time, columns streamed from HBM).  The
+ * operator of Sec. 2 (Eq. (los)) applied to a block of right-hand sides such
+ * as the time points of an interval.  IGM_ERR_ARG on the curved map. */
+igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x, float* y,
+                         long ld, igm_stream s);
+
 /* ---------------------------------------------------------------------------
  * p-multigrid (Sec. 4) for A = M + c K, c = kappa*dt.
  * ------------------------------------------------------------------------ */

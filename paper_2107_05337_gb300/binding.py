@@ -56,6 +56,8 @@ EXPORTS = {
     "iga_quadrature_points": (c_int, [c_void_p, POINTER(c_double)]),
     "iga_load_vector": (c_int, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
     "iga_project": (c_int, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
+    "iga_apply_f32": (c_int, [c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_long,
+                              c_void_p]),
     "iga_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p]),
     "pmg_default_opts": (None, [POINTER(PmgOpts)]),
     "pmg_setup": (c_int, [c_void_p, c_double, POINTER(PmgOpts), POINTER(c_void_p)]),
@@ -205,6 +207,16 @@ class Problem:
         _check(lib().iga_project(self.h, fq.ctypes.data_as(POINTER(c_double)), _dptr(out),
                                  _stream()))
         return out
+
+    def apply_f32(self, which, X, c=0.0):
+        """Y = M X, K X or (M + c K) X (which = 'M', 'K', 'A') on FP32 columns X [nrhs, N]
+        (unit square only)."""
+        torch = _torch()
+        X = X.contiguous()
+        Y = torch.empty_like(X)
+        _check(lib().iga_apply_f32(self.h, {"M": 0, "K": 1, "A": 2}[which], c, X.shape[0],
+                                   _dptr(X), _dptr(Y), X.shape[1], _stream()))
+        return Y
 
     def apply(self, which, X):
         """Y = M X (which='M') or K X (which='K') on columns X [nrhs, N] (CUDA float64)."""

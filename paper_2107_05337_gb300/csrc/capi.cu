@@ -19,6 +19,7 @@
 #include "host_setup.h"
 #include "kernels.h"
 #include "phic.h"
+#include "spmm.h"
 
 using namespace igm;
 
@@ -99,6 +100,8 @@ struct iga_ops {
   // device copies
   double *bM64 = nullptr, *bK64 = nullptr, *sM64 = nullptr, *sK64 = nullptr;
   float *bM32 = nullptr, *bK32 = nullptr;
+  float* bA32 = nullptr;   // scratch bands of M + c K for iga_apply_f32 (2 n (2p+1) floats)
+  std::mutex mu;
   std::vector<double> qpts, qwdet;
 };
 
@@ -1002,6 +1005,46 @@ extern "C" igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const d
   CU(launch_apply_op(d, which, nrhs, x, y, ld, scratch, st));
   g_launches++;
   CU(cudaFreeAsync(scratch, st));
+  return IGM_OK;
+}
+
+extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x,
+                                    float* y, long ld, igm_stream s) {
+  if (!ops || (nrhs > 0 && (!x || !y))) return fail(IGM_ERR_ARG, "null argument");
+  if (which < 0 || which > 2 || nrhs < 0 || ld < ops->hi.N) return fail(IGM_ERR_ARG, "bad which/nrhs/ld");
+  if (!ops->geom.affine) return fail(IGM_ERR_ARG, "iga_apply_f32 needs the affine (unit square) map");
+  if (nrhs == 0) return IGM_OK;
+  const int n = ops->hi.n, p = ops->hi.p, W = 2 * p + 1;
+  cudaStream_t st = (cudaStream_t)s;
+  const float *X1 = ops->bM32, *W1 = nullptr, *Y2 = ops->bM32, *Z2 = nullptr;
+  if (which == 1) {
+    W1 = ops->bK32;
+    Y2 = ops->bK32;
+    Z2 = ops->bM32;
+  } else if (which == 2) {
+    std::lock_guard<std::mutex> lock(ops->mu);
+    if (!ops->bA32) {
+      ops->bA32 = (float*)ops->up.raw(sizeof(float) * 2 * (size_t)n * W);
+      if (ops->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(ops->up.err));
+    }
+    std::vector<float> hb(2 * (size_t)n * W);
+    for (size_t i = 0; i < (size_t)n * W; ++i) {
+      hb[i] = (float)(ops->hi.M1[i] + c * ops->hi.K1[i]);
+      hb[(size_t)n * W + i] = (float)(c * ops->hi.M1[i]);
+    }
+    CU(cudaMemcpy(ops->bA32, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice));
+    W1 = ops->bK32;
+    Y2 = ops->bA32;
+    Z2 = ops->bA32 + (size_t)n * W;
+  }
+  if (spmm32_smem(n, p) > (size_t)dev_smem_optin()) return fail(IGM_ERR_ARG, "grid too large for iga_apply_f32");
+  int sms = 0, dev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int per_sm = std::max(1, (int)(dev_smem_optin() / std::max<size_t>(1, spmm32_smem(n, p))));
+  const int grid = std::min(nrhs, sms * std::min(per_sm, 2));
+  CU(launch_spmm32(n, p, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st));
+  g_launches++;
   return IGM_OK;
 }
 

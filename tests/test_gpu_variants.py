@@ -220,3 +220,27 @@ def test_autotuned_layout_gives_the_same_solve(B, p):
         gm.solve(torch.as_tensor(b, device="cuda"), Y)
         sols.append(Y.cpu().numpy())
     assert _rel(sols[1], sols[0]) < 1e-10
+
+
+@pytest.mark.parametrize("p,nel", [(2, 16), (4, 24), (5, 8)])
+@pytest.mark.parametrize("which", ["M", "K", "A"])
+def test_batched_fp32_operator_apply_matches_oracle(B, p, nel, which):
+    """iga_apply_f32 (FP32 sum factorisation over a block of columns) against
+    the oracle's assembled M, K in FP64: FP32 rounding only."""
+    import torch
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    c = 0.37
+    A = {"M": d.M, "K": d.K, "A": d.M + c * d.K}[which]
+    X = np.random.default_rng(6).standard_normal((7, d.N))
+    want = np.array([A @ x for x in X])
+    prob = B.Problem(p, nel)
+    Y = prob.apply_f32(which, torch.as_tensor(X, dtype=torch.float32, device="cuda"), c=c)
+    got = Y.double().cpu().numpy()
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-6
+
+
+def test_batched_fp32_apply_rejects_curved_map(B):
+    import torch
+    prob = B.Problem(2, 8, "quarter_annulus")
+    with pytest.raises(B.IgmError):
+        prob.apply_f32("M", torch.zeros((1, prob.N), dtype=torch.float32, device="cuda"))
