@@ -66,9 +66,10 @@ def manufactured():
 
 
 # DRAM bytes per V-cycle and unknown measured by ncu on k_mgrit_sweep (p = 4,
-# 64 x 64 elements, fine-level relaxation launch; profiles/
-# k_mgrit_sweep_heat_c2_p4_wavefront.md); re-measure whenever the kernel changes.
-DRAM_BYTES_PER_VCYCLE_DOF = 26.3
+# 64 x 64 elements, chosen form with autotuned layouts, fine-level relaxation
+# launch; profiles/k_mgrit_sweep_heat_c2_p4_wavefront.md); re-measure whenever
+# the kernel changes.
+DRAM_BYTES_PER_VCYCLE_DOF = 24.8
 
 
 def bytes_per_vcycle_dof(p, B):

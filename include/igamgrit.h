@@ -97,10 +97,14 @@ igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, d
 
 /* Batched FP32 apply on the affine map (the unit square): y_b = M x_b
  * (which = 0), K x_b (1) or (M + c K) x_b (2) for b < nrhs, x, y DEVICE
- * [nrhs][ld] FP32, ld >= N, by sum factorisation in shared memory (one
- * persistent CTA per column at a time, columns streamed from HBM).  The
- * operator of Sec. 2 (Eq. (los)) applied to a block of right-hand sides such
- * as the time points of an interval.  IGM_ERR_ARG on the curved map. */
+ * [nrhs][ld] FP32, ld >= N, any alignment; c is rounded to FP32.  Sum
+ * factorisation (Sec. 2: M = M1 (x) M1, K = K1 (x) M1 + M1 (x) K1) in
+ * shared memory: one persistent CTA per SM pipelines its columns (one warp
+ * group streams a column in and contracts along xi while the other contracts
+ * the previous column along eta).  The operator of Eq. (los) applied to a
+ * block of right-hand sides such as the time points of an interval.
+ * IGM_ERR_ARG on the curved map, or when the n x n grid (n = N^(1/2)) does not
+ * fit the shared-memory pipeline (about n > 90). */
 igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x, float* y,
                          long ld, igm_stream s);
 

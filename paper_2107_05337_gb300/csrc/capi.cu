@@ -100,8 +100,6 @@ struct iga_ops {
   // device copies
   double *bM64 = nullptr, *bK64 = nullptr, *sM64 = nullptr, *sK64 = nullptr;
   float *bM32 = nullptr, *bK32 = nullptr;
-  float* bA32 = nullptr;   // scratch bands of M + c K for iga_apply_f32 (2 n (2p+1) floats)
-  std::mutex mu;
   std::vector<double> qpts, qwdet;
 };
 
@@ -1014,36 +1012,21 @@ extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs,
   if (which < 0 || which > 2 || nrhs < 0 || ld < ops->hi.N) return fail(IGM_ERR_ARG, "bad which/nrhs/ld");
   if (!ops->geom.affine) return fail(IGM_ERR_ARG, "iga_apply_f32 needs the affine (unit square) map");
   if (nrhs == 0) return IGM_OK;
-  const int n = ops->hi.n, p = ops->hi.p, W = 2 * p + 1;
+  const int n = ops->hi.n, p = ops->hi.p;
   cudaStream_t st = (cudaStream_t)s;
-  const float *X1 = ops->bM32, *W1 = nullptr, *Y2 = ops->bM32, *Z2 = nullptr;
-  if (which == 1) {
-    W1 = ops->bK32;
-    Y2 = ops->bK32;
-    Z2 = ops->bM32;
-  } else if (which == 2) {
-    std::lock_guard<std::mutex> lock(ops->mu);
-    if (!ops->bA32) {
-      ops->bA32 = (float*)ops->up.raw(sizeof(float) * 2 * (size_t)n * W);
-      if (ops->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(ops->up.err));
-    }
-    std::vector<float> hb(2 * (size_t)n * W);
-    for (size_t i = 0; i < (size_t)n * W; ++i) {
-      hb[i] = (float)(ops->hi.M1[i] + c * ops->hi.K1[i]);
-      hb[(size_t)n * W + i] = (float)(c * ops->hi.M1[i]);
-    }
-    CU(cudaMemcpy(ops->bA32, hb.data(), sizeof(float) * hb.size(), cudaMemcpyHostToDevice));
-    W1 = ops->bK32;
-    Y2 = ops->bA32;
-    Z2 = ops->bA32 + (size_t)n * W;
-  }
-  if (spmm32_smem(n, p) > (size_t)dev_smem_optin()) return fail(IGM_ERR_ARG, "grid too large for iga_apply_f32");
+  // y = (Y2 (x) X1 + Z2 (x) W1) x with each factor a M1 + b K1:
+  //   M = M1 (x) M1;  K = K1 (x) M1 + M1 (x) K1;  M + c K = (M1 + c K1) (x) M1 + c M1 (x) K1
+  const float cf32 = (float)c;
+  SpmmCoef cf{1, 0, 0, 0, 1, 0, 0, 0};
+  if (which == 1) cf = SpmmCoef{1, 0, 0, 1, 0, 1, 1, 0};
+  if (which == 2) cf = SpmmCoef{1, 0, 0, 1, 1, cf32, cf32, 0};
+  const size_t smem_max = (size_t)dev_smem_optin();
+  if (spmm32_slots(n, p, smem_max) < 2) return fail(IGM_ERR_ARG, "grid too large for iga_apply_f32");
   int sms = 0, dev = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  const int per_sm = std::max(1, (int)(dev_smem_optin() / std::max<size_t>(1, spmm32_smem(n, p))));
-  const int grid = std::min(nrhs, sms * std::min(per_sm, 2));
-  CU(launch_spmm32(n, p, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st));
+  const int grid = std::min(nrhs, sms);
+  CU(launch_spmm32(n, p, nrhs, ops->bM32, ops->bK32, cf, x, y, ld, grid, smem_max, st));
   g_launches++;
   return IGM_OK;
 }

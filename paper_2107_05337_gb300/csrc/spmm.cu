@@ -4,9 +4,30 @@
 // M1 (x) K1 on the unit square), by sum factorisation:
 //   stage 1 (along xi):  tm = x X1^T, tk = x W1^T  (rows of the n x n grid)
 //   stage 2 (along eta): y = Y2 tm + Z2 tk          (columns of the grid)
-// Persistent CTAs loop over the columns; both stages run in shared memory
-// with four outputs per thread and the stage-1 band rows in registers.
+// Each of the four 1D factors is a combination a M1 + b K1 formed on the fly
+// from the FP32 bands of M1 and K1.
+//
+// One persistent CTA per SM, split into two warp groups that form a pipeline
+// over the CTA's columns:
+//   * stage-1 warps (0-6) stream column k + nb - 1 into a ring of nb shared
+//     slots by 4-byte cp.async (rows padded with p zero columns on each side,
+//     so the band windows need no bounds tests), then turn column k into
+//     (tm, tk) in one of two shared buffers;
+//   * stage-2 warps (7-15) turn the other buffer into y and store it; each
+//     half-warp takes one group of J grid rows, its 16 lanes 16 consecutive
+//     grid columns.
+// Both stages run on packed FP32 FMAs (two lanes per instruction): stage 1
+// accumulates the (tm, tk) pair of a grid point with the (X1, W1) band pair,
+// stage 2 the pair (Y2 tm, Z2 tk) with the (Y2, Z2) band pair.
+// The groups hand the two buffers back and forth by named barriers (bar.arrive
+// / bar.sync; hardware waits, no polling).  Both groups keep their band rows in
+// registers: a stage-1 thread owns J grid columns of every row it visits, a
+// stage-2 thread J grid rows of every column it visits.  All strides are
+// compile-time (two layouts, for grids up to 68 and 84 lines), so every band
+// tap is an immediate address offset.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 
 #include "device.cuh"
 #include "spmm.h"
@@ -15,299 +36,288 @@ namespace igm {
 
 namespace {
 
-constexpr int kThreads = 256;
+constexpr int kG1 = 224;               // stage-1 threads (warps 0-6)
+constexpr int kG2 = 288;               // stage-2 threads (warps 7-15): 18 half-warps
+constexpr int kThreads = kG1 + kG2;
+constexpr int kHalves = kG2 / 16;
+constexpr int kMaxSlots = 4;
+constexpr int kBarCopy = 1;            // stage-1 group: ring slot ready / released
+constexpr int kBarFull = 2;            // + buffer index: (tm, tk) written
+constexpr int kBarEmpty = 4;           // + buffer index: (tm, tk) consumed
 
-template <int W>
-__global__ void __launch_bounds__(kThreads, 2) k_spmm32(int n, int nrhs, const float* X1,
-                                                     const float* W1, const float* Y2,
-                                                     const float* Z2, const float* x, float* y,
-                                                     long ld) {
-  constexpr int p = (W - 1) / 2;
-  extern __shared__ __align__(16) float sm[];
-  const int G = (n + 3) / 4;                 // groups of four along a grid row
-  const int xs = ((4 * G + 2 * p + 3) / 4) * 4;   // padded x row (halo p each side)
-  float* xsm = sm;                           // [n][xs]
-  float* tm = xsm + (size_t)n * xs;          // [n + 2p][n] with zero halo rows
-  float* tk = tm + (size_t)(n + 2 * p) * n;
-  float* y2 = tk + (size_t)(n + 2 * p) * n;  // [n][W]
-  float* z2 = y2 + (size_t)n * W;
-  const bool haveK = W1 != nullptr;
-  for (int i = threadIdx.x; i < n * W; i += blockDim.x) {
-    y2[i] = Y2[i];
-    z2[i] = Z2 ? Z2[i] : 0.0f;
-  }
-  // zero the x halo and the tm / tk halo rows once (never overwritten)
-  for (int i = threadIdx.x; i < n * xs; i += blockDim.x) xsm[i] = 0.0f;
-  for (int i = threadIdx.x; i < p * n; i += blockDim.x) {
-    tm[i] = 0.0f;
-    tk[i] = 0.0f;
-    tm[(size_t)(n + p) * n + i] = 0.0f;
-    tk[(size_t)(n + p) * n + i] = 0.0f;
-  }
-  // stage-1 assignment: group g of every row iy = r0, r0 + R1, ...
-  const int R1 = blockDim.x / G;
-  const int g = threadIdx.x % G, r0 = threadIdx.x / G;
-  const bool on1 = r0 < R1;
-  float a[4][W], k[4][W];
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int ix = 4 * g + j;
-#pragma unroll
-    for (int o = 0; o < W; ++o) {
-      a[j][o] = ix < n ? X1[(size_t)ix * W + o] : 0.0f;
-      k[j][o] = (ix < n && haveK) ? W1[(size_t)ix * W + o] : 0.0f;
-    }
-  }
-  // stage-2 assignment: column ix, row groups gy = c0, c0 + R2, ...
-  const int R2 = blockDim.x / n;
-  const int ix2 = threadIdx.x % n, c0 = threadIdx.x / n;
-  const bool on2 = c0 < R2;
-  for (int b = blockIdx.x; b < nrhs; b += gridDim.x) {
-    const float* xb = x + (size_t)b * ld;
-    float* yb = y + (size_t)b * ld;
-    __syncthreads();  // the previous column's stage 2 is done with tm / tk
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
-      const int iy = i / n, ix = i % n;
-      xsm[(size_t)iy * xs + p + ix] = xb[i];
-    }
-    __syncthreads();
-    if (on1) {
-      for (int iy = r0; iy < n; iy += R1) {
-        // x[iy][4g - p .. 4g + 3 + p] sits at xsm[iy][4g .. 4g + 3 + 2p]
-        const float4* row = (const float4*)(xsm + (size_t)iy * xs + 4 * g);
-        float v[((W + 3 + 3) / 4) * 4];
-#pragma unroll
-        for (int q = 0; q < (W + 3 + 3) / 4; ++q) {
-          const float4 t = row[q];
-          v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int ix = 4 * g + j;
-          float sm_ = 0.0f, sk = 0.0f;
-#pragma unroll
-          for (int o = 0; o < W; ++o) {
-            sm_ = fmaf(a[j][o], v[j + o], sm_);
-            sk = fmaf(k[j][o], v[j + o], sk);
-          }
-          if (ix < n) {
-            tm[(size_t)(iy + p) * n + ix] = sm_;
-            tk[(size_t)(iy + p) * n + ix] = sk;
-          }
-        }
-      }
-    }
-    __syncthreads();
-    if (on2) {
-      for (int gy = c0; 4 * gy < n; gy += R2) {
-        float um[4 + W - 1], uk[4 + W - 1];
-#pragma unroll
-        for (int q = 0; q < 4 + W - 1; ++q) {
-          const int r = 4 * gy + q;  // halo row index (iy + p - p)
-          const bool in = r < n + 2 * p;
-          um[q] = in ? tm[(size_t)r * n + ix2] : 0.0f;
-          uk[q] = in ? tk[(size_t)r * n + ix2] : 0.0f;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int iy = 4 * gy + j;
-          if (iy >= n) break;
-          float s = 0.0f;
-#pragma unroll
-          for (int o = 0; o < W; ++o) {
-            s = fmaf(y2[iy * W + o], um[j + o], s);
-            s = fmaf(z2[iy * W + o], uk[j + o], s);
-          }
-          yb[(size_t)iy * n + ix2] = s;
-        }
-      }
-    }
-  }
+__device__ __forceinline__ void bar_sync(int id, int cnt) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(cnt) : "memory");
 }
+__device__ __forceinline__ void bar_arrive(int id, int cnt) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(cnt) : "memory");
+}
+// 4-byte copy issued only when on != 0 (predicated inside the asm: no branch)
+__device__ __forceinline__ void cp_async4_if(uint32_t dst, const float* src, int on) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.ca.shared.global [%0], [%1], 4;\n}"
+      ::"r"(dst), "l"(src), "r"(on) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// all but the nb - 2 most recent copy groups have landed
+__device__ __forceinline__ void cp_async_wait_ring(int nb) {
+  if (nb >= 4) cp_async_wait<2>();
+  else if (nb == 3) cp_async_wait<1>();
+  else cp_async_wait<0>();
+}
+// sum of W band taps: the first a packed multiply, the rest packed FMAs
+template <int W, class F>
+__device__ __forceinline__ float2 taps(F&& term) {
+  float2 acc = __fmul2_rn(term(0).x_, term(0).y_);
+#pragma unroll
+  for (int o = 1; o < W; ++o) acc = __ffma2_rn(term(o).x_, term(o).y_, acc);
+  return acc;
+}
+struct Term {
+  float2 x_, y_;
+};
 
-// The same operator with the columns streamed by cp.async.bulk through a ring
-// of NB shared-memory buffers (column k + NB is in flight while column k is
-// computed).  Needs ld % 4 == 0 (16-byte aligned columns).  A wait that does
-// not complete within the bounded number of polls ends the CTA's work early.
-constexpr int NB = 3;
-template <int W>
-__global__ void __launch_bounds__(kThreads, 2) k_spmm32_stream(int n, int nrhs, const float* X1,
-                                                               const float* W1, const float* Y2,
-                                                               const float* Z2, const float* x,
-                                                               float* y, long ld) {
-  constexpr int p = (W - 1) / 2;
-  extern __shared__ __align__(128) float sm[];
-  const int N = n * n;
-  const int Np = (N + 3) & ~3;                       // 16-byte multiple
-  float* xb = sm;                                    // [NB][Np]
-  float* tm = xb + (size_t)NB * Np;                  // [n + 2p][n], zero halo rows
-  float* tk = tm + (size_t)(n + 2 * p) * n;
-  float* y2 = tk + (size_t)(n + 2 * p) * n;
-  float* z2 = y2 + (size_t)n * W;
-  // every region above holds an even number of floats: the barriers are 8-byte aligned
-  uint64_t* bar = (uint64_t*)(z2 + (size_t)n * W);
-  const bool haveK = W1 != nullptr;
-  const int G = (n + 3) / 4;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NB; ++s) mbar_init(&bar[s], 1);
-    fence_mbar_init();
-  }
-  for (int i = threadIdx.x; i < n * W; i += blockDim.x) {
-    y2[i] = Y2[i];
-    z2[i] = Z2 ? Z2[i] : 0.0f;
-  }
-  for (int i = threadIdx.x; i < p * n; i += blockDim.x) {
-    tm[i] = 0.0f;
-    tk[i] = 0.0f;
-    tm[(size_t)(n + p) * n + i] = 0.0f;
-    tk[(size_t)(n + p) * n + i] = 0.0f;
-  }
+// Shared-memory layout for band width W and grids with J*G <= NC (G groups of
+// J grid lines), all strides compile-time so that every band tap is an
+// immediate offset.  (tm, tk) are stored interleaved, element (r, c) as the
+// pair at 2 (r NS + c): stage 1 writes its (tm, tk) accumulator pairs as they
+// are, stage 2 reads one pair per 64-bit load.
+template <int W, int NC>
+struct Lay {
+  static constexpr int p = (W - 1) / 2;
+  static constexpr int J = W <= 9 ? 4 : 2;            // grid columns / rows per thread
+  static constexpr int V = (J + W - 1 + J - 1) / J;   // J-vectors in a stage-1 window
+  static constexpr int XS = (NC - J + J * V + 3) / 4 * 4;  // padded x row, data at [p, p + n)
+  static constexpr int R = NC + W - 1;                // (tm, tk) rows, data at [p, p + n)
+  static constexpr int NS = NC;                       // (tm, tk) row stride in pairs
+  static constexpr int BUF = 2 * R * NS;              // floats per (tm, tk) buffer
+  static_assert(XS % 4 == 0 && NS % 2 == 0, "vector alignment");
+};
+
+template <int W, int NC>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_spmm32(int n, int nrhs, int nb, const float* __restrict__ M1, const float* __restrict__ K1,
+             SpmmCoef cf, const float* __restrict__ x, float* __restrict__ y, long ld) {
+  using L = Lay<W, NC>;
+  constexpr int p = L::p, J = L::J, V = L::V, XS = L::XS, NS = L::NS;
+  using VecJ = typename std::conditional<J == 4, float4, float2>::type;
+  const int G = (n + J - 1) / J, slot = n * XS;
+  extern __shared__ __align__(16) float sm[];
+  float* ring = sm;                               // [nb][n][XS]
+  float* tb = sm + (size_t)nb * slot;             // [2][R][NS][tm, tk]
+  const int total = nb * slot + 2 * L::BUF;
+  for (int i = threadIdx.x; i < total; i += kThreads) sm[i] = 0.0f;  // halos stay zero
   __syncthreads();
   const int cnt = nrhs > (int)blockIdx.x ? (nrhs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-  const uint32_t bytes = (uint32_t)Np * 4u;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < NB && k < cnt; ++k)
-      bulk_load(xb + (size_t)k * Np, x + (size_t)(blockIdx.x + k * gridDim.x) * ld, bytes, &bar[k]);
-  const int R1 = blockDim.x / G;
-  const int g = threadIdx.x % G, r0 = threadIdx.x / G;
-  const bool on1 = r0 < R1;
-  float a[4][W], kk[4][W];
+  auto column = [&](int k) { return (size_t)blockIdx.x + (size_t)k * gridDim.x; };
+
+  if (threadIdx.x < kG1) {
+    // ------------------------------ stage 1 ------------------------------
+    const int t = threadIdx.x;
+    const int R1 = kG1 / G, g = t % G, r0 = t / G;
+    const bool on = r0 < R1;
+    float2 ab[J][W];  // (X1, W1) band pairs of grid columns J g + j
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const int ix = 4 * g + j;
+    for (int j = 0; j < J; ++j) {
+      const int ix = J * g + j;
 #pragma unroll
-    for (int o = 0; o < W; ++o) {
-      a[j][o] = ix < n ? X1[(size_t)ix * W + o] : 0.0f;
-      kk[j][o] = (ix < n && haveK) ? W1[(size_t)ix * W + o] : 0.0f;
-    }
-  }
-  const int R2 = blockDim.x / n;
-  const int ix2 = threadIdx.x % n, c0 = threadIdx.x / n;
-  const bool on2 = c0 < R2;
-  int done = cnt;
-  for (int k = 0; k < cnt; ++k) {
-    const int s = k % NB;
-    const bool got = mbar_wait(&bar[s], (uint32_t)(k / NB) & 1u);
-    if (__syncthreads_or(!got)) {
-      done = k;
-      break;
-    }
-    const float* xs = xb + (size_t)s * Np;
-    float* yb = y + (size_t)(blockIdx.x + k * gridDim.x) * ld;
-    if (on1) {
-      for (int iy = r0; iy < n; iy += R1) {
-        const float* row = xs + (size_t)iy * n;
-        float v[W + 3];
-#pragma unroll
-        for (int q = 0; q < W + 3; ++q) {
-          const int ix = 4 * g + q - p;
-          const int ic = ix < 0 ? 0 : (ix >= n ? n - 1 : ix);  // in-bounds address always
-          v[q] = (ix >= 0 && ix < n) ? row[ic] : 0.0f;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int ix = 4 * g + j;
-          float sm_ = 0.0f, sk = 0.0f;
-#pragma unroll
-          for (int o = 0; o < W; ++o) {
-            sm_ = fmaf(a[j][o], v[j + o], sm_);
-            sk = fmaf(kk[j][o], v[j + o], sk);
-          }
-          if (ix < n) {
-            tm[(size_t)(iy + p) * n + ix] = sm_;
-            tk[(size_t)(iy + p) * n + ix] = sk;
-          }
-        }
+      for (int o = 0; o < W; ++o) {
+        const float m = ix < n ? M1[ix * W + o] : 0.0f;
+        const float kv = ix < n ? K1[ix * W + o] : 0.0f;
+        ab[j][o] = make_float2(fmaf(cf.xk, kv, cf.xm * m), fmaf(cf.wk, kv, cf.wm * m));
       }
     }
-    __syncthreads();
-    // buffer s is free: stream in column k + NB
-    if (threadIdx.x == 0 && k + NB < cnt) {
-      fence_proxy_async();
-      bulk_load(xb + (size_t)s * Np, x + (size_t)(blockIdx.x + (k + NB) * gridDim.x) * ld, bytes,
-                &bar[s]);
-    }
-    if (on2) {
-      for (int gy = c0; 4 * gy < n; gy += R2) {
-        float um[4 + W - 1], uk[4 + W - 1];
-#pragma unroll
-        for (int q = 0; q < 4 + W - 1; ++q) {
-          const int r = 4 * gy + q;
-          const bool in = r < n + 2 * p;
-          um[q] = in ? tm[(size_t)r * n + ix2] : 0.0f;
-          uk[q] = in ? tk[(size_t)r * n + ix2] : 0.0f;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int iy = 4 * gy + j;
-          if (iy >= n) break;
-          float sacc = 0.0f;
-#pragma unroll
-          for (int o = 0; o < W; ++o) {
-            sacc = fmaf(y2[iy * W + o], um[j + o], sacc);
-            sacc = fmaf(z2[iy * W + o], uk[j + o], sacc);
-          }
-          yb[(size_t)iy * n + ix2] = sacc;
+    // copies: warp w takes grid rows w, w + 7, ...; lane l columns l, l + 32, l + 64
+    const int wq = t >> 5, lane = t & 31;
+    const int c0 = lane < n, c1 = lane + 32 < n, c2 = lane + 64 < n;
+    const uint32_t ring_s = smem_u32(ring) + 4u * (p + lane);
+    auto issue = [&](int k, int s) {  // column k of this CTA into ring slot s
+      if (k < cnt) {
+        const float* src = x + column(k) * ld + lane;
+        const uint32_t dst = ring_s + 4u * (uint32_t)(s * slot);
+        for (int iy = wq; iy < n; iy += kG1 / 32) {
+          const float* sr = src + iy * n;
+          const uint32_t dr = dst + 4u * (uint32_t)(iy * XS);
+          cp_async4_if(dr, sr, c0);
+          cp_async4_if(dr + 128u, sr + 32, c1);
+          cp_async4_if(dr + 256u, sr + 64, c2);
         }
       }
+      cp_async_commit();  // empty groups keep the group count uniform
+    };
+    for (int s = 0; s + 1 < nb; ++s) issue(s, s);
+    int sk = 0;  // ring slot of column k
+    for (int k = 0; k < cnt; ++k) {
+      cp_async_wait_ring(nb);
+      bar_sync(kBarCopy, kG1);  // column k complete; slot (k - 1) % nb no longer read
+      issue(k + nb - 1, sk == 0 ? nb - 1 : sk - 1);
+      const float* xk = ring + sk * slot + J * g;
+      float* tm = tb + (k & 1) * L::BUF + 2 * (p * NS + J * g);
+      if (k >= 2) bar_sync(kBarEmpty + (k & 1), kThreads);
+      if (on) {
+        for (int iy = r0; iy < n; iy += R1) {
+          // x[iy][J g - p + q] sits at ring[iy][J g + q]
+          const VecJ* row = (const VecJ*)(xk + iy * XS);
+          float v[J * V];
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const VecJ w = row[q];
+            v[J * q] = w.x;
+            v[J * q + 1] = w.y;
+            if constexpr (J == 4) {
+              v[J * q + 2] = w.z;
+              v[J * q + 3] = w.w;
+            }
+          }
+          float2 acc[J];  // (tm, tk) of grid columns J g + j
+#pragma unroll
+          for (int j = 0; j < J; ++j)
+            acc[j] = taps<W>([&](int o) { return Term{ab[j][o], make_float2(v[j + o], v[j + o])}; });
+          // columns J g + j >= n carry zero bands; they land in the row padding
+          float4* d = (float4*)(tm + 2 * iy * NS);
+#pragma unroll
+          for (int j = 0; j < J; j += 2) d[j / 2] = make_float4(acc[j].x, acc[j].y, acc[j + 1].x, acc[j + 1].y);
+        }
+      }
+      bar_arrive(kBarFull + (k & 1), kThreads);
+      sk = sk + 1 == nb ? 0 : sk + 1;
     }
-    __syncthreads();
+    cp_async_wait<0>();
+  } else {
+    // ------------------------------ stage 2 ------------------------------
+    // half-warp h takes row groups h, h + 18, ...; lane c of it columns c, c + 16, ...
+    // (16 consecutive pairs: one 128-byte wavefront per half-warp and load)
+    const int u = threadIdx.x - kG1;
+    const int h = u >> 4, c = u & 15;
+    auto coefs = [&](int gy, float2 (&yz)[J][W]) {  // (Y2, Z2) band pairs of rows J gy + j
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const int iy = J * gy + j;
+#pragma unroll
+        for (int o = 0; o < W; ++o) {
+          const float m = iy < n ? M1[iy * W + o] : 0.0f;
+          const float kv = iy < n ? K1[iy * W + o] : 0.0f;
+          yz[j][o] = make_float2(fmaf(cf.yk, kv, cf.ym * m), fmaf(cf.zk, kv, cf.zm * m));
+        }
+      }
+    };
+    auto rows = [&](int gy, const float2 (&yz)[J][W], const float* tm, float* yb) {
+      const float2* tg = (const float2*)tm + J * gy * NS;
+      float* yg = yb + (size_t)(J * gy) * n;
+      const int jn = J * gy < n ? min(J, n - J * gy) : 0;  // valid rows of the group
+      for (int ix = c; ix < n; ix += 16) {
+        // (tm, tk)[iy - p + o][ix] sits at row iy + o (halo rows)
+        float2 w[J + W - 1];
+#pragma unroll
+        for (int q = 0; q < J + W - 1; ++q) w[q] = tg[q * NS + ix];
+        float* yc = yg + ix;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          const float2 acc = taps<W>([&](int o) { return Term{yz[j][o], w[j + o]}; });
+          if (j < jn) yc[j * n] = acc.x + acc.y;
+        }
+      }
+    };
+    float2 yz[J][W];
+    const bool one = G <= kHalves;  // one row group per half-warp: bands stay in registers
+    if (one) coefs(h, yz);
+    for (int k = 0; k < cnt; ++k) {
+      bar_sync(kBarFull + (k & 1), kThreads);
+      const float* tm = tb + (k & 1) * L::BUF;
+      float* yb = y + column(k) * ld;
+      if (one) {
+        if (h < G) rows(h, yz, tm, yb);
+      } else {
+        for (int gy = h; gy < G; gy += kHalves) {
+          coefs(gy, yz);
+          rows(gy, yz, tm, yb);
+        }
+      }
+      if (k + 2 < cnt) bar_arrive(kBarEmpty + (k & 1), kThreads);
+    }
   }
-  // after an early exit, drain the copies still in flight (bounded) before
-  // the CTA's shared memory is released
-  if (threadIdx.x == 0)
-    for (int k = done; k < cnt && k < done + NB; ++k)
-      mbar_wait(&bar[k % NB], (uint32_t)(k / NB) & 1u);
 }
 
-template <int W>
-size_t stream_smem(int n) {
-  const int p = (W - 1) / 2, N = n * n, Np = (N + 3) & ~3;
-  return sizeof(float) * ((size_t)NB * Np + 2 * (size_t)(n + 2 * p) * n + 2 * (size_t)n * W) +
-         8 * NB;
+constexpr int kCaps[] = {68, 84};  // J*G limits of the two layouts
+
+template <int W, int NC>
+size_t smem_of(int n, int nb) {
+  using L = Lay<W, NC>;
+  return sizeof(float) * ((size_t)nb * n * L::XS + 2 * (size_t)L::BUF);
 }
 
+// layout cap and ring depth for an n x n grid (cap 0: does not fit)
 template <int W>
-cudaError_t launch_w(int n, int nrhs, const float* X1, const float* W1, const float* Y2,
-                     const float* Z2, const float* x, float* y, long ld, int grid, cudaStream_t st) {
-  if (ld % 4 == 0) {
-    const size_t smem = stream_smem<W>(n);
-    cudaError_t e = cudaFuncSetAttribute(k_spmm32_stream<W>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    k_spmm32_stream<W><<<grid, kThreads, smem, st>>>(n, nrhs, X1, W1, Y2, Z2, x, y, ld);
-    return cudaGetLastError();
+void plan(int n, size_t smem_max, int* cap, int* nb) {
+  constexpr int J = W <= 9 ? 4 : 2;
+  const int JG = (n + J - 1) / J * J;
+  *cap = 0;
+  *nb = 0;
+  for (int d = kMaxSlots; d >= 2 && !*cap; --d) {
+    if (JG <= kCaps[0] && smem_of<W, kCaps[0]>(n, d) <= smem_max) *cap = kCaps[0];
+    else if (JG <= kCaps[1] && smem_of<W, kCaps[1]>(n, d) <= smem_max) *cap = kCaps[1];
+    if (*cap) *nb = d;
   }
-  const int p = (W - 1) / 2;
-  const int G = (n + 3) / 4;
-  const int xs = ((4 * G + 2 * p + 3) / 4) * 4;
-  const size_t smem = sizeof(float) * ((size_t)n * xs + 2 * (size_t)(n + 2 * p) * n + 2 * (size_t)n * W);
-  cudaError_t e = cudaFuncSetAttribute(k_spmm32<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+}
+
+template <int W, int NC>
+cudaError_t launch_nc(int n, int nrhs, int nb, const float* M1, const float* K1, SpmmCoef cf,
+                      const float* x, float* y, long ld, int grid, cudaStream_t st) {
+  const size_t smem = smem_of<W, NC>(n, nb);
+  cudaError_t e = cudaFuncSetAttribute(k_spmm32<W, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  k_spmm32<W><<<grid, kThreads, smem, st>>>(n, nrhs, X1, W1, Y2, Z2, x, y, ld);
+  k_spmm32<W, NC><<<grid, kThreads, smem, st>>>(n, nrhs, nb, M1, K1, cf, x, y, ld);
   return cudaGetLastError();
+}
+
+template <int W>
+int slots_w(int n, size_t smem_max) {
+  int cap, nb;
+  plan<W>(n, smem_max, &cap, &nb);
+  return nb;
+}
+
+template <int W>
+cudaError_t launch_w(int n, int nrhs, const float* M1, const float* K1, SpmmCoef cf,
+                     const float* x, float* y, long ld, int grid, size_t smem_max, cudaStream_t st) {
+  int cap, nb;
+  plan<W>(n, smem_max, &cap, &nb);
+  if (cap == kCaps[0]) return launch_nc<W, kCaps[0]>(n, nrhs, nb, M1, K1, cf, x, y, ld, grid, st);
+  if (cap == kCaps[1]) return launch_nc<W, kCaps[1]>(n, nrhs, nb, M1, K1, cf, x, y, ld, grid, st);
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-size_t spmm32_smem(int n, int p) {
-  const int W = 2 * p + 1, G = (n + 3) / 4, xs = ((4 * G + 2 * p + 3) / 4) * 4;
-  return sizeof(float) * ((size_t)n * xs + 2 * (size_t)(n + 2 * p) * n + 2 * (size_t)n * W);
+int spmm32_slots(int n, int p, size_t smem_max) {
+  switch (p) {
+    case 2: return slots_w<5>(n, smem_max);
+    case 3: return slots_w<7>(n, smem_max);
+    case 4: return slots_w<9>(n, smem_max);
+    case 5: return slots_w<11>(n, smem_max);
+    case 6: return slots_w<13>(n, smem_max);
+    case 7: return slots_w<15>(n, smem_max);
+    case 8: return slots_w<17>(n, smem_max);
+    default: return 0;
+  }
 }
 
-cudaError_t launch_spmm32(int n, int p, int nrhs, const float* X1, const float* W1,
-                          const float* Y2, const float* Z2, const float* x, float* y, long ld,
-                          int grid, cudaStream_t st) {
+cudaError_t launch_spmm32(int n, int p, int nrhs, const float* M1, const float* K1, SpmmCoef cf,
+                          const float* x, float* y, long ld, int grid, size_t smem_max,
+                          cudaStream_t st) {
   switch (p) {
-    case 1: return launch_w<3>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    case 2: return launch_w<5>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    case 3: return launch_w<7>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    case 4: return launch_w<9>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    case 5: return launch_w<11>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    case 6: return launch_w<13>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    case 7: return launch_w<15>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
-    default: return launch_w<17>(n, nrhs, X1, W1, Y2, Z2, x, y, ld, grid, st);
+    case 2: return launch_w<5>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    case 3: return launch_w<7>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    case 4: return launch_w<9>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    case 5: return launch_w<11>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    case 6: return launch_w<13>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    case 7: return launch_w<15>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    case 8: return launch_w<17>(n, nrhs, M1, K1, cf, x, y, ld, grid, smem_max, st);
+    default: return cudaErrorInvalidValue;
   }
 }
 

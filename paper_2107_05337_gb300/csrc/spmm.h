@@ -5,11 +5,21 @@
 
 namespace igm {
 
-// y_b = (Y2 (x) X1 + Z2 (x) W1) x_b for b < nrhs (W1, Z2 may be null), 1D bands
-// [n][2p+1]; x, y [nrhs][ld] FP32 with n*n <= ld.  grid: persistent CTAs.
-cudaError_t launch_spmm32(int n, int p, int nrhs, const float* X1, const float* W1,
-                          const float* Y2, const float* Z2, const float* x, float* y, long ld,
-                          int grid, cudaStream_t st);
-size_t spmm32_smem(int n, int p);
+// The four 1D factors of y = (Y2 (x) X1 + Z2 (x) W1) x as combinations of the
+// bands of M1 and K1: X1 = xm M1 + xk K1, W1 = wm M1 + wk K1, and so on.
+struct SpmmCoef {
+  float xm, xk, wm, wk, ym, yk, zm, zk;
+};
+
+// y_b for b < nrhs; M1, K1 the 1D interior bands [n][2p+1] (entry o of row i
+// couples column i - p + o), FP32 in device memory; x, y [nrhs][ld] FP32 with
+// n*n <= ld, any alignment.  grid: persistent CTAs, one per SM.  smem_max: the
+// device's opt-in shared memory per block; cudaErrorInvalidValue when the
+// grid does not fit (spmm32_slots == 0) or p is outside [2, 8].
+cudaError_t launch_spmm32(int n, int p, int nrhs, const float* M1, const float* K1, SpmmCoef cf,
+                          const float* x, float* y, long ld, int grid, size_t smem_max,
+                          cudaStream_t st);
+// copy ring depth the kernel would use for an n x n grid (0: does not fit)
+int spmm32_slots(int n, int p, size_t smem_max);
 
 }  // namespace igm

@@ -239,6 +239,50 @@ def test_batched_fp32_operator_apply_matches_oracle(B, p, nel, which):
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-6
 
 
+@pytest.mark.parametrize("p,nel,pad", [(2, 16, 3), (3, 20, 1), (5, 12, 0), (2, 80, 5)])
+def test_batched_fp32_apply_many_columns_per_cta(B, p, nel, pad):
+    """Several columns per persistent CTA (ring-slot reuse, both (tm, tk)
+    buffers, the buffer hand-back), a leading dimension that is not a multiple
+    of four, and (nel = 80: 80 grid lines) the wider shared-memory layout;
+    every column against the oracle's assembled M + c K."""
+    import torch
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    c = 1.0 / 256
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    nrhs = 4 * sms + 37
+    X = np.random.default_rng(7).standard_normal((nrhs, d.N + pad))
+    want = ((d.M + c * d.K) @ X[:, :d.N].T).T
+    prob = B.Problem(p, nel)
+    Xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    Y = prob.apply_f32("A", Xd, c=c)
+    got = Y[:, :d.N].double().cpu().numpy()
+    err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert err.max() < 2e-6
+    assert torch.equal(Xd, torch.as_tensor(X, dtype=torch.float32, device="cuda"))
+
+
+def test_batched_fp32_apply_full_size_sampled(B):
+    """The measured configuration (p = 4, h = 1/64, 8192 columns padded to a
+    multiple of four floats, one launch): sampled columns, including the first
+    and last of a CTA's share, against the oracle."""
+    import torch
+    p, nel, ncol = 4, 64, 8192
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    c = 1.0 / 256
+    ld = (d.N + 3) // 4 * 4
+    g = torch.Generator(device="cuda").manual_seed(11)
+    Xd = torch.randn((ncol, ld), dtype=torch.float32, device="cuda", generator=g)
+    Y = B.Problem(p, nel).apply_f32("A", Xd, c=c)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    cols = sorted({0, 1, sms - 1, sms, 2 * sms + 5, ncol // 2, ncol - sms, ncol - 1}
+                  | set(np.random.default_rng(8).integers(0, ncol, 16).tolist()))
+    X = Xd[cols, :d.N].double().cpu().numpy()
+    want = ((d.M + c * d.K) @ X.T).T
+    got = Y[cols, :d.N].double().cpu().numpy()
+    err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert err.max() < 2e-6
+
+
 def test_batched_fp32_apply_rejects_curved_map(B):
     import torch
     prob = B.Problem(2, 8, "quarter_annulus")
