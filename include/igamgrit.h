@@ -225,7 +225,9 @@ typedef struct {
   int Nt;          /* fine time steps */
   int m;           /* coarsening factor (Sec. 3: dt_C = m dt_F) */
   int max_levels;  /* time levels including the fine one (2 = two-level) */
-  int min_coarse;  /* stop coarsening once a level has <= min_coarse steps */
+  int min_coarse;  /* stop coarsening once a level has <= min_coarse steps; a level of N_l
+                      steps coarsens to floor(N_l/m) (needs N_l >= m); when m does not divide
+                      N_l its last N_l mod m points are F-points of a partial interval */
   int relax;       /* 0: F-relaxation, 1: FCF-relaxation (Sec. 3) */
   double tol;      /* stop when rho_k <= tol * rho_0 (C-point residual 2-norm) */
   int max_iter;    /* iteration limit */

@@ -18,7 +18,10 @@ Test infrastructure (see ``oracle/__init__``).  Pinned by
     nothing when the spatial solves are exact.
 
 The method (Sec. 3, the MGRIT algorithm box; ideal interpolation P):
-  level l has time step dt_l = m^l dt and N_l = N_t / m^l steps; on level l
+  level l has time step dt_l = m^l dt and N_{l+1} = floor(N_l / m) steps: the
+  C-points of level l are the multiples of m, and when m does not divide N_l
+  the last N_l - m N_{l+1} points form a partial interval of F-points only
+  (relaxed from the last C-point, never injected); on level l
   the step is  u_n = Phi_l(u_{n-1}) + g_n,  Phi_l = Psi_l R_l,
   Psi_l = (M + theta kappa dt_l K)^{-1}, R_l = M - (1-theta) kappa dt_l K
   (rediscretised on every level; theta = 1 is backward Euler, Sec. 3).  On the
@@ -44,7 +47,9 @@ Readings of points the paper leaves open or prints garbled (also in the design doc):
   * The interpolation's inverse A_FF^{-1} (missing in the printed P) is an
     F-relaxation from the corrected C-points.
   * Level count: coarsen while the level has more than ``min_coarse`` steps,
-    N_l is divisible by m and fewer than ``max_levels`` levels exist.
+    has at least one full interval (N_l >= m) and fewer than ``max_levels``
+    levels exist.  A step count not divisible by m leaves a partial last
+    interval of F-points (the coarsening XBraid, the paper's library, uses).
   * Stopping test: after the relaxation of iteration k, rho_k =
     sqrt(sum_j ||r_j||_2^2) over the fine-level C-points; stop when
     rho_k <= tol * rho_0 (the reported iteration count is k, the number of
@@ -64,8 +69,7 @@ import numpy as np
 
 def level_sizes(Nt, m, max_levels=30, min_coarse=4):
     sizes = [Nt]
-    while len(sizes) < max_levels and sizes[-1] > min_coarse and sizes[-1] % m == 0 \
-            and sizes[-1] // m >= 1:
+    while len(sizes) < max_levels and sizes[-1] > min_coarse and sizes[-1] // m >= 1:
         sizes.append(sizes[-1] // m)
     return sizes
 
@@ -125,10 +129,13 @@ class MGRIT:
 
     def f_relax(self, l):
         m = self.m
-        for j in range(self.sizes[l] // m):
+        nint = self.sizes[l] // m
+        for j in range(nint):
             for k in range(1, m):
                 n = j * m + k
                 self.W[l][n] = self.phi(l, n)
+        for n in range(nint * m + 1, self.sizes[l] + 1):  # partial last interval
+            self.W[l][n] = self.phi(l, n)
 
     def c_relax(self, l):
         m = self.m

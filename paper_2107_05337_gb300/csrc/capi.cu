@@ -1260,6 +1260,10 @@ struct mgrit_handle {
   }
 };
 
+// CTAs of the F-relaxation sweeps on a level of Nl steps: one per interval,
+// plus one for a partial last interval
+static int f_grid(int Nl, int m) { return Nl / m + (Nl % m != 0); }
+
 extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, mgrit_handle** out) {
   if (!ops || !opts || !out) return fail(IGM_ERR_ARG, "null argument");
   const mgrit_opts& o = *opts;
@@ -1280,8 +1284,9 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   l0.Nl = o.Nt;
   l0.dt = o.T / o.Nt;
   L.push_back(l0);
-  while ((int)L.size() < o.max_levels && L.back().Nl > o.min_coarse && L.back().Nl % o.m == 0 &&
-         L.back().Nl / o.m >= 1) {
+  // coarsen to floor(N_l / m) C-points; a remainder leaves a partial last
+  // interval of F-points on level l
+  while ((int)L.size() < o.max_levels && L.back().Nl > o.min_coarse && L.back().Nl / o.m >= 1) {
     Level nx;
     nx.Nl = L.back().Nl / o.m;
     nx.dt = L.back().dt * o.m;
@@ -1301,7 +1306,7 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
       L[l].g = (double*)up.raw(sizeof(double) * (size_t)(L[l].Nl + 1) * N);
     }
   }
-  for (int l = 0; l < nlev; ++l) mg->max_grid = std::max(mg->max_grid, L[l].Nl / o.m);
+  for (int l = 0; l < nlev; ++l) mg->max_grid = std::max(mg->max_grid, f_grid(L[l].Nl, o.m));
   mg->scratch = (double*)up.raw(sizeof(double) * 2 * (size_t)N * mg->max_grid);
   mg->norms = (double*)up.raw(sizeof(double) * (size_t)mg->max_grid);
   mg->counters = (unsigned long long*)up.raw(sizeof(unsigned long long) * 2);
@@ -1414,15 +1419,17 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
 // C-point residual, injected into g^(1); copies the per-interval norms.
 static igm_status part_A(mgrit_handle* mg, bool first, double* U, const double* fhat,
                          cudaStream_t st, bool profile) {
-  const int nint0 = mg->L[0].Nl / mg->o.m;
+  const int nint0 = mg->L[0].Nl / mg->o.m, nf0 = f_grid(mg->L[0].Nl, mg->o.m);
   if (mg->o.relax == 1) {
     // the leading F-relaxation is skipped after the first iteration: the
     // interpolation has just made the F-points Phi-consistent
-    if (first) SWEEP(0, MODE_F, nint0, nullptr);
+    if (first) SWEEP(0, MODE_F, nf0, nullptr);
     SWEEP(0, MODE_C, nint0, nullptr);
-    SWEEP(0, MODE_FR, nint0, mg->norms);
+    SWEEP(0, MODE_FR, nf0, mg->norms);
+  } else if (first) {
+    SWEEP(0, MODE_FR, nf0, mg->norms);
   } else {
-    SWEEP(0, first ? MODE_FR : MODE_R, nint0, mg->norms);
+    SWEEP(0, MODE_R, nint0, mg->norms);
   }
   CU(cudaMemcpyAsync(mg->hnorms, mg->norms, sizeof(double) * nint0, cudaMemcpyDeviceToHost, st));
   return IGM_OK;
@@ -1441,12 +1448,12 @@ static igm_status visit(mgrit_handle* mg, int l, int kind, double* U, const doub
     SWEEP(l, MODE_SEQ, 1, nullptr);
     return IGM_OK;
   }
-  const int ni = L[l].Nl / mg->o.m;
+  const int ni = L[l].Nl / mg->o.m, nf = f_grid(L[l].Nl, mg->o.m);
   if (mg->o.relax == 1) {
-    SWEEP(l, MODE_F, ni, nullptr);
+    SWEEP(l, MODE_F, nf, nullptr);
     SWEEP(l, MODE_C, ni, nullptr);
   }
-  SWEEP(l, MODE_FR, ni, nullptr);
+  SWEEP(l, MODE_FR, nf, nullptr);
   CU(cudaMemsetAsync(L[l + 1].W, 0, sizeof(double) * (size_t)(L[l + 1].Nl + 1) * N, st));
   const int sub[3][2] = {{0, -1}, {1, 0}, {2, 2}};
   for (int v = 0; v < 2; ++v) {
@@ -1455,7 +1462,7 @@ static igm_status visit(mgrit_handle* mg, int l, int kind, double* U, const doub
     igm_status r = visit(mg, l + 1, k, U, fhat, st, profile);
     if (r != IGM_OK) return r;
   }
-  SWEEP(l, MODE_CF, ni, nullptr);
+  SWEEP(l, MODE_CF, nf, nullptr);
   return IGM_OK;
 }
 
@@ -1474,7 +1481,7 @@ static igm_status part_B(mgrit_handle* mg, double* U, const double* fhat, cudaSt
     igm_status r = visit(mg, 1, k, U, fhat, st, profile);
     if (r != IGM_OK) return r;
   }
-  SWEEP(0, MODE_CF, L[0].Nl / mg->o.m, nullptr);
+  SWEEP(0, MODE_CF, f_grid(L[0].Nl, mg->o.m), nullptr);
   return IGM_OK;
 }
 
@@ -1502,7 +1509,7 @@ static igm_status part_learned(mgrit_handle* mg, double* U, const double* fhat, 
                      cudaMemcpyDeviceToDevice, st));
   CU(phic_fas_coarse(mg->phic->net, Nc, m, U, mg->L[1].g, mg->fas_tau, mg->fas_v, mg->L[1].W,
                      mg->phic->work, st));
-  SWEEP(0, MODE_CF, mg->L[0].Nl / m, nullptr);
+  SWEEP(0, MODE_CF, f_grid(mg->L[0].Nl, m), nullptr);
   return IGM_OK;
 }
 

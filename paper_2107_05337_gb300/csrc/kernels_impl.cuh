@@ -96,30 +96,39 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
 
 // One CTA per interval j of the level (or one CTA for the sequential coarsest
 // level).  Every mode is a run of consecutive steps n0..n1 of one interval,
-// the last of which may be the C-point residual.
+// the last of which may be the C-point residual.  When m does not divide N_l,
+// CTA j = nint (launched in the F-relaxation modes only) owns the partial last
+// interval: steps nint*m + 1 .. N_l, all F-points.
 template <int PREC>
 __global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
   __shared__ double red[32];
   Pipe pp;
   char* arena = cta_setup(a.P, a.garena, pp);
   const int j = blockIdx.x, m = a.m, N = a.P.N;
-  int n0 = j * m + 1, n1 = j * m + m - 1;
+  const bool tail = j == a.nint;
+  int n0 = j * m + 1, n1 = tail ? a.Nl : j * m + m - 1;
   bool resid = false;
   switch (a.mode) {
     case MODE_C: n0 = n1 = (j + 1) * m; break;
     case MODE_R: n0 = n1 = (j + 1) * m; resid = true; break;
-    case MODE_FR: n1 = (j + 1) * m; resid = true; break;
+    case MODE_FR:
+      if (!tail) {
+        n1 = (j + 1) * m;
+        resid = true;
+      }
+      break;
     case MODE_SEQ: n0 = 1; n1 = a.Nl; break;
     case MODE_CF:
-      // u_{jm} += u^(l+1)_j at the C-point this CTA starts from; the last CTA
-      // also corrects the final C-point (read by no F-relaxation)
+      // u_{jm} += u^(l+1)_j at the C-point this CTA starts from; when the
+      // level ends on a C-point, the last CTA also corrects it (read by no
+      // F-relaxation)
       if (j >= 1) {
         double* w = a.W + (size_t)(j * m) * N;
         const double* wc = a.Wc + (size_t)j * N;
         const double* gc = a.gc + (size_t)j * N;
         IGM_FOR_CTA(i, N) w[i] += wc[i] + gc[i];
       }
-      if (j == a.nint - 1) {
+      if (j == a.nint - 1 && a.Nl == a.nint * m) {
         double* w = a.W + (size_t)a.Nl * N;
         const double* wc = a.Wc + (size_t)a.nint * N;
         const double* gc = a.gc + (size_t)a.nint * N;

@@ -208,10 +208,46 @@ def test_mgrit_nt_equals_m_and_sequential_fallback(B):
     d, seq = _oracle_heat(2, 8, 0.5, 4)
     U, st = _gpu_heat(B, 2, 8, 0.5, 4, m=4, min_coarse=0, tol=1e-12, pmg=dict(tol=1e-13))
     assert st["iters"] <= 1 and _rel(U, seq) < 1e-10
-    # N_t not divisible by m: no coarse level, plain sequential stepping
+    # N_t = m + 3: one interval and a partial last interval of three F-points
+    # over a one-step coarse level: exact after the first correction
     d, seq = _oracle_heat(2, 8, 0.5, 7)
     U, st = _gpu_heat(B, 2, 8, 0.5, 7, m=4, tol=1e-12, pmg=dict(tol=1e-13))
+    assert st["levels"] == 2 and st["iters"] <= 1 and _rel(U, seq) < 1e-10
+    # fewer steps than m: no coarse level, plain sequential stepping
+    d, seq = _oracle_heat(2, 8, 0.5, 3)
+    U, st = _gpu_heat(B, 2, 8, 0.5, 3, m=4, min_coarse=0, tol=1e-12, pmg=dict(tol=1e-13))
     assert st["levels"] == 1 and _rel(U, seq) < 1e-10
+
+
+def test_mgrit_ragged_fixed_iterations_match_oracle(B):
+    """Step counts that m does not divide (N_t = 50, m = 4: levels 50, 12, 3,
+    a partial last interval on the fine level): fixed iterations, FP64, tight
+    spatial tolerance, against the oracle iterate and residual history."""
+    p, nel, T, Nt, m = 2, 8, 1.0, 50, 4
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    u0, fhat = d.project(S), d.load_vector(S)
+    for k in (1, 2):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, T, Nt, m, mgrit.direct_factory(d.M, d.K), u0, fhat, C,
+                         min_coarse=2)
+        assert mg.sizes == [50, 12, 3]
+        Uo, it, hist = mg.run(tol=0.0, max_iter=k)
+        U, st = _gpu_heat(B, p, nel, T, Nt, check=False, m=m, min_coarse=2, tol=0.0, max_iter=k,
+                          pmg=dict(tol=1e-14, precision=0, max_cycles=60))
+        assert st["levels"] == 3 and st["iters"] == k
+        assert _rel(U, Uo) < 1e-10, k
+        np.testing.assert_allclose(st["res_hist"], hist, rtol=1e-8)
+
+
+@pytest.mark.parametrize("Nt,m,cycle", [(250, 2, 0), (99, 4, 2)])
+def test_mgrit_ragged_converged(B, Nt, m, cycle):
+    """Partial last intervals on several levels (N_t = 250, m = 2: seven
+    levels; N_t = 99, m = 4 with W-cycles), mixed form, against sequential
+    stepping."""
+    d, seq = _oracle_heat(2, 8, 1.0, Nt)
+    U, st = _gpu_heat(B, 2, 8, 1.0, Nt, m=m, min_coarse=2, cycle=cycle, tol=1e-12, max_iter=60,
+                      pmg=dict(tol=1e-13, precision=1))
+    assert st["levels"] == len(mgrit.level_sizes(Nt, m, min_coarse=2))
+    assert _rel(U, seq) < 1e-10, st
 
 
 def test_invalid_arguments_raise(B):

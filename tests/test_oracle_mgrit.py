@@ -38,11 +38,13 @@ def test_single_interval_exact():
     np.testing.assert_allclose(U, seq, atol=1e-14 * np.abs(seq).max())
 
 
+@pytest.mark.parametrize("Nt", [60, 62])
 @pytest.mark.parametrize("relax,reach", [("F", 1), ("FCF", 2)])
-def test_exactness_propagation(relax, reach):
-    """Two-level: after k iterations the first reach*k C-points are exact."""
+def test_exactness_propagation(relax, reach, Nt):
+    """Two-level: after k iterations the first reach*k C-points are exact (also
+    with a partial last interval, N_t = 62 = 20 m + 2)."""
     d, u0, fhat = _problem()
-    Nt, m = 60, 3
+    m = 3
     seq = timestep.sequential(d.M, d.K, 1.0, 1.0, Nt, u0, fhat, C)
     for k in (1, 2, 3):
         mg = mgrit.MGRIT(d.M, d.K, 1.0, 1.0, Nt, m, mgrit.direct_factory(d.M, d.K), u0, fhat, C,
@@ -100,6 +102,40 @@ def test_level_sizes():
     assert mgrit.level_sizes(256, 4) == [256, 64, 16, 4]
     assert mgrit.level_sizes(1024, 8) == [1024, 128, 16, 2]
     assert mgrit.level_sizes(100, 4, max_levels=2) == [100, 25]
+
+
+def test_level_sizes_ragged():
+    """Step counts not divisible by m coarsen to floor(N_l / m) (a partial last
+    interval of F-points on the finer level)."""
+    assert mgrit.level_sizes(250, 4, min_coarse=2) == [250, 62, 15, 3]
+    assert mgrit.level_sizes(7, 4) == [7, 1]
+    assert mgrit.level_sizes(3, 4, min_coarse=0) == [3]
+
+
+@pytest.mark.parametrize("Nt,m,cycle", [(50, 4, "V"), (250, 2, "V"), (61, 3, "F"), (45, 4, "W")])
+def test_ragged_fixed_point_is_sequential(Nt, m, cycle):
+    """With partial last intervals on several levels the fixed point is still
+    sequential stepping, the tail F-points included."""
+    d, u0, fhat = _problem()
+    seq = timestep.sequential(d.M, d.K, 1.0, 1.0, Nt, u0, fhat, C)
+    mg = mgrit.MGRIT(d.M, d.K, 1.0, 1.0, Nt, m, mgrit.direct_factory(d.M, d.K), u0, fhat, C,
+                     min_coarse=2, cycle=cycle)
+    assert any(s % m for s in mg.sizes[:-1])
+    U, it, hist = mg.run(tol=1e-13, max_iter=80)
+    assert hist[-1] <= 1e-13 * hist[0]
+    assert np.linalg.norm(U - seq) <= 1e-12 * np.linalg.norm(seq)
+
+
+def test_one_interval_and_tail_exact():
+    """N_t = m + 3: one full interval and a tail of three F-points over a
+    one-step coarse level; the first correction makes everything exact."""
+    d, u0, fhat = _problem()
+    seq = timestep.sequential(d.M, d.K, 1.0, 0.5, 7, u0, fhat, C)
+    mg = mgrit.MGRIT(d.M, d.K, 1.0, 0.5, 7, 4, mgrit.direct_factory(d.M, d.K), u0, fhat, C)
+    assert mg.sizes == [7, 1]
+    U, it, hist = mg.run(tol=1e-10)
+    assert it <= 1
+    np.testing.assert_allclose(U, seq, atol=1e-14 * np.abs(seq).max())
 
 
 def test_paper_problem_iteration_count_loose():
