@@ -40,7 +40,7 @@ constexpr int kG1 = 224;               // stage-1 threads (warps 0-6)
 constexpr int kG2 = 288;               // stage-2 threads (warps 7-15): 18 half-warps
 constexpr int kThreads = kG1 + kG2;
 constexpr int kHalves = kG2 / 16;
-constexpr int kMaxSlots = 4;
+constexpr int kMaxSlots = 3;
 constexpr int kBarCopy = 1;            // stage-1 group: ring slot ready / released
 constexpr int kBarFull = 2;            // + buffer index: (tm, tk) written
 constexpr int kBarEmpty = 4;           // + buffer index: (tm, tk) consumed
@@ -64,9 +64,15 @@ __device__ __forceinline__ void cp_async_wait() {
 }
 // all but the nb - 2 most recent copy groups have landed
 __device__ __forceinline__ void cp_async_wait_ring(int nb) {
-  if (nb >= 4) cp_async_wait<2>();
-  else if (nb == 3) cp_async_wait<1>();
-  else cp_async_wait<0>();
+  switch (nb) {
+    case 8: cp_async_wait<6>(); break;
+    case 7: cp_async_wait<5>(); break;
+    case 6: cp_async_wait<4>(); break;
+    case 5: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<1>(); break;
+    default: cp_async_wait<0>(); break;
+  }
 }
 // sum of W band taps: the first a packed multiply, the rest packed FMAs
 template <int W, class F>
