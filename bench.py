@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--learned", action="store_true",
                     help="learned_c4: two-level MGRIT with the learned coarse propagator against "
                          "backward Euler on the coarse level, one JSON line (not the headline)")
+    ap.add_argument("--annulus", action="store_true",
+                    help="annulus_c3 (curved map, N = 16900, N_t = 1024, m = 8): chosen form, "
+                         "throughput and the sweep kernel's roofline")
     ap.add_argument("--spmm", action="store_true",
                     help="batched FP32 operator apply (iga_apply_f32) on 8192 columns: achieved "
                          "HBM GB/s against the measured peak, one JSON line per order")
@@ -361,6 +364,77 @@ def run_learned(args):
     print(json.dumps(line))
 
 
+def run_annulus(args):
+    """annulus_c3: quarter annulus (cubic Bezier arc x radial line), p = 4, 128 x 128
+    elements (N = 16900), kappa = 1, T = 1, N_t = 1024, m = 8 (1024 -> 128 -> 16 -> 2),
+    f = 0, 8-mode Fourier initial condition (seed 20210712).  Chosen form (FP32
+    p-multigrid cycles with FP64 refinement, one cycle per coarse-level solve,
+    autotuned sweep layouts) to MGRIT relative residual 1e-10: DOF*timesteps/s over
+    --steps solves after --warmup, and the V-cycle-model GB/s of k_mgrit_sweep from a
+    per-launch profiled solve, against the measured HBM bandwidth.  The fine-level
+    iterate is 139 MB (above L2).  --profile-only prints each launch's grid and
+    V-cycles (to pair with ncu's per-launch DRAM counters)."""
+    import numpy as np
+    import torch
+    from paper_2107_05337_gb300 import binding as B
+    from paper_2107_05337_gb300 import inputs
+    torch.cuda.set_device(0)
+    w = inputs.WORKLOADS["annulus_c3"]
+    p, nel, T, Nt, m = w["p"][0], w["nel"], w["T"], w["Nt"], w["m"]
+    k, l, a = inputs.fourier_modes()
+    u0fn = lambda xi, eta, x, y: sum(a[s] * np.sin(k[s] * np.pi * xi) * np.sin(l[s] * np.pi * eta)
+                                     for s in range(len(a)))
+    prob = B.Problem(p, nel, w["geom"])
+    u0 = prob.project(u0fn)
+    U = torch.empty((Nt + 1, prob.N), dtype=torch.float64, device="cuda")
+    opts = dict(T=T, Nt=Nt, m=m, max_levels=w["max_levels"], min_coarse=w["min_coarse"], relax=1,
+                tol=1e-10, max_iter=100, coarse_cycles=1)
+    pmg = dict(precision=1, tol=1e-10, autotune=1)
+    h = B.MGRIT(prob, **opts, pmg=pmg)
+    if args.profile_only:
+        h.run(u0, None, None, U)
+        torch.cuda.synchronize()
+        hp = B.MGRIT(prob, **opts, pmg=pmg, profile=1, graphs=0)
+        hp.run(u0, None, None, U)
+        pr = hp.profile()
+        print(json.dumps({"order": p, "N": int(prob.N), "grid": [int(g) for g in pr["grid"]],
+                          "cycles": [int(c) for c in pr["cycles"]]}))
+        return
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        h.run(u0, None, None, U)
+    torch.cuda.synchronize()
+    ms, st = [], None
+    with Clocks(0) as ck:
+        for _ in range(args.steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st, _ = h.run(u0, None, None, U)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+    hp = B.MGRIT(prob, **opts, pmg=pmg, profile=1, graphs=0)
+    hp.run(u0, None, None, U)
+    pr = hp.profile()
+    tot_ms = sum(pr["ms"])
+    byts = sum(c * prob.N * bytes_per_vcycle_dof(p, g) for g, c in zip(pr["grid"], pr["cycles"]))
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    achieved = byts / (tot_ms * 1e-3) / 1e9
+    print(json.dumps({"workload": "annulus_c3", "metric": "DOF*timesteps/s to MGRIT rel. residual 1e-10",
+                      "value": prob.N * Nt * len(ms) / (sum(ms) * 1e-3), "unit": UNIT,
+                      "ms_per_solve": round(sum(ms) / len(ms), 2), "steps": len(ms),
+                      "warmup": args.warmup, "iters": st["iters"], "levels": st["levels"],
+                      "vcyc_mean": round(st["vcyc_mean"], 3),
+                      "roofline": {"kernel": "k_mgrit_sweep", "bound": "hbm", "achieved": round(achieved, 2),
+                                   "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
+                                   "launches_profiled": len(pr["ms"]),
+                                   "mean_launch_ms": round(tot_ms / len(pr["ms"]), 3),
+                                   "peak_source": "measured" if peaks else "fallback"},
+                      "clocks": ck.summary()}))
+
+
 def run_spmm(args):
     """(M + c K) applied to 8192 FP32 columns of the 64 x 64-element unit square
     (one column per time point of a long interval), p = 2..5: bytes moved
@@ -404,6 +478,8 @@ def main():
         return run_reference(args)
     if args.spmm:
         return run_spmm(args)
+    if args.annulus:
+        return run_annulus(args)
     if args.learned:
         return run_learned(args)
     if args.batch:
