@@ -20,7 +20,7 @@ The tensor-product basis is Phi_(a,b)(xi,eta) = phi_a(xi) phi_b(eta), numbered
 a + nb*b (xi fastest).  Integrals are taken over the parameter domain with the
 Jacobian of F: d Omega = |det J| d xi d eta, grad = J^{-T} grad_xi.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
   * nq = p+1 Gauss points per direction per element for every matrix and
     vector of a problem of order p, including its p=1 matrices and P.
   * Dirichlet condition: the first and last univariate function in each
@@ -156,7 +156,8 @@ class Discretisation:
         return b[self.interior]
 
     def project(self, fn):
-        """Consistent L2 projection onto the interior spline space: M u = b."""
+        """Consistent L2 projection onto the interior spline space: M u = b (Sec. 3: the
+        initial condition is projected onto the spline space)."""
         from scipy.sparse.linalg import spsolve
         return spsolve(self.M.tocsc(), self.load_vector(fn))
 

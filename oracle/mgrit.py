@@ -40,7 +40,7 @@ The method (Sec. 3, the MGRIT algorithm box; ideal interpolation P):
              correct u_{jm} += u^(l+1)_j and F-relax (= ideal interpolation
              P = [-A_FF^{-1} A_FC; I_C]).
 
-Readings of points the paper leaves open or prints garbled (also in the design doc):
+Readings of points the paper leaves open or prints garbled:
   * Correction scheme: the coarse right-hand side is the injected residual,
     i.e. the algorithm box's residual is g^(l) - A^(l) u^(l) (printed with
     g^(L)).  Coarse levels start from u^(l+1) = 0 on every visit.

@@ -23,7 +23,7 @@ The method (Sec. 4):
   4. x <- x + I_1^p e_1,  I_1^p v = (M_p^L)^{-1} P v;
   5. nu2 post-smoothing steps.
 
-Readings of points the paper leaves open (also in the design doc):
+Readings of points the paper leaves open:
   * ILUT is Saad's dual-threshold ILUT in natural (lexicographic) order:
     entries below droptol * ||a_i||_2 are dropped, then the ceil(fill*nnz_L(a_i))
     largest strictly-lower and ceil(fill*nnz_U(a_i)) largest strictly-upper

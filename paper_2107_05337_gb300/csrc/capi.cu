@@ -1035,7 +1035,7 @@ extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs,
 // MGRIT (Sec. 3)
 // ---------------------------------------------------------------------------
 // ---------------------------------------------------------------------------
-// learned coarse propagator (the benchmark spec (4))
+// learned coarse propagator
 // ---------------------------------------------------------------------------
 struct phic_handle {
   PhicNet net;
