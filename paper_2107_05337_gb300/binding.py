@@ -139,6 +139,14 @@ def _dptr(t):
     return c_void_p(t.data_ptr())
 
 
+def _dptr_of(t, dtype, what):
+    """Device pointer of a CUDA tensor of the given dtype; TypeError otherwise
+    (the library reads the memory as that type)."""
+    if not t.is_cuda or t.dtype != dtype:
+        raise TypeError(f"{what}: expected a CUDA {dtype} tensor, got {t.dtype} on {t.device}")
+    return c_void_p(t.data_ptr())
+
+
 def quarter_annulus_net():
     """B-spline control net (degrees (3,1), 4 x 2 points) of the map
     F(xi, eta) = (1 + eta) C(xi), C the cubic Bezier quarter arc with control
@@ -212,19 +220,23 @@ class Problem:
         """Y = M X, K X or (M + c K) X (which = 'M', 'K', 'A') on FP32 columns X [nrhs, N]
         (unit square only)."""
         torch = _torch()
+        if X.dim() != 2:
+            raise ValueError("apply_f32: X must be [nrhs, ld] with ld >= N")
         X = X.contiguous()
+        px = _dptr_of(X, torch.float32, "apply_f32")
         Y = torch.empty_like(X)
         _check(lib().iga_apply_f32(self.h, {"M": 0, "K": 1, "A": 2}[which], c, X.shape[0],
-                                   _dptr(X), _dptr(Y), X.shape[1], _stream()))
+                                   px, _dptr(Y), X.shape[1], _stream()))
         return Y
 
     def apply(self, which, X):
         """Y = M X (which='M') or K X (which='K') on columns X [nrhs, N] (CUDA float64)."""
         torch = _torch()
         X = X.contiguous()
+        px = _dptr_of(X, torch.float64, "apply")
         Y = torch.empty_like(X)
         nrhs = X.shape[0] if X.dim() == 2 else 1
-        _check(lib().iga_apply(self.h, 0 if which == "M" else 1, nrhs, _dptr(X), _dptr(Y),
+        _check(lib().iga_apply(self.h, 0 if which == "M" else 1, nrhs, px, _dptr(Y),
                                self.N, _stream()))
         return Y
 
