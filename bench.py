@@ -10,8 +10,17 @@ relative residual 1e-10.  One "step" of the benchmark = one MGRIT solve for
 each of the four orders (a unit of work = N_p * N_t DOF*timesteps, summed).
 
 Forms: "chosen" = FP32 smoothing / SpMM / transfers / Gauss--Seidel with FP64
-residual refinement (precision 1); "plain" = everything FP64 (precision 0).
-The value is the chosen form's throughput; the plain form is reported beside it.
+residual refinement (precision 1), one p-multigrid cycle per coarse-level solve,
+sweep layouts autotuned at setup; "plain" = everything FP64 (precision 0) to
+1e-10 on every level.  The value is the chosen form's throughput; the plain form
+is reported beside it.
+
+Other modes (one JSON line each): --annulus (the curved-map workload annulus_c3),
+--batch (the uneven 64-problem batch, latency percentiles), --learned (two-level
+MGRIT with the trained coarse propagator against backward Euler and the plain
+form), --spmm (the batched FP32 operator apply against the HBM copy bandwidth),
+--profile-only (per-launch grids and V-cycles, to pair with ncu), and
+--impl reference (the oracle timed on the host cores).
 """
 import argparse
 import json
