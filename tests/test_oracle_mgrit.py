@@ -138,16 +138,37 @@ def test_one_interval_and_tail_exact():
     np.testing.assert_allclose(U, seq, atol=1e-14 * np.abs(seq).max())
 
 
+def _paper_iterations():
+    """(domain, k, N_t) -> iterations from tests/golden/tables7_8_mgrit_iterations.txt."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "tables7_8_mgrit_iterations.txt")
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            _, dom, k, nt, it = [f.strip() for f in line.split("|")]
+            out[(dom, int(k), int(nt))] = int(it)
+    return out
+
+
 def test_paper_problem_iteration_count_loose():
-    """Loose pin on Table 8 (unit square, N_t = 100, V-cycles: 9 iterations at
-    h = 2^-6): the paper's problem f = 1, u0 = 0, T = 0.1, kappa = 1, tolerance
-    1e-10.  XBraid's defaults are not reproducible here, so a band is checked."""
+    """Loose pin on the iteration counts of Tables 7-8 for the paper's problem
+    f = 1, u0 = 0, T = 0.1, kappa = 1, tolerance 1e-10, m = 2, min_coarse = 2
+    (XBraid's defaults; its other settings are not reproducible here).  The
+    paper's counts do not depend on p or h (Table 8), so a coarse mesh (h = 2^-4)
+    stands in for h = 2^-6: each count lies within [printed - 2, printed + 1]
+    and, like the printed ones, does not decrease as N_t grows."""
+    paper = _paper_iterations()
     d = assembly.Discretisation(2, 16, geometry.UnitSquare())
     fhat = d.load_vector(lambda xi, eta, x, y: np.ones_like(x))
-    mg = mgrit.MGRIT(d.M, d.K, 1.0, 0.1, 100, 2, mgrit.direct_factory(d.M, d.K),
-                     np.zeros(d.N), fhat, lambda t: 1.0, min_coarse=2)
-    U, it, hist = mg.run(tol=1e-10)
-    assert 6 <= it <= 12, it
+    its = []
+    for Nt in (100, 250, 500, 1000):
+        mg = mgrit.MGRIT(d.M, d.K, 1.0, 0.1, Nt, 2, mgrit.direct_factory(d.M, d.K),
+                         np.zeros(d.N), fhat, lambda t: 1.0, min_coarse=2)
+        U, it, hist = mg.run(tol=1e-10)
+        want = paper[("unit_square", 6, Nt)]
+        assert want - 2 <= it <= want + 1, (Nt, it, want)
+        its.append(it)
+    assert its == sorted(its)
 
 
 def test_mgrit_with_pmg_solves_matches_sequential():
