@@ -232,7 +232,10 @@ typedef struct {
   double tol;      /* stop when rho_k <= tol * rho_0 (C-point residual 2-norm) */
   int max_iter;    /* iteration limit */
   pmg_opts pmg;    /* spatial solver options used on every level */
-  int initial_guess; /* 0: u_n = 0 for n >= 1; 1: start from the U passed in */
+  int initial_guess; /* 0: u_n = 0 for n >= 1; 1: start from the U passed in (a warm
+                        restart from an earlier run's iterate; the stopping test is relative
+                        to this run's first residual, so a restart aiming at the original
+                        target passes tol scaled by the earlier run's residual reduction) */
   int graphs;      /* 1: replay each iteration's launches as CUDA graphs (default 1) */
   int profile;     /* 1: record CUDA events around every sweep launch (mgrit_profile) */
   double theta;    /* theta-scheme of Sec. 2, Eq. (los): 1 backward Euler (default),
