@@ -86,6 +86,19 @@ igm_status iga_quadrature_points(const iga_ops* ops, double* pts);
  * quadrature points; writes DEVICE out[N]. */
 igm_status iga_load_vector(const iga_ops* ops, const double* fq, double* out, igm_stream s);
 
+/* The univariate B-spline basis of order p on the open uniform knot vector of
+ * nel elements on [0, 1] (Sec. 2: the Cox--de Boor recursion, knots repeated
+ * p+1 times at the ends), evaluated on the HOST; needs no device.  For each of
+ * the nx HOST points x[i] in [0, 1]: span[i] = the index s of the knot span
+ * holding x[i] (knots[s] <= x[i] < knots[s+1]; the last non-empty span at
+ * x = 1), so that the nonzero functions are s-p .. s; N[i*(p+1) + k] and
+ * dN[i*(p+1) + k] = the value and first derivative of function s-p+k (HOST
+ * outputs [nx][p+1]; dN may be NULL).  The same code serves the assembly of
+ * iga_assemble.  IGM_ERR_ARG for p outside [1, 8], nel < 1, a null array or a
+ * point outside [0, 1]. */
+igm_status iga_basis_eval(int p, int nel, int nx, const double* x, int* span, double* N,
+                          double* dN);
+
 /* Consistent L2 projection onto the spline space (Sec. 3: g^0 is u^0
  * projected onto V_{h,p}): solves M u = b(fq); writes DEVICE out[N]. */
 igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_stream s);

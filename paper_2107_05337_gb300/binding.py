@@ -58,6 +58,8 @@ EXPORTS = {
     "iga_project": (c_int, [c_void_p, POINTER(c_double), c_void_p, c_void_p]),
     "iga_apply_f32": (c_int, [c_void_p, c_int, c_double, c_int, c_void_p, c_void_p, c_long,
                               c_void_p]),
+    "iga_basis_eval": (c_int, [c_int, c_int, c_int, POINTER(c_double), POINTER(c_int),
+                               POINTER(c_double), POINTER(c_double)]),
     "iga_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p]),
     "pmg_default_opts": (None, [POINTER(PmgOpts)]),
     "pmg_setup": (c_int, [c_void_p, c_double, POINTER(PmgOpts), POINTER(c_void_p)]),
@@ -145,6 +147,21 @@ def _dptr_of(t, dtype, what):
     if not t.is_cuda or t.dtype != dtype:
         raise TypeError(f"{what}: expected a CUDA {dtype} tensor, got {t.dtype} on {t.device}")
     return c_void_p(t.data_ptr())
+
+
+def basis_eval(p, nel, x):
+    """iga_basis_eval on host points x in [0, 1]: (span [nx] int32, N [nx, p+1],
+    dN [nx, p+1]) of the order-p basis on the open uniform knots of nel
+    elements; the nonzero functions at x[i] are span[i]-p .. span[i]."""
+    x = np.ascontiguousarray(x, dtype=np.float64).ravel()
+    span = np.zeros(x.size, dtype=np.int32)
+    N = np.zeros((x.size, p + 1))
+    dN = np.zeros((x.size, p + 1))
+    _check(lib().iga_basis_eval(p, nel, x.size, x.ctypes.data_as(POINTER(c_double)),
+                                span.ctypes.data_as(POINTER(c_int)),
+                                N.ctypes.data_as(POINTER(c_double)),
+                                dN.ctypes.data_as(POINTER(c_double))))
+    return span, N, dN
 
 
 def quarter_annulus_net():

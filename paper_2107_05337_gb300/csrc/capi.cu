@@ -147,6 +147,21 @@ static int dev_smem_optin() {
 // ---------------------------------------------------------------------------
 // iga_assemble and friends
 // ---------------------------------------------------------------------------
+extern "C" igm_status iga_basis_eval(int p, int nel, int nx, const double* x, int* span,
+                                     double* N, double* dN) {
+  if (p < 1 || p > 8 || nel < 1 || nx < 0 || (nx > 0 && (!x || !span || !N)))
+    return fail(IGM_ERR_ARG, "iga_basis_eval: p in [1, 8], nel >= 1, non-null x, span, N");
+  for (int i = 0; i < nx; ++i)
+    if (!(x[i] >= 0.0 && x[i] <= 1.0)) return fail(IGM_ERR_ARG, "iga_basis_eval: x outside [0, 1]");
+  const std::vector<double> t = open_uniform_knots(p, nel);
+  for (int i = 0; i < nx; ++i) {
+    span[i] = find_span(t, p, x[i]);
+    basis_on_span(t, p, span[i], x[i], N + (size_t)i * (p + 1),
+                  dN ? dN + (size_t)i * (p + 1) : nullptr);
+  }
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
   if (!desc || !out) return fail(IGM_ERR_ARG, "null argument");
   if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");

@@ -107,7 +107,7 @@ void basis_on_span(const std::vector<double>& t, int p, int s, double x, double*
   }
 }
 
-static int find_span(const std::vector<double>& t, int p, double x) {
+int find_span(const std::vector<double>& t, int p, double x) {
   int nb = (int)t.size() - p - 1;
   if (x >= t[nb]) return nb - 1;  // right end: last non-empty span
   int lo = p, hi = nb;

@@ -56,6 +56,9 @@ void gauss_legendre(int nq, std::vector<double>& x, std::vector<double>& w);  //
 // Values and first derivatives of the p+1 functions nonzero on knot span s
 // (knots[s] <= x < knots[s+1]): functions s-p .. s.
 void basis_on_span(const std::vector<double>& knots, int p, int s, double x, double* N, double* dN);
+// Index s of the knot span holding x (knots[s] <= x < knots[s+1]; the last
+// non-empty span at the right end).
+int find_span(const std::vector<double>& knots, int p, double x);
 
 // Assemble order p on nel elements with nq Gauss points per direction.
 std::string assemble(const Geometry& g, int p, int nel, int nq, Discretisation& d);
