@@ -230,6 +230,18 @@ igm_status pmg_trace(pmg_handle* h, long long* out, int reset);
 igm_status pmg_ilut_factors(const pmg_handle* h, int* nnz_l, int* nnz_u, int* l_ptr, int* l_col,
                             double* l_val, int* u_ptr, int* u_col, double* u_val);
 
+/* The ILUT factorisation of pmg_setup (Sec. 4's smoother; dual threshold in
+ * natural order, the drop tolerance relative to each row's 2-norm, at most
+ * ceil(fill * nnz) entries per strictly-lower and strictly-upper row part),
+ * applied to a caller's HOST CSR matrix of n rows (ptr[n+1], col, val; any
+ * column order within a row).  Outputs as pmg_ilut_factors: L strictly lower,
+ * U upper with the diagonal; call once with NULL arrays for *nnz_l, *nnz_u,
+ * then with arrays of those sizes (l_ptr, u_ptr [n+1]).  Needs no device.
+ * IGM_ERR_ARG for malformed CSR or parameters, IGM_ERR_NUMERIC for a zero pivot. */
+igm_status pmg_ilut_host(int n, const int* ptr, const int* col, const double* val, double droptol,
+                         double fill, int* nnz_l, int* nnz_u, int* l_ptr, int* l_col,
+                         double* l_val, int* u_ptr, int* u_col, double* u_val);
+
 /* ---------------------------------------------------------------------------
  * MGRIT (Sec. 3).
  * ------------------------------------------------------------------------ */

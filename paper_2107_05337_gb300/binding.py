@@ -60,6 +60,10 @@ EXPORTS = {
                               c_void_p]),
     "iga_basis_eval": (c_int, [c_int, c_int, c_int, POINTER(c_double), POINTER(c_int),
                                POINTER(c_double), POINTER(c_double)]),
+    "pmg_ilut_host": (c_int, [c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double), c_double,
+                              c_double, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                              POINTER(c_int), POINTER(c_double), POINTER(c_int), POINTER(c_int),
+                              POINTER(c_double)]),
     "iga_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_long, c_void_p]),
     "pmg_default_opts": (None, [POINTER(PmgOpts)]),
     "pmg_setup": (c_int, [c_void_p, c_double, POINTER(PmgOpts), POINTER(c_void_p)]),
@@ -162,6 +166,29 @@ def basis_eval(p, nel, x):
                                 N.ctypes.data_as(POINTER(c_double)),
                                 dN.ctypes.data_as(POINTER(c_double))))
     return span, N, dN
+
+
+def ilut_host(A, droptol=1e-12, fill=1.0):
+    """pmg_ilut_host on a scipy CSR matrix A: (L, U) as scipy CSR (L strictly
+    lower, U upper with the diagonal), computed by the library's host code."""
+    import scipy.sparse as sp
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    ptr = np.ascontiguousarray(A.indptr, dtype=np.int32)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    ip = lambda a: a.ctypes.data_as(POINTER(c_int))
+    dp = lambda a: a.ctypes.data_as(POINTER(c_double))
+    nl, nu = c_int(), c_int()
+    _check(lib().pmg_ilut_host(n, ip(ptr), ip(col), dp(val), droptol, fill, ctypes.byref(nl),
+                               ctypes.byref(nu), None, None, None, None, None, None))
+    lp, lc, lv = np.zeros(n + 1, np.int32), np.zeros(max(nl.value, 1), np.int32), np.zeros(max(nl.value, 1))
+    up, uc, uv = np.zeros(n + 1, np.int32), np.zeros(max(nu.value, 1), np.int32), np.zeros(max(nu.value, 1))
+    _check(lib().pmg_ilut_host(n, ip(ptr), ip(col), dp(val), droptol, fill, None, None,
+                               ip(lp), ip(lc), dp(lv), ip(up), ip(uc), dp(uv)))
+    L = sp.csr_matrix((lv[:nl.value], lc[:nl.value], lp), shape=(n, n))
+    U = sp.csr_matrix((uv[:nu.value], uc[:nu.value], up), shape=(n, n))
+    return L, U
 
 
 def quarter_annulus_net():

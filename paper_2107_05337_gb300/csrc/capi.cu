@@ -1000,6 +1000,35 @@ extern "C" igm_status pmg_ilut_factors(const pmg_handle* h, int* nnz_l, int* nnz
   return IGM_OK;
 }
 
+extern "C" igm_status pmg_ilut_host(int n, const int* ptr, const int* col, const double* val,
+                                    double droptol, double fill, int* nnz_l, int* nnz_u,
+                                    int* l_ptr, int* l_col, double* l_val, int* u_ptr, int* u_col,
+                                    double* u_val) {
+  if (n < 1 || !ptr || !col || !val || !(droptol >= 0.0) || !(fill > 0.0))
+    return fail(IGM_ERR_ARG, "pmg_ilut_host: n >= 1, non-null CSR arrays, droptol >= 0, fill > 0");
+  if (ptr[0] != 0) return fail(IGM_ERR_ARG, "pmg_ilut_host: ptr[0] must be 0");
+  for (int i = 0; i < n; ++i)
+    if (ptr[i + 1] < ptr[i]) return fail(IGM_ERR_ARG, "pmg_ilut_host: ptr must not decrease");
+  for (int k = 0; k < ptr[n]; ++k)
+    if (col[k] < 0 || col[k] >= n) return fail(IGM_ERR_ARG, "pmg_ilut_host: column out of range");
+  Csr A, L, U;
+  A.rows = A.cols = n;
+  A.ptr.assign(ptr, ptr + n + 1);
+  A.col.assign(col, col + ptr[n]);
+  A.val.assign(val, val + ptr[n]);
+  const std::string e = ilut(A, droptol, fill, L, U);
+  if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+  if (nnz_l) *nnz_l = L.nnz();
+  if (nnz_u) *nnz_u = U.nnz();
+  if (l_ptr) std::memcpy(l_ptr, L.ptr.data(), L.ptr.size() * sizeof(int));
+  if (l_col) std::memcpy(l_col, L.col.data(), L.col.size() * sizeof(int));
+  if (l_val) std::memcpy(l_val, L.val.data(), L.val.size() * sizeof(double));
+  if (u_ptr) std::memcpy(u_ptr, U.ptr.data(), U.ptr.size() * sizeof(int));
+  if (u_col) std::memcpy(u_col, U.col.data(), U.col.size() * sizeof(int));
+  if (u_val) std::memcpy(u_val, U.val.data(), U.val.size() * sizeof(double));
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, double* y,
                                 long ld, igm_stream s) {
   if (!ops || !x || !y) return fail(IGM_ERR_ARG, "null argument");
