@@ -99,6 +99,18 @@ igm_status iga_load_vector(const iga_ops* ops, const double* fq, double* out, ig
 igm_status iga_basis_eval(int p, int nel, int nx, const double* x, int* span, double* N,
                           double* dN);
 
+/* The matrices iga_assemble builds (Sec. 2: M_ij = int phi_i phi_j, K_ij =
+ * int grad phi_i . grad phi_j over the mapped domain, Gauss quadrature), on
+ * the HOST; needs no device.  which = 0: M, 1: K, as stencils of the interior
+ * unknowns (i = ix + n*iy): out[i*(2p+1)^2 + (dy+p)*(2p+1) + (dx+p)] = the
+ * entry coupling i to (ix+dx) + n*(iy+dy), 0 where that point lies outside
+ * the grid (HOST out [n*n*(2p+1)^2]); which = 2: the lumped masses (full-basis
+ * row sums of M on the interior rows, HOST out [n*n]).  *n = interior
+ * unknowns per direction; out may be NULL to query n.  The descriptor is
+ * iga_assemble's, with p in [1, 8] and nel in [1, 1024]; IGM_ERR_ARG for
+ * invalid input. */
+igm_status iga_assemble_host(const iga_desc* desc, int which, int* n, double* out);
+
 /* Consistent L2 projection onto the spline space (Sec. 3: g^0 is u^0
  * projected onto V_{h,p}): solves M u = b(fq); writes DEVICE out[N]. */
 igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_stream s);

@@ -60,6 +60,7 @@ EXPORTS = {
                               c_void_p]),
     "iga_basis_eval": (c_int, [c_int, c_int, c_int, POINTER(c_double), POINTER(c_int),
                                POINTER(c_double), POINTER(c_double)]),
+    "iga_assemble_host": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
     "pmg_ilut_host": (c_int, [c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double), c_double,
                               c_double, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int), POINTER(c_double), POINTER(c_int), POINTER(c_int),
@@ -201,25 +202,60 @@ def quarter_annulus_net():
     return (3, 1), (4, 2), np.ascontiguousarray(ctrl)
 
 
+def _desc(p, nel, geom="unit_square", kappa=1.0, nquad=0):
+    """iga_desc for the unit square or the quarter annulus; returns (desc, the
+    control-net array the descriptor points into, or None)."""
+    d = IgaDesc()
+    d.p, d.nel, d.nquad, d.kappa = p, nel, nquad, kappa
+    ctrl = None
+    if geom == "unit_square":
+        d.geom = 0
+    elif geom == "quarter_annulus":
+        deg, gn, net = quarter_annulus_net()
+        d.geom = 1
+        d.gdeg[0], d.gdeg[1] = deg
+        d.gn[0], d.gn[1] = gn
+        ctrl = np.ascontiguousarray(net.ravel())
+        d.gctrl = ctrl.ctypes.data_as(POINTER(c_double))
+    else:
+        raise ValueError(geom)
+    return d, ctrl
+
+
+def assemble_host(p, nel, geom="unit_square", which="M", nquad=0):
+    """iga_assemble_host: M or K as a scipy CSR matrix of the interior unknowns,
+    or the lumped masses (which = 'lumped'), from the library's host assembly."""
+    import scipy.sparse as sp
+    d, ctrl = _desc(p, nel, geom, 1.0, nquad)
+    w = {"M": 0, "K": 1, "lumped": 2}[which]
+    n = c_int()
+    _check(lib().iga_assemble_host(ctypes.byref(d), w, ctypes.byref(n), None))
+    n = n.value
+    N, q = n * n, 2 * p + 1
+    out = np.zeros(N if w == 2 else N * q * q)
+    _check(lib().iga_assemble_host(ctypes.byref(d), w, None, out.ctypes.data_as(POINTER(c_double))))
+    if w == 2:
+        return out
+    i = np.arange(N)
+    ix, iy = i % n, i // n
+    rows, cols, vals = [], [], []
+    for dy in range(-p, p + 1):
+        for dx in range(-p, p + 1):
+            jx, jy = ix + dx, iy + dy
+            ok = (jx >= 0) & (jx < n) & (jy >= 0) & (jy < n)
+            rows.append(i[ok])
+            cols.append((jx + n * jy)[ok])
+            vals.append(out[i[ok] * q * q + (dy + p) * q + (dx + p)])
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N, N))
+
+
 class Problem:
     """IgA discretisation (iga_assemble): order p, nel x nel elements."""
 
     def __init__(self, p, nel, geom="unit_square", kappa=1.0, nquad=0):
         L = lib()
-        d = IgaDesc()
-        d.p, d.nel, d.nquad, d.kappa = p, nel, nquad, kappa
-        self._ctrl = None
-        if geom == "unit_square":
-            d.geom = 0
-        elif geom == "quarter_annulus":
-            deg, gn, ctrl = quarter_annulus_net()
-            d.geom = 1
-            d.gdeg[0], d.gdeg[1] = deg
-            d.gn[0], d.gn[1] = gn
-            self._ctrl = np.ascontiguousarray(ctrl.ravel())
-            d.gctrl = self._ctrl.ctypes.data_as(POINTER(c_double))
-        else:
-            raise ValueError(geom)
+        d, self._ctrl = _desc(p, nel, geom, kappa, nquad)
         h = c_void_p()
         _check(L.iga_assemble(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

@@ -162,6 +162,46 @@ extern "C" igm_status iga_basis_eval(int p, int nel, int nx, const double* x, in
   return IGM_OK;
 }
 
+// The map of an iga_desc: the unit square, or the B-spline map with open
+// uniform knots.  Returns "" or an error text.
+static std::string make_geometry(const iga_desc* desc, Geometry& g) {
+  if (desc->geom == 0) {
+    g.affine = true;
+    return "";
+  }
+  if (desc->geom != 1) return "geom must be 0 or 1";
+  g.affine = false;
+  for (int d = 0; d < 2; ++d) {
+    g.deg[d] = desc->gdeg[d];
+    g.nctrl[d] = desc->gn[d];
+    if (g.deg[d] < 1 || g.nctrl[d] <= g.deg[d]) return "invalid geometry net";
+    g.knots[d] = open_uniform_knots(g.deg[d], g.nctrl[d] - g.deg[d]);
+  }
+  if (!desc->gctrl) return "geometry control net missing";
+  g.ctrl.assign(desc->gctrl, desc->gctrl + 2 * g.nctrl[0] * g.nctrl[1]);
+  return "";
+}
+
+extern "C" igm_status iga_assemble_host(const iga_desc* desc, int which, int* n, double* out) {
+  if (!desc) return fail(IGM_ERR_ARG, "null argument");
+  if (desc->p < 1 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [1, 8]");
+  if (desc->nel < 1 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [1, 1024]");
+  if (which < 0 || which > 2) return fail(IGM_ERR_ARG, "which must be 0 (M), 1 (K) or 2 (lumped)");
+  Geometry g;
+  const std::string ge = make_geometry(desc, g);
+  if (!ge.empty()) return fail(IGM_ERR_ARG, ge);
+  Discretisation d;
+  const int nq = desc->nquad > 0 ? desc->nquad : desc->p + 1;
+  const std::string e = assemble(g, desc->p, desc->nel, nq, d);
+  if (!e.empty()) return fail(IGM_ERR_ARG, e);
+  if (n) *n = d.n;
+  if (out) {
+    const std::vector<double>& v = which == 0 ? d.M.val : (which == 1 ? d.K.val : d.lumped);
+    std::memcpy(out, v.data(), v.size() * sizeof(double));
+  }
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
   if (!desc || !out) return fail(IGM_ERR_ARG, "null argument");
   if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");
@@ -172,21 +212,8 @@ extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
   auto ops = std::make_unique<iga_ops>();
   ops->kappa = desc->kappa;
   Geometry& g = ops->geom;
-  if (desc->geom == 0) {
-    g.affine = true;
-  } else if (desc->geom == 1) {
-    g.affine = false;
-    for (int d = 0; d < 2; ++d) {
-      g.deg[d] = desc->gdeg[d];
-      g.nctrl[d] = desc->gn[d];
-      if (g.deg[d] < 1 || g.nctrl[d] <= g.deg[d]) return fail(IGM_ERR_ARG, "invalid geometry net");
-      g.knots[d] = open_uniform_knots(g.deg[d], g.nctrl[d] - g.deg[d]);
-    }
-    if (!desc->gctrl) return fail(IGM_ERR_ARG, "geometry control net missing");
-    g.ctrl.assign(desc->gctrl, desc->gctrl + 2 * g.nctrl[0] * g.nctrl[1]);
-  } else {
-    return fail(IGM_ERR_ARG, "geom must be 0 or 1");
-  }
+  const std::string ge = make_geometry(desc, g);
+  if (!ge.empty()) return fail(IGM_ERR_ARG, ge);
   const int nq = desc->nquad > 0 ? desc->nquad : desc->p + 1;
   std::string e = assemble(g, desc->p, desc->nel, nq, ops->hi);
   if (!e.empty()) return fail(IGM_ERR_ARG, e);

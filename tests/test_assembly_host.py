@@ -1,0 +1,38 @@
+"""The library's host assembly (iga_assemble_host: the matrices iga_assemble
+uploads; Sec. 2) against the oracle's independent assembly: M, K and the
+lumped masses on the unit square and on the curved quarter annulus, to FP64
+rounding (the two sum the quadrature in different orders).  Runs on the CPU:
+the call needs no device."""
+import numpy as np
+import pytest
+
+from oracle import assembly, geometry
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2107_05337_gb300 import binding, build
+    build.build()
+    return binding
+
+
+@pytest.mark.parametrize("geom,G", [("unit_square", geometry.UnitSquare),
+                                    ("quarter_annulus", geometry.QuarterAnnulus)])
+@pytest.mark.parametrize("p,nel", [(1, 5), (2, 4), (3, 7), (4, 6), (5, 5)])
+def test_host_assembly_matches_oracle(B, geom, G, p, nel):
+    d = assembly.Discretisation(p, nel, G())
+    for which, A in (("M", d.M), ("K", d.K)):
+        H = B.assemble_host(p, nel, geom, which)
+        assert H.shape == A.shape
+        assert abs(H - A).max() <= 1e-13 * abs(A).max(), which
+        # same sparsity: every stencil coupling inside the grid is structurally nonzero
+        assert (abs(H) > 0).nnz == (abs(A) > 0).nnz
+    lum = B.assemble_host(p, nel, geom, "lumped")
+    assert np.abs(lum - d.lumped).max() <= 1e-13 * np.abs(d.lumped).max()
+
+
+def test_invalid_arguments(B):
+    with pytest.raises(B.IgmError):
+        B.assemble_host(0, 4)
+    with pytest.raises(ValueError):
+        B.assemble_host(2, 4, "disk")
