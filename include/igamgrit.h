@@ -111,6 +111,15 @@ igm_status iga_basis_eval(int p, int nel, int nx, const double* x, int* span, do
  * invalid input. */
 igm_status iga_assemble_host(const iga_desc* desc, int which, int* n, double* out);
 
+/* The transfer matrix of the p-multigrid (Sec. 4, Eq. (PM): P_ij = int phi_i
+ * psi_j, phi of order p, psi of order 1 on the same knot spans and quadrature),
+ * interior x interior, as iga_assemble builds it, on the HOST; needs no
+ * device.  CSR over the N = n^2 order-p rows (ptr [N+1], col, val: columns are
+ * the interior order-1 unknowns); call once with NULL arrays for *nnz, then
+ * with arrays of that size.  The descriptor is iga_assemble's (p in [2, 8]);
+ * IGM_ERR_ARG for invalid input. */
+igm_status iga_transfer_host(const iga_desc* desc, int* nnz, int* ptr, int* col, double* val);
+
 /* Consistent L2 projection onto the spline space (Sec. 3: g^0 is u^0
  * projected onto V_{h,p}): solves M u = b(fq); writes DEVICE out[N]. */
 igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_stream s);

@@ -61,6 +61,8 @@ EXPORTS = {
     "iga_basis_eval": (c_int, [c_int, c_int, c_int, POINTER(c_double), POINTER(c_int),
                                POINTER(c_double), POINTER(c_double)]),
     "iga_assemble_host": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
+    "iga_transfer_host": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                  POINTER(c_double)]),
     "pmg_ilut_host": (c_int, [c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double), c_double,
                               c_double, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int), POINTER(c_double), POINTER(c_int), POINTER(c_int),
@@ -248,6 +250,22 @@ def assemble_host(p, nel, geom="unit_square", which="M", nquad=0):
             vals.append(out[i[ok] * q * q + (dy + p) * q + (dx + p)])
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(N, N))
+
+
+def transfer_host(p, nel, geom="unit_square", nquad=0):
+    """iga_transfer_host: the order-p x order-1 transfer matrix as scipy CSR."""
+    import scipy.sparse as sp
+    d, ctrl = _desc(p, nel, geom, 1.0, nquad)
+    nnz = c_int()
+    _check(lib().iga_transfer_host(ctypes.byref(d), ctypes.byref(nnz), None, None, None))
+    n, n1 = nel + p - 2, nel - 1
+    ptr = np.zeros(n * n + 1, dtype=np.int32)
+    col = np.zeros(max(nnz.value, 1), dtype=np.int32)
+    val = np.zeros(max(nnz.value, 1))
+    _check(lib().iga_transfer_host(ctypes.byref(d), None, ptr.ctypes.data_as(POINTER(c_int)),
+                                   col.ctypes.data_as(POINTER(c_int)),
+                                   val.ctypes.data_as(POINTER(c_double))))
+    return sp.csr_matrix((val[:nnz.value], col[:nnz.value], ptr), shape=(n * n, n1 * n1))
 
 
 class Problem:

@@ -202,6 +202,27 @@ extern "C" igm_status iga_assemble_host(const iga_desc* desc, int which, int* n,
   return IGM_OK;
 }
 
+extern "C" igm_status iga_transfer_host(const iga_desc* desc, int* nnz, int* ptr, int* col,
+                                        double* val) {
+  if (!desc) return fail(IGM_ERR_ARG, "null argument");
+  if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");
+  if (desc->nel < 1 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [1, 1024]");
+  Geometry g;
+  const std::string ge = make_geometry(desc, g);
+  if (!ge.empty()) return fail(IGM_ERR_ARG, ge);
+  Discretisation hi, lo;
+  const int nq = desc->nquad > 0 ? desc->nquad : desc->p + 1;
+  std::string e = assemble(g, desc->p, desc->nel, nq, hi);
+  if (e.empty()) e = assemble(g, 1, desc->nel, nq, lo);
+  if (!e.empty()) return fail(IGM_ERR_ARG, e);
+  const Csr P = transfer(g, hi, lo);
+  if (nnz) *nnz = P.nnz();
+  if (ptr) std::memcpy(ptr, P.ptr.data(), P.ptr.size() * sizeof(int));
+  if (col) std::memcpy(col, P.col.data(), P.col.size() * sizeof(int));
+  if (val) std::memcpy(val, P.val.data(), P.val.size() * sizeof(double));
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
   if (!desc || !out) return fail(IGM_ERR_ARG, "null argument");
   if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");

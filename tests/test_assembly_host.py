@@ -36,3 +36,16 @@ def test_invalid_arguments(B):
         B.assemble_host(0, 4)
     with pytest.raises(ValueError):
         B.assemble_host(2, 4, "disk")
+
+
+@pytest.mark.parametrize("geom,G", [("unit_square", geometry.UnitSquare),
+                                    ("quarter_annulus", geometry.QuarterAnnulus)])
+@pytest.mark.parametrize("p,nel", [(2, 4), (3, 7), (5, 6)])
+def test_host_transfer_matches_oracle(B, geom, G, p, nel):
+    """The order-p x order-1 transfer matrix P of Eq. (PM), interior x interior."""
+    hi, lo = assembly.problem(p, nel, G())
+    O = hi.transfer_to(lo)
+    H = B.transfer_host(p, nel, geom)
+    assert H.shape == O.shape
+    assert (abs(H) > 0).nnz == (abs(O) > 0).nnz
+    assert abs(H - O).max() <= 1e-13 * abs(O).max()
