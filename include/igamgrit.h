@@ -263,6 +263,20 @@ igm_status pmg_ilut_host(int n, const int* ptr, const int* col, const double* va
                          double fill, int* nnz_l, int* nnz_u, int* l_ptr, int* l_col,
                          double* l_val, int* u_ptr, int* u_col, double* u_val);
 
+/* The order-1 operator M_1 + kappa_dt K_1 of the p-multigrid's coarse
+ * correction and its h-multigrid hierarchy as pmg_setup builds it (Sec. 4,
+ * Fig. 5: bilinear prolongation, Galerkin coarse operators P^T A P, coarsening
+ * while the element count is even and above coarsest_nel), on the HOST; needs
+ * no device.  Level 0 is the operator on the descriptor's mesh.  *nlevels =
+ * the number of h-levels; *n = interior nodes per direction of the level;
+ * out (HOST [n*n*9], may be NULL) = its 9-point stencil, out[i*9 + (dy+1)*3 +
+ * (dx+1)] coupling node i = ix + n*iy to (ix+dx) + n*(iy+dy), 0 outside the
+ * grid.  The descriptor is iga_assemble's (its p only sets the quadrature
+ * rule, p+1 points, unless nquad > 0).  IGM_ERR_ARG for invalid input or a
+ * level beyond the coarsest. */
+igm_status pmg_hmg_host(const iga_desc* desc, double kappa_dt, int coarsest_nel, int level,
+                        int* nlevels, int* n, double* out);
+
 /* ---------------------------------------------------------------------------
  * MGRIT (Sec. 3).
  * ------------------------------------------------------------------------ */

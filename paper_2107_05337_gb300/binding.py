@@ -63,6 +63,8 @@ EXPORTS = {
     "iga_assemble_host": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
     "iga_transfer_host": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                   POINTER(c_double)]),
+    "pmg_hmg_host": (c_int, [c_void_p, c_double, c_int, c_int, POINTER(c_int), POINTER(c_int),
+                             POINTER(c_double)]),
     "pmg_ilut_host": (c_int, [c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double), c_double,
                               c_double, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int), POINTER(c_double), POINTER(c_int), POINTER(c_int),
@@ -266,6 +268,36 @@ def transfer_host(p, nel, geom="unit_square", nquad=0):
                                    col.ctypes.data_as(POINTER(c_int)),
                                    val.ctypes.data_as(POINTER(c_double))))
     return sp.csr_matrix((val[:nnz.value], col[:nnz.value], ptr), shape=(n * n, n1 * n1))
+
+
+def hmg_host(p, nel, kappa_dt, geom="unit_square", coarsest_nel=8):
+    """pmg_hmg_host: the order-1 operators of every h-level as scipy CSR."""
+    import scipy.sparse as sp
+    d, ctrl = _desc(p, nel, geom, 1.0, 0)
+    nlev, n = c_int(), c_int()
+    _check(lib().pmg_hmg_host(ctypes.byref(d), kappa_dt, coarsest_nel, 0, ctypes.byref(nlev),
+                              None, None))
+    out = []
+    for lev in range(nlev.value):
+        _check(lib().pmg_hmg_host(ctypes.byref(d), kappa_dt, coarsest_nel, lev, None,
+                                  ctypes.byref(n), None))
+        m = n.value
+        st = np.zeros(m * m * 9)
+        _check(lib().pmg_hmg_host(ctypes.byref(d), kappa_dt, coarsest_nel, lev, None, None,
+                                  st.ctypes.data_as(POINTER(c_double))))
+        i = np.arange(m * m)
+        ix, iy = i % m, i // m
+        rows, cols, vals = [], [], []
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                jx, jy = ix + dx, iy + dy
+                ok = (jx >= 0) & (jx < m) & (jy >= 0) & (jy < m)
+                rows.append(i[ok])
+                cols.append((jx + m * jy)[ok])
+                vals.append(st[i[ok] * 9 + (dy + 1) * 3 + (dx + 1)])
+        out.append(sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                                 shape=(m * m, m * m)))
+    return out
 
 
 class Problem:

@@ -223,6 +223,41 @@ extern "C" igm_status iga_transfer_host(const iga_desc* desc, int* nnz, int* ptr
   return IGM_OK;
 }
 
+// The p = 1 operator M_1 + c K_1 and its Galerkin h-hierarchy (Sec. 4, Fig. 5):
+// coarsen while the element count is even and above coarsest_nel, at most kMaxH levels.
+static std::vector<Stencil> hmg_hierarchy(const Discretisation& lo, double c, int coarsest_nel) {
+  std::vector<Stencil> H;
+  Stencil A1 = lo.M;
+  for (size_t i = 0; i < A1.val.size(); ++i) A1.val[i] = lo.M.val[i] + c * lo.K.val[i];
+  H.push_back(A1);
+  int nel_k = lo.nel;
+  while (nel_k > coarsest_nel && nel_k % 2 == 0 && (int)H.size() < kMaxH) {
+    H.push_back(galerkin_coarse(H.back()));
+    nel_k /= 2;
+  }
+  return H;
+}
+
+extern "C" igm_status pmg_hmg_host(const iga_desc* desc, double kappa_dt, int coarsest_nel,
+                                   int level, int* nlevels, int* n, double* out) {
+  if (!desc) return fail(IGM_ERR_ARG, "null argument");
+  if (desc->nel < 2 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [2, 1024]");
+  if (coarsest_nel < 2 || level < 0) return fail(IGM_ERR_ARG, "coarsest_nel >= 2, level >= 0");
+  Geometry g;
+  const std::string ge = make_geometry(desc, g);
+  if (!ge.empty()) return fail(IGM_ERR_ARG, ge);
+  Discretisation lo;
+  const int nq = desc->nquad > 0 ? desc->nquad : desc->p + 1;
+  const std::string e = assemble(g, 1, desc->nel, nq, lo);
+  if (!e.empty()) return fail(IGM_ERR_ARG, e);
+  const std::vector<Stencil> H = hmg_hierarchy(lo, kappa_dt, coarsest_nel);
+  if (nlevels) *nlevels = (int)H.size();
+  if (level >= (int)H.size()) return fail(IGM_ERR_ARG, "level beyond the coarsest h-level");
+  if (n) *n = H[level].n;
+  if (out) std::memcpy(out, H[level].val.data(), H[level].val.size() * sizeof(double));
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
   if (!desc || !out) return fail(IGM_ERR_ARG, "null argument");
   if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");
@@ -583,15 +618,7 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   if (e.empty()) e = block_upper(h->U, n, BU);
   if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
   // p = 1 operator and its h-hierarchy (Sec. 4, Fig. 5)
-  std::vector<Stencil> H;
-  Stencil A1 = lo.M;
-  for (size_t i = 0; i < A1.val.size(); ++i) A1.val[i] = lo.M.val[i] + kappa_dt * lo.K.val[i];
-  H.push_back(A1);
-  int nel_k = hi.nel;
-  while (nel_k > o.hmg_coarsest_nel && nel_k % 2 == 0 && (int)H.size() < kMaxH) {
-    H.push_back(galerkin_coarse(H.back()));
-    nel_k /= 2;
-  }
+  std::vector<Stencil> H = hmg_hierarchy(lo, kappa_dt, o.hmg_coarsest_nel);
   std::vector<double> Cinv;
   e = spd_inverse(H.back(), Cinv);
   if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);

@@ -6,7 +6,7 @@ the call needs no device."""
 import numpy as np
 import pytest
 
-from oracle import assembly, geometry
+from oracle import assembly, geometry, pmg
 
 
 @pytest.fixture(scope="module")
@@ -49,3 +49,20 @@ def test_host_transfer_matches_oracle(B, geom, G, p, nel):
     assert H.shape == O.shape
     assert (abs(H) > 0).nnz == (abs(O) > 0).nnz
     assert abs(H - O).max() <= 1e-13 * abs(O).max()
+
+
+@pytest.mark.parametrize("geom,G", [("unit_square", geometry.UnitSquare),
+                                    ("quarter_annulus", geometry.QuarterAnnulus)])
+@pytest.mark.parametrize("p,nel,coarsest", [(2, 32, 8), (4, 16, 8), (3, 24, 4), (2, 12, 8)])
+def test_host_h_hierarchy_matches_oracle(B, geom, G, p, nel, coarsest):
+    """The order-1 operator and its Galerkin h-levels (Sec. 4, Fig. 5): the same
+    number of levels (coarsening while the element count is even and above the
+    coarsest) and the same operators as the oracle's P^T A P."""
+    hi, lo = assembly.problem(p, nel, G())
+    c = 1.0 / 64
+    O = pmg.HMG((lo.M + c * lo.K).tocsr(), nel, coarsest).A
+    H = B.hmg_host(p, nel, c, geom, coarsest)
+    assert len(H) == len(O)
+    for h, o in zip(H, O):
+        assert h.shape == o.shape
+        assert abs(h - o).max() <= 1e-13 * abs(o).max()
