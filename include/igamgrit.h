@@ -142,6 +142,15 @@ igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, d
 igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x, float* y,
                          long ld, igm_stream s);
 
+/* The shared-memory plan iga_apply_f32 uses for an n x n grid at order p on a
+ * device with smem_max bytes of opt-in shared memory per block (HOST out[7]):
+ * the grid-line cap of the chosen layout (68 or 84; 0 when the grid does not
+ * fit and iga_apply_f32 refuses it), the copy-ring depth, grid lines per
+ * thread, the padded row stride of the staged columns, the row stride and row
+ * count of the (tm, tk) buffers, and the dynamic shared bytes per CTA.  Host
+ * only (needs no device).  IGM_ERR_ARG for p outside [2, 8] or n < 1. */
+igm_status iga_apply_f32_layout(int n, int p, long smem_max, int* out);
+
 /* ---------------------------------------------------------------------------
  * p-multigrid (Sec. 4) for A = M + c K, c = kappa*dt.
  * ------------------------------------------------------------------------ */

@@ -63,6 +63,7 @@ EXPORTS = {
     "iga_assemble_host": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_double)]),
     "iga_transfer_host": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                   POINTER(c_double)]),
+    "iga_apply_f32_layout": (c_int, [c_int, c_int, c_long, POINTER(c_int)]),
     "pmg_hmg_host": (c_int, [c_void_p, c_double, c_int, c_int, POINTER(c_int), POINTER(c_int),
                              POINTER(c_double)]),
     "pmg_ilut_host": (c_int, [c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double), c_double,
@@ -298,6 +299,13 @@ def hmg_host(p, nel, kappa_dt, geom="unit_square", coarsest_nel=8):
         out.append(sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                  shape=(m * m, m * m)))
     return out
+
+
+def apply_f32_layout(n, p, smem_max=232448):
+    """iga_apply_f32_layout as a dict (cap 0: the grid does not fit)."""
+    out = (c_int * 7)()
+    _check(lib().iga_apply_f32_layout(n, p, smem_max, out))
+    return dict(zip(("cap", "ring", "J", "xs", "ns", "rows", "smem"), list(out)))
 
 
 class Problem:

@@ -1125,6 +1125,13 @@ extern "C" igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const d
   return IGM_OK;
 }
 
+extern "C" igm_status iga_apply_f32_layout(int n, int p, long smem_max, int* out) {
+  if (!out || n < 1 || p < 2 || p > 8 || smem_max <= 0)
+    return fail(IGM_ERR_ARG, "iga_apply_f32_layout: n >= 1, p in [2, 8], smem_max > 0, out");
+  spmm32_layout(n, p, (size_t)smem_max, out);
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x,
                                     float* y, long ld, igm_stream s) {
   if (!ops || (nrhs > 0 && (!x || !y))) return fail(IGM_ERR_ARG, "null argument");

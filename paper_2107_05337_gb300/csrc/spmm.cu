@@ -299,6 +299,38 @@ cudaError_t launch_w(int n, int nrhs, const float* M1, const float* K1, SpmmCoef
 
 }  // namespace
 
+template <int W>
+void layout_w(int n, size_t smem_max, int* out) {
+  int cap, nb;
+  plan<W>(n, smem_max, &cap, &nb);
+  out[0] = cap;
+  out[1] = nb;
+  if (cap == kCaps[0] || cap == kCaps[1]) {
+    const bool a = cap == kCaps[0];
+    out[2] = a ? Lay<W, kCaps[0]>::J : Lay<W, kCaps[1]>::J;
+    out[3] = a ? Lay<W, kCaps[0]>::XS : Lay<W, kCaps[1]>::XS;
+    out[4] = a ? Lay<W, kCaps[0]>::NS : Lay<W, kCaps[1]>::NS;
+    out[5] = a ? Lay<W, kCaps[0]>::R : Lay<W, kCaps[1]>::R;
+    out[6] = (int)(a ? smem_of<W, kCaps[0]>(n, nb) : smem_of<W, kCaps[1]>(n, nb));
+  } else {
+    out[2] = out[3] = out[4] = out[5] = out[6] = 0;
+  }
+}
+
+int spmm32_layout(int n, int p, size_t smem_max, int* out) {
+  switch (p) {
+    case 2: layout_w<5>(n, smem_max, out); break;
+    case 3: layout_w<7>(n, smem_max, out); break;
+    case 4: layout_w<9>(n, smem_max, out); break;
+    case 5: layout_w<11>(n, smem_max, out); break;
+    case 6: layout_w<13>(n, smem_max, out); break;
+    case 7: layout_w<15>(n, smem_max, out); break;
+    case 8: layout_w<17>(n, smem_max, out); break;
+    default: return 0;
+  }
+  return out[0] != 0;
+}
+
 int spmm32_slots(int n, int p, size_t smem_max) {
   switch (p) {
     case 2: return slots_w<5>(n, smem_max);

@@ -21,5 +21,10 @@ cudaError_t launch_spmm32(int n, int p, int nrhs, const float* M1, const float* 
                           cudaStream_t st);
 // copy ring depth the kernel would use for an n x n grid (0: does not fit)
 int spmm32_slots(int n, int p, size_t smem_max);
+// The shared-memory plan for an n x n grid: out[7] = {grid-line cap of the
+// layout (0: does not fit), ring depth, grid lines per thread J, padded x row
+// stride, (tm, tk) row stride in pairs, (tm, tk) rows, dynamic shared bytes}.
+// Returns 1 when the grid fits.  Host code only.
+int spmm32_layout(int n, int p, size_t smem_max, int* out);
 
 }  // namespace igm
