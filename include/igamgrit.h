@@ -286,6 +286,22 @@ igm_status pmg_ilut_host(int n, const int* ptr, const int* col, const double* va
 igm_status pmg_hmg_host(const iga_desc* desc, double kappa_dt, int coarsest_nel, int level,
                         int* nlevels, int* n, double* out);
 
+/* The block-row form in which the ILUT sweeps consume a factor (Sec. 4's
+ * smoother: L y = r and U z = y, solved one grid row at a time), on the HOST;
+ * needs no device.  Input: an ILUT factor of an n x n grid of unknowns (N =
+ * n^2, i = ix + n*iy) as HOST CSR (ptr[N+1], col, val): upper = 0: L strictly
+ * lower (unit diagonal implied), upper = 1: U upper with the diagonal.
+ * Outputs: the entries coupling to other grid rows as CSR (call once with
+ * NULL arrays for *nnz_off, then with off_ptr [N+1] and arrays of that size),
+ * and inv (HOST [n * n(n+1)/2], may be NULL) = the inverse of each grid row's
+ * diagonal block, packed per block iy: for L, row r holds columns 0..r at
+ * r(r+1)/2 + j; for U, row r holds columns r..n-1 at r*n - r(r-1)/2 + (j-r).
+ * IGM_ERR_ARG for malformed input or an entry outside the triangle,
+ * IGM_ERR_NUMERIC for a zero diagonal of U. */
+igm_status pmg_block_tri_host(int n, int upper, const int* ptr, const int* col, const double* val,
+                              int* nnz_off, int* off_ptr, int* off_col, double* off_val,
+                              double* inv);
+
 /* ---------------------------------------------------------------------------
  * MGRIT (Sec. 3).
  * ------------------------------------------------------------------------ */

@@ -64,6 +64,9 @@ EXPORTS = {
     "iga_transfer_host": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                   POINTER(c_double)]),
     "iga_apply_f32_layout": (c_int, [c_int, c_int, c_long, POINTER(c_int)]),
+    "pmg_block_tri_host": (c_int, [c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double),
+                                   POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                   POINTER(c_double), POINTER(c_double)]),
     "pmg_hmg_host": (c_int, [c_void_p, c_double, c_int, c_int, POINTER(c_int), POINTER(c_int),
                              POINTER(c_double)]),
     "pmg_ilut_host": (c_int, [c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double), c_double,
@@ -195,6 +198,40 @@ def ilut_host(A, droptol=1e-12, fill=1.0):
     L = sp.csr_matrix((lv[:nl.value], lc[:nl.value], lp), shape=(n, n))
     U = sp.csr_matrix((uv[:nu.value], uc[:nu.value], up), shape=(n, n))
     return L, U
+
+
+def block_tri_host(F, n, upper):
+    """pmg_block_tri_host on a scipy CSR factor of an n x n grid: (off-block
+    CSR, [n] list of dense n x n inverses of the grid rows' diagonal blocks)."""
+    import scipy.sparse as sp
+    F = sp.csr_matrix(F)
+    N = n * n
+    ptr = np.ascontiguousarray(F.indptr, dtype=np.int32)
+    col = np.ascontiguousarray(F.indices, dtype=np.int32)
+    val = np.ascontiguousarray(F.data, dtype=np.float64)
+    ip = lambda a: a.ctypes.data_as(POINTER(c_int))
+    dp = lambda a: a.ctypes.data_as(POINTER(c_double))
+    nnz = c_int()
+    _check(lib().pmg_block_tri_host(n, int(upper), ip(ptr), ip(col), dp(val), ctypes.byref(nnz),
+                                    None, None, None, None))
+    op = np.zeros(N + 1, np.int32)
+    oc = np.zeros(max(nnz.value, 1), np.int32)
+    ov = np.zeros(max(nnz.value, 1))
+    inv = np.zeros(n * n * (n + 1) // 2)
+    _check(lib().pmg_block_tri_host(n, int(upper), ip(ptr), ip(col), dp(val), None, ip(op),
+                                    ip(oc), dp(ov), dp(inv)))
+    off = sp.csr_matrix((ov[:nnz.value], oc[:nnz.value], op), shape=(N, N))
+    blocks, per = [], n * (n + 1) // 2
+    for b in range(n):
+        pk, X = inv[b * per:(b + 1) * per], np.zeros((n, n))
+        for r in range(n):
+            if upper:
+                base = r * n - r * (r - 1) // 2
+                X[r, r:] = pk[base:base + n - r]
+            else:
+                X[r, :r + 1] = pk[r * (r + 1) // 2:r * (r + 1) // 2 + r + 1]
+        blocks.append(X)
+    return off, blocks
 
 
 def quarter_annulus_net():

@@ -3,6 +3,8 @@
 // MGRIT sweeps (Sec. 3).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -1101,6 +1103,36 @@ extern "C" igm_status pmg_ilut_host(int n, const int* ptr, const int* col, const
   if (u_ptr) std::memcpy(u_ptr, U.ptr.data(), U.ptr.size() * sizeof(int));
   if (u_col) std::memcpy(u_col, U.col.data(), U.col.size() * sizeof(int));
   if (u_val) std::memcpy(u_val, U.val.data(), U.val.size() * sizeof(double));
+  return IGM_OK;
+}
+
+extern "C" igm_status pmg_block_tri_host(int n, int upper, const int* ptr, const int* col,
+                                         const double* val, int* nnz_off, int* off_ptr,
+                                         int* off_col, double* off_val, double* inv) {
+  if (n < 1 || n > 4096 || !ptr || !col || !val)
+    return fail(IGM_ERR_ARG, "pmg_block_tri_host: n in [1, 4096], non-null CSR arrays");
+  const int N = n * n;
+  if (ptr[0] != 0) return fail(IGM_ERR_ARG, "pmg_block_tri_host: ptr[0] must be 0");
+  for (int i = 0; i < N; ++i)
+    if (ptr[i + 1] < ptr[i]) return fail(IGM_ERR_ARG, "pmg_block_tri_host: ptr must not decrease");
+  for (int k = 0; k < ptr[N]; ++k) {
+    const int i = (int)(std::upper_bound(ptr, ptr + N + 1, k) - ptr) - 1;
+    if (col[k] < 0 || col[k] >= N || (upper ? col[k] < i : col[k] >= i))
+      return fail(IGM_ERR_ARG, "pmg_block_tri_host: entry outside the factor's triangle");
+  }
+  Csr F;
+  F.rows = F.cols = N;
+  F.ptr.assign(ptr, ptr + N + 1);
+  F.col.assign(col, col + ptr[N]);
+  F.val.assign(val, val + ptr[N]);
+  BlockTri B;
+  const std::string e = upper ? block_upper(F, n, B) : block_lower(F, n, B);
+  if (!e.empty()) return fail(IGM_ERR_NUMERIC, e);
+  if (nnz_off) *nnz_off = B.off.nnz();
+  if (off_ptr) std::memcpy(off_ptr, B.off.ptr.data(), B.off.ptr.size() * sizeof(int));
+  if (off_col) std::memcpy(off_col, B.off.col.data(), B.off.col.size() * sizeof(int));
+  if (off_val) std::memcpy(off_val, B.off.val.data(), B.off.val.size() * sizeof(double));
+  if (inv) std::memcpy(inv, B.inv.data(), B.inv.size() * sizeof(double));
   return IGM_OK;
 }
 

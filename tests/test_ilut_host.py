@@ -63,3 +63,33 @@ def test_errors(B):
         B.ilut_host(A)
     with pytest.raises(B.IgmError):        # negative drop tolerance
         B.ilut_host(sp.identity(3, format="csr"), droptol=-1.0)
+
+
+@pytest.mark.parametrize("geom,p,nel", [(geometry.UnitSquare, 3, 8), (geometry.QuarterAnnulus, 4, 6)])
+def test_block_row_form_of_the_factors(B, geom, p, nel):
+    """pmg_block_tri_host (the data the ILUT sweeps stream): the couplings to
+    other grid rows plus the diagonal blocks give back the factor exactly, and
+    each packed inverse is the inverse of its (unit-)triangular diagonal block."""
+    hi, lo = assembly.problem(p, nel, geom())
+    P = pmg.PMG(hi, lo, 1.0 / 64)
+    L, U = B.ilut_host(P.A)
+    n = hi.n
+    N = n * n
+    for F, upper in ((L, False), (U, True)):
+        off, inv = B.block_tri_host(F, n, upper)
+        D = sp.lil_matrix((N, N))
+        dense = F.toarray()
+        for b in range(n):
+            s = slice(b * n, (b + 1) * n)
+            blk = dense[s, s] + (0.0 if upper else np.eye(n))
+            I = inv[b] @ blk
+            assert np.abs(I - np.eye(n)).max() <= 1e-10, (upper, b)
+            D[s, s] = dense[s, s]
+        assert abs(off + D.tocsr() - F).max() == 0.0
+        assert all(c // n != r // n for r in range(N) for c in off.indices[off.indptr[r]:off.indptr[r + 1]])
+
+
+def test_block_row_form_rejects_entries_outside_the_triangle(B):
+    F = sp.csr_matrix(np.triu(np.ones((4, 4))))      # n = 2: an upper factor passed as lower
+    with pytest.raises(B.IgmError):
+        B.block_tri_host(F, 2, upper=False)
