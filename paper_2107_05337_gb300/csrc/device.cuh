@@ -273,26 +273,6 @@ __device__ __forceinline__ void for_group_rows(int nrows, F&& f) {
   }
 }
 
-// As for_group_rows with G lanes per row (G a power of two <= 32).
-template <int G, typename F>
-__device__ __forceinline__ void for_rows_g(int nrows, F&& f) {
-  const int gl = threadIdx.x % G;
-  const int per = blockDim.x / G;
-  const int wrow = (int)(threadIdx.x & ~31u) / G;
-  for (int r0 = 0; r0 < nrows; r0 += per) {
-    if (r0 + wrow >= nrows) break;
-    const int r = r0 + (int)threadIdx.x / G;
-    f(r, r < nrows, gl);
-  }
-}
-
-template <int G, typename T>
-__device__ __forceinline__ T group_sum_g(T s) {
-#pragma unroll
-  for (int o = 1; o < G; o <<= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  return s;
-}
-
 // ---------------------------------------------------------------------------
 // operator application: affine sum factorisation and curved stencils
 // ---------------------------------------------------------------------------
@@ -452,13 +432,6 @@ __device__ double apply_stencil(int n, int w, const T* sA, const S* x, const S* 
 // ---------------------------------------------------------------------------
 // block-row triangular sweeps (ILUT factors) and Gauss--Seidel
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ size_t lower_off(int i) { return (size_t)i * (i + 1) / 2; }
-__device__ __forceinline__ size_t upper_off(int i, int n) {
-  return (size_t)i * n - (size_t)i * (i - 1) / 2;
-}
-
-__device__ __forceinline__ int align16(int bytes) { return (bytes + 15) & ~15; }
-
 // Byte offsets inside a factor record (must match the host packing in
 // capi.cu).  Record of grid row `by`: int header[4] = {KF, KN, by, 0}; the
 // off-block entries coupling to grid rows two or more steps back in the sweep

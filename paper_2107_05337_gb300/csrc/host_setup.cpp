@@ -565,29 +565,6 @@ std::string block_upper(const Csr& U, int n, BlockTri& out) {
   return "";
 }
 
-std::string gs_blocks(const Stencil& A, std::vector<double>& inv) {
-  if (A.w != 1) return "gs_blocks: 9-point operator expected";
-  const int n = A.n;
-  inv.assign((size_t)n * lower_off(n), 0.0);
-  for (int by = 0; by < n; ++by) {
-    double* blk = &inv[(size_t)by * lower_off(n)];
-    // (D + W) lower bidiagonal: diag a_C(r), sub a_W(r) (coupling to r-1)
-    std::vector<double> x(n);
-    for (int j = 0; j < n; ++j) {
-      for (int r = 0; r < n; ++r) x[r] = 0.0;
-      for (int r = j; r < n; ++r) {
-        const double* a = &A.val[(size_t)(by * n + r) * 9];
-        double rhs = (r == j) ? 1.0 : 0.0;
-        if (r > j) rhs -= a[3] * x[r - 1];  // a[(dy+1)*3 + (dx+1)], W at (dx,dy)=(-1,0)
-        if (a[4] == 0.0) return "gs_blocks: zero diagonal";
-        x[r] = rhs / a[4];
-      }
-      for (int r = j; r < n; ++r) blk[lower_off(r) + j] = x[r];
-    }
-  }
-  return "";
-}
-
 Stencil galerkin_coarse(const Stencil& A) {
   // fine grid nf = 2 nc + 1 interior nodes per direction; coarse node J
   // (0-based c) sits at fine index 2c+1 with weights 1/2, 1, 1/2 on 2c, 2c+1, 2c+2.

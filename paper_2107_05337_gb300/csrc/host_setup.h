@@ -23,7 +23,6 @@ struct Stencil {
   int n = 0, w = 0;
   std::vector<double> val;
   int width() const { return 2 * w + 1; }
-  int per_row() const { return width() * width(); }
   Csr to_csr(bool drop_zeros) const;
 };
 
@@ -90,10 +89,6 @@ struct BlockTri {
 };
 std::string block_lower(const Csr& L, int n, BlockTri& out);  // L strictly lower, unit diag
 std::string block_upper(const Csr& U, int n, BlockTri& out);  // U with diagonal
-
-// Gauss--Seidel block data for a 9-point operator A on an n x n grid: the
-// dense inverse of (D + W) for every grid row (lower packed).
-std::string gs_blocks(const Stencil& A, std::vector<double>& inv);
 
 // Galerkin coarse operator P^T A P for the bilinear prolongation from an
 // (nc x nc)-unknown grid (nel_c elements) to the (2 nel_c - 1)^2 grid.

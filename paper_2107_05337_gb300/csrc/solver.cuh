@@ -229,12 +229,6 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
   return true;
 }
 
-__device__ __forceinline__ double block_dot(const double* a, int N, double* red) {
-  double s = 0.0;
-  IGM_FOR_CTA(i, N) s += a[i] * a[i];
-  return block_sum(s, red);
-}
-
 // Conjugate gradients with the preconditioner D^-1 = diag(A)^-1 on A x = b
 // in FP64 (the comparison solver of Sec. 5), warm start x, on the FP64
 // arena: r at o_t; p, q and the operator's two temporaries at o_u.
