@@ -6,8 +6,8 @@
  * Problem (Sec. 2, Eq. (heat)): d_t u - kappa Laplace(u) = f on
  * Omega = F((0,1)^2), u = 0 on the boundary, u(.,0) = u0.  B-splines of order
  * p on a uniform open knot vector with nel elements per direction (Sec. 2);
- * backward Euler, theta = 1 (Sec. 2, Eq. (los)):
- *     (M + kappa dt K) u^{k+1} = M u^k + dt f^{k+1}.
+ * the theta-scheme of Sec. 2, Eq. (los), backward Euler (theta = 1) by default:
+ *     (M + theta kappa dt K) u^{k+1} = (M - (1-theta) kappa dt K) u^k + dt f.
  * Each such spatial solve is done by the p-multigrid cycle of Sec. 4 (ILUT
  * smoother, L2-projection transfers to p = 1, one h-multigrid W-cycle with
  * Gauss--Seidel at p = 1, direct coarsest solve).  The time stepping is
@@ -53,7 +53,8 @@ typedef void* igm_stream; /* a cudaStream_t */
  * Discretisation (Sec. 2).
  * ------------------------------------------------------------------------ */
 typedef struct {
-  int p;          /* B-spline order p >= 1 (Sec. 2, Cox--de Boor) */
+  int p;          /* B-spline order (Sec. 2, Cox--de Boor): 2..8 for iga_assemble,
+                     1..8 for the host-side calls */
   int nel;        /* elements per direction (uniform open knot vector, span 1/nel) */
   int nquad;      /* Gauss points per direction per element; 0 -> p+1 */
   int geom;       /* 0: unit square (affine, F = identity);
@@ -69,8 +70,10 @@ typedef struct iga_ops iga_ops;
 /* Assemble M, K (Sec. 2), the order-1 matrices on the same knots, the
  * transfer matrix P_1^p and the row-sum lumped masses (Sec. 4, Eq. (PM)) on
  * the host with Gauss quadrature, and upload them.  *out receives a handle.
- * Errors: IGM_ERR_ARG for p < 1, nel < 2, a geometry with a non-positive
- * Jacobian determinant sign change, or an invalid control net. */
+ * Errors: IGM_ERR_ARG for p outside [2, 8], nel outside [4, 1024] or an
+ * invalid geometry control net (the map is assumed regular: the quadrature
+ * uses |det J|); IGM_ERR_CUDA without a device; IGM_ERR_OOM when the upload
+ * fails. */
 igm_status iga_assemble(const iga_desc* desc, iga_ops** out);
 void iga_destroy(iga_ops* ops);
 
@@ -107,7 +110,7 @@ igm_status iga_basis_eval(int p, int nel, int nx, const double* x, int* span, do
  * the grid (HOST out [n*n*(2p+1)^2]); which = 2: the lumped masses (full-basis
  * row sums of M on the interior rows, HOST out [n*n]).  *n = interior
  * unknowns per direction; out may be NULL to query n.  The descriptor is
- * iga_assemble's, with p in [1, 8] and nel in [1, 1024]; IGM_ERR_ARG for
+ * iga_assemble's, with p in [1, 8] and nel in [2, 1024]; IGM_ERR_ARG for
  * invalid input. */
 igm_status iga_assemble_host(const iga_desc* desc, int which, int* n, double* out);
 
@@ -116,7 +119,8 @@ igm_status iga_assemble_host(const iga_desc* desc, int which, int* n, double* ou
  * interior x interior, as iga_assemble builds it, on the HOST; needs no
  * device.  CSR over the N = n^2 order-p rows (ptr [N+1], col, val: columns are
  * the interior order-1 unknowns); call once with NULL arrays for *nnz, then
- * with arrays of that size.  The descriptor is iga_assemble's (p in [2, 8]);
+ * with arrays of that size.  The descriptor is iga_assemble's (p in [2, 8], nel in
+ * [2, 1024]);
  * IGM_ERR_ARG for invalid input. */
 igm_status iga_transfer_host(const iga_desc* desc, int* nnz, int* ptr, int* col, double* val);
 
@@ -138,7 +142,8 @@ igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, d
  * the previous column along eta).  The operator of Eq. (los) applied to a
  * block of right-hand sides such as the time points of an interval.
  * IGM_ERR_ARG on the curved map, or when the n x n grid (n = N^(1/2)) does not
- * fit the shared-memory pipeline (about n > 90). */
+ * fit the shared-memory layouts (n > 84, or a device with less shared memory
+ * than the plan needs; iga_apply_f32_layout reports the plan). */
 igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x, float* y,
                          long ld, igm_stream s);
 
@@ -182,10 +187,13 @@ typedef struct pmg_handle pmg_handle;
 void pmg_default_opts(pmg_opts* o);
 
 /* Build the p-multigrid hierarchy for A = M + kappa_dt K: ILUT factors in
- * natural order with their block-row (grid-row) schedule and dense
+ * natural order with their block-row (grid-row) form and dense
  * diagonal-block inverses, the p=1 operator and its Galerkin h-hierarchy
- * with Gauss--Seidel block data, and the coarsest dense factor.  Host setup
- * plus one upload.  Errors: IGM_ERR_NUMERIC on a zero ILUT pivot. */
+ * (9-point stencils), and the coarsest dense inverse.  Host setup plus one
+ * upload.  Errors: IGM_ERR_ARG for invalid options or a mesh the p = 1
+ * sweeps do not support (nel > 129), IGM_ERR_NUMERIC on a zero ILUT pivot or
+ * a coarsest operator that is not positive definite, IGM_ERR_OOM/CUDA when
+ * the upload fails. */
 igm_status pmg_setup(const iga_ops* ops, double kappa_dt, const pmg_opts* opts, pmg_handle** out);
 void pmg_destroy(pmg_handle* h);
 

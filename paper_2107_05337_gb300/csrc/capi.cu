@@ -187,7 +187,7 @@ static std::string make_geometry(const iga_desc* desc, Geometry& g) {
 extern "C" igm_status iga_assemble_host(const iga_desc* desc, int which, int* n, double* out) {
   if (!desc) return fail(IGM_ERR_ARG, "null argument");
   if (desc->p < 1 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [1, 8]");
-  if (desc->nel < 1 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [1, 1024]");
+  if (desc->nel < 2 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [2, 1024]");
   if (which < 0 || which > 2) return fail(IGM_ERR_ARG, "which must be 0 (M), 1 (K) or 2 (lumped)");
   Geometry g;
   const std::string ge = make_geometry(desc, g);
@@ -208,7 +208,7 @@ extern "C" igm_status iga_transfer_host(const iga_desc* desc, int* nnz, int* ptr
                                         double* val) {
   if (!desc) return fail(IGM_ERR_ARG, "null argument");
   if (desc->p < 2 || desc->p > 8) return fail(IGM_ERR_ARG, "p must be in [2, 8]");
-  if (desc->nel < 1 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [1, 1024]");
+  if (desc->nel < 2 || desc->nel > 1024) return fail(IGM_ERR_ARG, "nel must be in [2, 1024]");
   Geometry g;
   const std::string ge = make_geometry(desc, g);
   if (!ge.empty()) return fail(IGM_ERR_ARG, ge);
