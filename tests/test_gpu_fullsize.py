@@ -39,19 +39,23 @@ def test_wait_selftest_times_out_and_device_stays_usable(B):
 @pytest.mark.parametrize("p", [2, 3, 4, 5])
 def test_heat_c2_full_size(B, p):
     """Unit square, 64 x 64 elements, N_t = 256, m = 4, 256 -> 64 -> 16 -> 4.
-    Bench tolerances (1e-10, both forms): error vs sequential BE within the
-    tolerance-stacking bound 5e-10; tight tolerances: within 1e-10."""
+    Bench tolerances (1e-10; the mixed and FP64 forms, and the benchmarked form
+    with one cycle per coarse-level solve and autotuned sweep layouts): error
+    vs sequential BE within the tolerance-stacking bound 5e-10; tight
+    tolerances: within 1e-10."""
     nel, T, Nt = 64, 1.0, 256
     d = assembly.Discretisation(p, nel, geometry.UnitSquare())
     seq = timestep.sequential(d.M, d.K, 1.0, T, Nt, d.project(S), d.load_vector(S), C)
     prob = B.Problem(p, nel)
     u0, fhat = prob.project(S), prob.load_vector(S)
     fc = np.array([C(n * T / Nt) for n in range(Nt + 1)])
-    for precision in (1, 0):
-        mg = B.MGRIT(prob, T=T, Nt=Nt, m=4, tol=1e-10, pmg=dict(precision=precision, tol=1e-10))
+    forms = ((dict(precision=1, tol=1e-10), {}), (dict(precision=0, tol=1e-10), {}),
+             (dict(precision=1, tol=1e-10, autotune=1), dict(coarse_cycles=1)))
+    for pmg_opts, extra in forms:
+        mg = B.MGRIT(prob, T=T, Nt=Nt, m=4, tol=1e-10, pmg=pmg_opts, **extra)
         U, st, _ = mg.run(u0, fhat, fc)
         assert st["levels"] == 4 and 7 <= st["iters"] <= 12
-        assert _rel(U.cpu().numpy(), seq) < 5e-10, (precision, st)
+        assert _rel(U.cpu().numpy(), seq) < 5e-10, (pmg_opts, extra, st)
     mg = B.MGRIT(prob, T=T, Nt=Nt, m=4, tol=1e-12, pmg=dict(precision=1, tol=1e-13))
     U, st, _ = mg.run(u0, fhat, fc)
     assert _rel(U.cpu().numpy(), seq) < 1e-10, st
