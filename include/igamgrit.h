@@ -179,6 +179,13 @@ typedef struct {
                              of the ILUT sweeps (sweep team of 128 or 256 threads; arena in shared
                              memory, swept vector staged in shared memory, or everything in global
                              memory) on a probe solve at setup and keep the fastest */
+  int layout;             /* 0: the fixed policy or autotune (default); 1..6 force one layout
+                             of the ILUT sweeps (for tests and measurements): sweep teams of
+                             128 (1..3) or 256 (4..6) threads, with the working vectors in
+                             shared memory (1, 4), the swept vector staged in shared memory and
+                             the working vectors in global memory (2, 5), or everything in
+                             global memory (3, 6); pmg_setup returns IGM_ERR_ARG when the
+                             forced layout does not fit in shared memory */
 } pmg_opts;
 
 typedef struct pmg_handle pmg_handle;
@@ -202,7 +209,10 @@ void pmg_destroy(pmg_handle* h);
  * that many cycles (p-multigrid V-cycles in the FP64 form; FP64 refinement
  * steps of inner_cycles FP32 V-cycles in the mixed form); ncycles == 0: cycle
  * until the stop test holds or max_cycles.  cycles_out: HOST [nrhs] or NULL.
- * Returns IGM_ERR_NOT_CONVERGED if some column hit max_cycles. */
+ * Synchronises the stream (the cycle counts and the status word are read
+ * back).  Returns IGM_ERR_NOT_CONVERGED if some column hit max_cycles,
+ * IGM_ERR_NUMERIC on a NaN residual, IGM_ERR_TIMEOUT if a bounded device wait
+ * gave up (the solve was abandoned part way and x is incomplete). */
 igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long ld, int ncycles,
                       int* cycles_out, igm_stream s);
 
@@ -218,10 +228,11 @@ igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, double* x, long 
  * one static 16 MiB device buffer that every device which loads the library
  * holds until the process exits.  Calls needing more than 16 MiB of scratch
  * return IGM_ERR_ARG with the required size in igm_last_error().  The first
- * call on a device looks up the buffer's device address, so make that first
- * call before any stream capture.  All calls share the buffer, which keeps
- * the last call's contents (the call clears what must start at zero): calls
- * that overlap on the GPU (other streams, other host threads) race. */
+ * call looks up the buffer's device address on the current device (which
+ * allocates nothing).  Like pmg_vcycle it synchronises the stream before it
+ * returns, to read the status word back.  All calls share the buffer, which
+ * keeps the last call's contents (the call clears what must start at zero):
+ * calls that overlap on the GPU (other streams, other host threads) race. */
 igm_status pmg_vcycle_static(pmg_handle* h, int nrhs, const double* b, double* x, long ld,
                              int ncycles, int* cycles_out, igm_stream s);
 
@@ -374,7 +385,9 @@ void mgrit_destroy(mgrit_handle* mg);
  * of a separable source f(x,t) = c(t) fhat(x) or NULL; U: DEVICE [Nt+1][N],
  * caller-owned, receives all time levels (U[0] = u0).  Reads one FP64 vector
  * of C-point residual norms back per iteration for the stopping test.
- * Returns IGM_ERR_NOT_CONVERGED when max_iter is reached first. */
+ * Returns IGM_ERR_NOT_CONVERGED when max_iter is reached first (or a spatial
+ * solve hit its cycle limit), IGM_ERR_NUMERIC on a NaN residual,
+ * IGM_ERR_TIMEOUT if a bounded device wait gave up (U is then incomplete). */
 igm_status mgrit_run(mgrit_handle* mg, const double* u0, const double* fhat, const double* fcoef,
                      double* U, mgrit_stats* stats, igm_stream s);
 

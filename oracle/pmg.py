@@ -4,9 +4,14 @@ Test infrastructure (see ``oracle/__init__``).  Pinned by
 ``tests/test_oracle_pmg.py``:
   * ILUT with drop tolerance 0 and unlimited fill is the exact LU factorisation
     (L U reproduces A; one smoothing step then solves A x = b exactly);
-  * ILUT(tau, fill) keeps at most ceil(fill*nnz) entries per row part, always
-    keeps the diagonal, and L U agrees with A on A's pattern for ILU-like
-    settings on an M-matrix example (brute-force check on a tiny matrix);
+  * ILUT(tau, fill) keeps at most ceil(fill*nnz) entries per row part and
+    always keeps the diagonal; when the limit bites it keeps the largest
+    |values|, exact ties going to the smaller column (a tiny matrix whose
+    candidates are known by hand); on the 5-point Laplacian with fill = 1 it
+    keeps exactly A's pattern;
+  * the h-multigrid cycle is a W-cycle: its error propagation operator equals
+    the one composed by hand from dense Gauss--Seidel, Galerkin and exact
+    coarsest-solve operators with two coarse visits (three-level hierarchy);
   * lexicographic Gauss--Seidel equals the textbook element-by-element sweep
     (brute-force loop on a tiny grid);
   * the L2 transfers reproduce constants on the full basis:

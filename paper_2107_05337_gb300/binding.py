@@ -31,7 +31,7 @@ class PmgOpts(ctypes.Structure):
     _fields_ = [("nu1", c_int), ("nu2", c_int), ("ilut_droptol", c_double),
                 ("ilut_fill", c_double), ("hmg_coarsest_nel", c_int), ("precision", c_int),
                 ("inner_cycles", c_int), ("tol", c_double), ("max_cycles", c_int),
-                ("trace", c_int), ("solver", c_int), ("autotune", c_int)]
+                ("trace", c_int), ("solver", c_int), ("autotune", c_int), ("layout", c_int)]
 
 
 class MgritOpts(ctypes.Structure):
@@ -440,26 +440,40 @@ class PMG:
             _LIB.pmg_destroy(self.h)
             self.h = None
 
+    def _columns(self, B, X, what):
+        """Device pointers of the column blocks B, X: contiguous CUDA float64
+        tensors of the same shape [nrhs, N] (TypeError otherwise, before any
+        launch: the kernels read and write nrhs * N doubles)."""
+        import torch
+        for t, nm in ((B, "B"), (X, "X")):
+            if t.dtype != torch.float64:
+                raise TypeError(f"{what}: {nm} must be float64, got {t.dtype}")
+        if B.dim() != 2 or tuple(B.shape) != tuple(X.shape) or B.shape[1] != self.N:
+            raise TypeError(f"{what}: B and X must both be [nrhs, {self.N}], got "
+                            f"{tuple(B.shape)} and {tuple(X.shape)}")
+        if not (B.is_contiguous() and X.is_contiguous()):
+            raise TypeError(f"{what}: B and X must be contiguous")
+        return _dptr_of(B, torch.float64, what + " B"), _dptr_of(X, torch.float64, what + " X")
+
     def solve(self, B, X, ncycles=0, check=True):
         """In-place solves on columns: B, X CUDA float64 [nrhs, N]; returns cycles per column."""
-        assert B.dtype == X.dtype and B.is_contiguous() and X.is_contiguous()
+        pb, px = self._columns(B, X, "solve")
         nrhs = B.shape[0]
-        cyc = (c_int * nrhs)()
-        st = lib().pmg_vcycle(self.h, nrhs, _dptr(B), _dptr(X), self.N, ncycles, cyc, _stream())
+        cyc = (c_int * max(nrhs, 1))()
+        st = lib().pmg_vcycle(self.h, nrhs, pb, px, self.N, ncycles, cyc, _stream())
         if check:
             _check(st)
-        return np.array(cyc[:], dtype=np.int64), st
+        return np.array(cyc[:nrhs], dtype=np.int64), st
 
     def solve_static(self, B, X, ncycles=0, check=True):
         """As solve(), through pmg_vcycle_static (no device allocation)."""
-        assert B.dtype == X.dtype and B.is_contiguous() and X.is_contiguous()
+        pb, px = self._columns(B, X, "solve_static")
         nrhs = B.shape[0]
-        cyc = (c_int * nrhs)()
-        st = lib().pmg_vcycle_static(self.h, nrhs, _dptr(B), _dptr(X), self.N, ncycles, cyc,
-                                     _stream())
+        cyc = (c_int * max(nrhs, 1))()
+        st = lib().pmg_vcycle_static(self.h, nrhs, pb, px, self.N, ncycles, cyc, _stream())
         if check:
             _check(st)
-        return np.array(cyc[:], dtype=np.int64), st
+        return np.array(cyc[:nrhs], dtype=np.int64), st
 
     def layout(self):
         """(threads per sweep team, ring slots, arena in shared memory, staged vector)."""

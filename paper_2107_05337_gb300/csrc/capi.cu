@@ -415,6 +415,7 @@ extern "C" void pmg_default_opts(pmg_opts* o) {
   o->trace = 0;
   o->solver = 0;
   o->autotune = 0;
+  o->layout = 0;
 }
 
 static void gen_wcycle(int k, int last, std::vector<int>& ops) {
@@ -603,6 +604,7 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   if (o.max_cycles < 1) return fail(IGM_ERR_ARG, "max_cycles must be >= 1");
   if (!(o.tol >= 0.0)) return fail(IGM_ERR_ARG, "tol must be >= 0");
   if (o.solver != 0 && o.solver != 1) return fail(IGM_ERR_ARG, "solver must be 0 or 1");
+  if (o.layout < 0 || o.layout > 6) return fail(IGM_ERR_ARG, "layout must be in [0, 6]");
   if (o.solver == 1) h->opts.precision = 0;  // CG runs in FP64
   h->c = kappa_dt;
   const Discretisation& hi = ops->hi;
@@ -825,7 +827,20 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   if (!arena_off) return fail(IGM_ERR_ARG, "a factor record does not fit in shared memory");
   Packed pk256;
   const Packed* chosen = &pk128;
-  if (o.autotune) {
+  if (o.layout > 0) {
+    // a forced layout: team of 128 (1..3) or 256 (4..6) threads, placement
+    // 0 arena in shared memory, 1 staged vector, 2 all global
+    const int team = o.layout <= 3 ? 128 : 256, only = (o.layout - 1) % 3;
+    if (team == 256) {
+      e = pack(256, pk256);
+      if (!e.empty()) return fail(IGM_ERR_ARG, e);
+      chosen = &pk256;
+    }
+    arena_off = place(slot_of(*chosen), team, only);
+    if (!arena_off)
+      return fail(IGM_ERR_ARG, "layout " + std::to_string(o.layout) +
+                                   " does not fit in shared memory for this problem");
+  } else if (o.autotune) {
     // time every distinct candidate layout on a probe solve (3 cycles, one
     // right-hand side) and keep the fastest
     e = pack(256, pk256);
@@ -954,6 +969,7 @@ extern "C" igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, doubl
   CU(cudaStreamSynchronize(st));
   if (cycles_out) std::memcpy(cycles_out, hc.data(), sizeof(int) * nrhs);
   if (hc[nrhs] == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
+  if (hc[nrhs] == ST_TIMEOUT) return fail(IGM_ERR_TIMEOUT, "a bounded device wait gave up");
   if (hc[nrhs] == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "spatial solve hit max_cycles");
   return IGM_OK;
 }
@@ -963,26 +979,18 @@ extern "C" igm_status pmg_vcycle(pmg_handle* h, int nrhs, const double* b, doubl
 // (status word, per-column cycle counts and, when the working vectors do not
 // fit in shared memory, the per-CTA arenas) lives in this file-scope device
 // array.  Host code must not use the array's name as a device address: the
-// address is looked up once per device with cudaGetSymbolAddress.
+// address of the current device's copy comes from cudaGetSymbolAddress.
 // ---------------------------------------------------------------------------
 constexpr size_t kStaticScratchBytes = (size_t)16 << 20;  // 16 MiB on every device
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
-static std::mutex g_static_mutex;
-static void* g_static_ptr[128] = {nullptr};
 
-// Device address of g_static_scratch on the current device (looked up on the
-// first call for that device).
+// Device address of g_static_scratch on the current device.  Looked up on
+// every call (cudaGetSymbolAddress does not allocate and is cheap), so the
+// address stays valid across a cudaDeviceReset or a new primary context.
 static igm_status static_scratch(void** out) {
-  int dev = 0;
-  CU(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 128) return fail(IGM_ERR_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_static_mutex);
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    CU(cudaGetSymbolAddress(&p, g_static_scratch));
-    g_static_ptr[dev] = p;
-  }
-  *out = g_static_ptr[dev];
+  void* p = nullptr;
+  CU(cudaGetSymbolAddress(&p, g_static_scratch));
+  *out = p;
   return IGM_OK;
 }
 
@@ -1863,6 +1871,7 @@ static igm_status run_finish(mgrit_handle* mg, mgrit_stats* stats) {
     stats->coarse_fallback = R.fallback ? 1 : 0;
   }
   if (hstat == ST_NUMERIC) return fail(IGM_ERR_NUMERIC, "NaN in a spatial residual");
+  if (hstat == ST_TIMEOUT) return fail(IGM_ERR_TIMEOUT, "a bounded device wait gave up");
   if (hstat == ST_NOT_CONVERGED) return fail(IGM_ERR_NOT_CONVERGED, "a spatial solve hit max_cycles");
   if (nlev > 1 && !hist.empty() && !(hist.back() <= o.tol * hist[0]) && hist.back() != 0.0)
     return fail(IGM_ERR_NOT_CONVERGED, "MGRIT hit max_iter");

@@ -153,3 +153,108 @@ def test_pmg_annulus_converges():
     x, cyc = P.solve(b, np.zeros(hi.N), tol=1e-12)
     assert np.linalg.norm(b - P.A @ x) <= 1e-12 * np.linalg.norm(b)
     assert cyc <= 10
+
+
+def _bilinear_prolongation_dense(nel_coarse):
+    """Interior p = 1 nodes of nel_coarse elements -> interior nodes of
+    2 nel_coarse elements, by linear interpolation written out from the nodal
+    positions (x_c = c / nel_coarse, x_f = f / (2 nel_coarse)); tensor product
+    in 2D with index ix + n iy."""
+    nc, nf = nel_coarse - 1, 2 * nel_coarse - 1
+    P1 = np.zeros((nf, nc))
+    for f in range(1, nf + 1):            # fine node f at x = f / (2 nel_coarse)
+        for c in range(1, nc + 1):        # coarse hat centred at x = 2c / (2 nel_coarse)
+            d = abs(f - 2 * c)
+            P1[f - 1, c - 1] = max(0.0, 1.0 - d / 2.0)
+    return np.kron(P1, P1)
+
+
+def test_hmg_cycle_is_a_w_cycle_gamma_2():
+    """Fig. 5 (Sec. 4): one W-cycle visits each coarser level twice per visit of
+    the level above.  On a three-level p = 1 hierarchy (32 -> 16 -> 8 elements)
+    the cycle's error propagation operator is composed by hand from dense
+    matrices: Gauss--Seidel S = I - (D + L)^{-1} A, Galerkin coarse operators
+    P^T A P with the interpolation written out above, the exact solve on the
+    coarsest level, and gamma = 2 coarse visits:
+        E_k = S_k (I - P_k (I - E_{k+1}^2) A_{k+1}^{-1} P_k^T A_k) S_k,  E_last = 0.
+    The oracle's cycle applied to x = e_j with b = 0 must reproduce column j.
+    A V-cycle (gamma = 1), a missing smoothing step or a transposed transfer
+    gives a different operator."""
+    fine = assembly.Discretisation(1, 32, geometry.UnitSquare())
+    A0 = (fine.M + 0.02 * fine.K).toarray()
+    P01 = _bilinear_prolongation_dense(16)
+    A1 = P01.T @ A0 @ P01
+    P12 = _bilinear_prolongation_dense(8)
+    A2 = P12.T @ A1 @ P12
+
+    def smoother(A):
+        return np.eye(A.shape[0]) - np.linalg.solve(np.tril(A), A)
+
+    def two_grid(A, P, Ac, Ec):
+        I = np.eye(A.shape[0])
+        Ic = np.eye(Ac.shape[0])
+        S = smoother(A)
+        return S @ (I - P @ (Ic - Ec @ Ec) @ np.linalg.solve(Ac, P.T @ A)) @ S
+
+    E2 = np.zeros_like(A2)
+    E1 = two_grid(A1, P12, A2, E2)
+    E0 = two_grid(A0, P01, A1, E1)
+    h = pmg.HMG(sp.csr_matrix(A0), 32, coarsest_nel=8)
+    assert len(h.A) == 3
+    cols = np.stack([h.cycle(0, np.zeros(A0.shape[0]), e) for e in np.eye(A0.shape[0])], axis=1)
+    np.testing.assert_allclose(cols, E0, atol=1e-12)
+    # the V-cycle operator differs from it by far more than rounding
+    E1v = two_grid(A1, P12, A2, E2)
+    I1 = np.eye(A1.shape[0])
+    S0 = smoother(A0)
+    E0v = S0 @ (np.eye(A0.shape[0]) - P01 @ (I1 - E1v) @ np.linalg.solve(A1, P01.T @ A0)) @ S0
+    assert np.abs(E0v - E0).max() > 1e-4
+
+
+def test_ilut_count_limit_keeps_largest_then_smaller_column():
+    """Sec. 4's ILUT, the count limit (reading: keep the ceil(fill * nnz) largest
+    |values| of each strictly-lower and strictly-upper row part, exact ties
+    going to the smaller column, the diagonal always).  The matrix makes the
+    elimination trivial so that the candidates are known by hand: rows 0..7
+    hold only their diagonal 1, except row 0 whose upper part is
+    (col 3: 2, col 4: -5, col 6: 5, col 7: 2, col 9: -1); row 9 has the lower
+    entries (col 1: 3, col 2: -3, col 4: 1, col 5: -4, col 7: 3) and no upper
+    part, and every other row only its diagonal.  The pivot rows of row 9
+    have no upper entries (and row 0 is not a pivot of row 9), so its
+    candidates are its own entries.  With fill = 0.6 the limits are
+    ceil(0.6 * 5) = 3 in both row parts."""
+    n = 10
+    A = np.eye(n) * 4.0
+    A[0, [3, 4, 6, 7, 9]] = [2.0, -5.0, 5.0, 2.0, -1.0]
+    A[9, [1, 2, 4, 5, 7]] = [3.0, -3.0, 1.0, -4.0, 3.0]
+    L, U = pmg.ilut(sp.csr_matrix(A), droptol=0.0, fill=0.6)
+    # row 0, upper part: |-5| = |5| (cols 4 and 6), then |2| = |2| tie -> col 3
+    u0 = U.getrow(0).toarray().ravel()
+    assert sorted(np.nonzero(u0)[0].tolist()) == [0, 3, 4, 6]
+    assert u0[4] == -5.0 and u0[6] == 5.0 and u0[3] == 2.0 and u0[0] == 4.0
+    # row 9, lower part (pivots are diagonal 4: w_k = a_9k / 4): |-4| (col 5),
+    # then the three-way tie |3| = |-3| = |3| at cols 1, 2, 7 -> cols 1 and 2
+    l9 = L.getrow(9).toarray().ravel()
+    assert sorted(np.nonzero(l9)[0].tolist()) == [1, 2, 5]
+    np.testing.assert_array_equal(l9[[1, 2, 5]], [0.75, -0.75, -1.0])
+    # the diagonal of row 9 stays: 4, no upper entries
+    u9 = U.getrow(9).toarray().ravel()
+    assert np.nonzero(u9)[0].tolist() == [9] and u9[9] == 4.0
+
+
+def test_ilut_on_five_point_laplacian_keeps_the_pattern_of_a():
+    """For the 5-point Laplacian every fill-in of the elimination is smaller in
+    magnitude than the row's original entries, so with fill = 1 the count
+    limit keeps exactly A's pattern in L and U.  (Unlike ILU(0), ILUT uses a
+    fill-in pivot before the count limit drops it, so L U does not reproduce
+    A on its pattern; the exact-LU and count-limit pins above fix the values.)"""
+    A = _grid_laplacian(6).tocsr()
+    L, U = pmg.ilut(A, droptol=0.0, fill=1.0)
+    low = sp.tril(A, -1).tocsr()
+    upp = sp.triu(A, 0).tocsr()
+    for M, F in ((low, L), (upp, U)):
+        M.sort_indices(); F.sort_indices()
+        assert np.array_equal(M.indptr, F.indptr) and np.array_equal(M.indices, F.indices)
+    # and dropping did happen: the factors are not the exact LU
+    LU = ((sp.identity(A.shape[0]) + L) @ U).toarray()
+    assert np.abs(LU - A.toarray()).max() > 1e-3

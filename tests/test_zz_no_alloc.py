@@ -16,6 +16,23 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+def _device_memory():
+    """(free bytes of the device from cudaMemGetInfo, bytes reserved by the
+    device's default stream-ordered memory pool, the one cudaMallocAsync
+    draws on), read through the driver library."""
+    import ctypes
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    cu = ctypes.CDLL("libcuda.so.1")
+    pool = ctypes.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(ctypes.byref(pool), torch.cuda.current_device()) == 0
+    reserved = ctypes.c_uint64()
+    CU_MEMPOOL_ATTR_RESERVED_MEM_CURRENT = 5
+    assert cu.cuMemPoolGetAttribute(pool, CU_MEMPOOL_ATTR_RESERVED_MEM_CURRENT,
+                                    ctypes.byref(reserved)) == 0
+    return free, reserved.value
+
+
 @pytest.mark.parametrize("p,nel,precision", [(5, 64, 0), (3, 16, 1)])
 def test_static_scratch_solve_matches_pmg_vcycle(p, nel, precision):
     import torch
@@ -51,3 +68,23 @@ def test_static_scratch_rejects_oversize():
     _, st = g.solve_static(Bm, X, check=False)
     assert st == -1
     assert "static buffer holds" in B.lib().igm_last_error().decode()
+
+
+def test_static_calls_allocate_no_device_memory():
+    """After a first call (which may load the kernels' code), further calls
+    leave the device's free memory and the default memory pool unchanged:
+    nothing is allocated, neither by cudaMalloc nor by cudaMallocAsync."""
+    import torch
+    from paper_2107_05337_gb300 import binding as B
+    prob = B.Problem(5, 64)   # FP64 working vectors too large for shared memory: the
+    g = B.PMG(prob, 1.0 / 256, precision=0, tol=1e-12)   # static buffer holds them
+    Bm = torch.as_tensor(inputs.random_block(43, prob.N, 4), dtype=torch.float64, device="cuda")
+    X = torch.zeros_like(Bm)
+    g.solve_static(Bm, X, ncycles=1)
+    torch.cuda.synchronize()
+    before = _device_memory()
+    for _ in range(3):
+        X.zero_()
+        g.solve_static(Bm, X)
+    torch.cuda.synchronize()
+    assert _device_memory() == before
