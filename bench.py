@@ -11,9 +11,16 @@ each of the four orders (a unit of work = N_p * N_t DOF*timesteps, summed).
 
 Forms: "chosen" = FP32 smoothing / SpMM / transfers / Gauss--Seidel with FP64
 residual refinement (precision 1), one p-multigrid cycle per coarse-level solve,
-sweep layouts autotuned at setup; "plain" = everything FP64 (precision 0) to
-1e-10 on every level.  The value is the chosen form's throughput; the plain form
-is reported beside it.
+sweep layouts autotuned at setup; "mixed_only" = the same precision split with
+every level solved to 1e-10; "plain" = everything FP64 (precision 0) to 1e-10
+on every level.  The value is the chosen form's throughput; the other two are
+reported beside it, so that the speed-up over the plain form splits into its
+precision and coarse-propagator parts.  Every form's iterate of the last timed
+step is compared with the oracle's sequential backward Euler (the fixed point of
+MGRIT, Sec. 3) per order ("error_vs_oracle").  The default run also measures the
+curved-map workload annulus_c3 ("annulus_c3", with its own roofline and error)
+and the CPU baseline: the oracle on a bounded sample of heat_c2, on one core
+and as independent replicas on every host core.
 
 Other modes (one JSON line each): --annulus (the curved-map workload annulus_c3),
 --batch (the uneven 64-problem batch, latency percentiles), --learned (two-level
@@ -50,7 +57,10 @@ def parse():
     ap.add_argument("--Nt", type=int, default=256)
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-check", action="store_true")
-    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true",
+                    help="skip the CPU baseline leg (oracle timings and the errors against it)")
+    ap.add_argument("--skip-annulus", action="store_true",
+                    help="skip the annulus_c3 sub-measurement of the default run")
     ap.add_argument("--sjf", type=int, default=1,
                     help="--batch: 1 = shortest-job-first stream priorities (default), 0 = equal")
     ap.add_argument("--learned", action="store_true",
@@ -77,11 +87,11 @@ def manufactured():
     return S, C
 
 
-# DRAM bytes per V-cycle and unknown measured by ncu on k_mgrit_sweep (p = 4,
-# 64 x 64 elements, chosen form with autotuned layouts, fine-level relaxation
-# launch; profiles/k_mgrit_sweep_heat_c2_p4_wavefront.md); re-measure whenever
-# the kernel changes.
-DRAM_BYTES_PER_VCYCLE_DOF = 24.8
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
+# dominant kernel, averaged over the launches of one chosen-form solve of the
+# workload at its full size, from one ncu capture of that solve (the launch
+# list's metric pass); None until captured on the current kernel.
+NCU_DRAM_BYTES_PER_LAUNCH = {"heat_c2": None, "annulus_c3": None}
 
 
 def bytes_per_vcycle_dof(p, B):
@@ -162,12 +172,42 @@ def measured_peaks():
         return None
 
 
-def oracle_sample(reps=1, p=2, nel=64, Nt=64):
-    """The oracle (CPU, FP64, as it stands) on a bounded sample of the workload:
-    order p, nel x nel elements, N_t steps (levels N_t -> ... <= 4), MGRIT with
-    p-multigrid spatial solves to the workload's tolerances.  Setup (assembly,
-    Python ILUT) is excluded from the timing.  Returns (DOF*ts/s, seconds, desc)."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
+# ---------------------------------------------------------------------------
+# CPU baseline leg: the only part of this file that runs the oracle.  The
+# oracle runs in processes started with "spawn" (never forked from a process
+# that has used the GPU), one solve per process, BLAS threads pinned to 1.
+# ---------------------------------------------------------------------------
+SAMPLE = dict(p=2, nel=64, Nt=32)   # bounded sample of heat_c2 for the CPU legs
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the ISA)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def _single_thread_env():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_replica(p, nel, Nt, cmd, res):
+    """Worker: build the oracle's MGRIT with p-multigrid spatial solves for the
+    sample (setup: assembly and ILUT per time level), then one timed solve to
+    MGRIT tolerance 1e-10 per command received; None ends it."""
     import numpy as np
     from oracle import assembly, geometry, mgrit
     S, C = manufactured()
@@ -176,32 +216,133 @@ def oracle_sample(reps=1, p=2, nel=64, Nt=64):
     fac = mgrit.pmg_factory(hi, lo, tol=1e-10)
     cache = {}
     mk = lambda l, c: cache.setdefault(l, fac(l, c))
-    times = []
-    for _ in range(reps):
+    mgrit.MGRIT(hi.M, hi.K, 1.0, 1.0, Nt, 4, mk, u0, fhat, C)   # builds every level's solver
+    res.put(("ready", hi.N))
+    while cmd.get() is not None:
         mg = mgrit.MGRIT(hi.M, hi.K, 1.0, 1.0, Nt, 4, mk, u0, fhat, C)
         t0 = time.perf_counter()
-        mg.run(tol=1e-10)
-        times.append(time.perf_counter() - t0)
-    desc = (f"oracle MGRIT (NumPy/SciPy FP64, p-multigrid spatial solves) on p={p}, "
-            f"{nel}x{nel} elements, N_t={Nt} (levels {mgrit.level_sizes(Nt, 4)}), tol 1e-10; "
-            f"setup excluded; 1 thread")
-    return hi.N * Nt, times, desc
+        _, it, _ = mg.run(tol=1e-10)
+        res.put(("done", time.perf_counter() - t0, it))
+
+
+class OracleReplicas:
+    """`cores` independent replicas of the oracle sample, one spawned process
+    each (weak scaling over host cores, like the GPU replicas of --gpus N)."""
+
+    def __init__(self, cores, p=SAMPLE["p"], nel=SAMPLE["nel"], Nt=SAMPLE["Nt"]):
+        import multiprocessing as mp
+        _single_thread_env()
+        ctx = mp.get_context("spawn")
+        self.cores, self.p, self.nel, self.Nt = cores, p, nel, Nt
+        self.res = ctx.Queue()
+        self.cmds = [ctx.Queue() for _ in range(cores)]
+        self.procs = [ctx.Process(target=_oracle_replica, args=(p, nel, Nt, q, self.res), daemon=True)
+                      for q in self.cmds]
+        for pr in self.procs:
+            pr.start()
+        self.N = None
+        for _ in range(cores):
+            tag, N = self.res.get(timeout=1800)
+            assert tag == "ready"
+            self.N = N
+
+    def step(self):
+        """Wall seconds for every replica to finish one solve (the units of
+        work are cores * N * N_t)."""
+        t0 = time.perf_counter()
+        for q in self.cmds:
+            q.put(1)
+        its = [self.res.get(timeout=1800)[2] for _ in range(self.cores)]
+        return time.perf_counter() - t0, its
+
+    def desc(self):
+        from oracle import mgrit
+        return (f"oracle MGRIT (NumPy/SciPy FP64, p-multigrid spatial solves) on p={self.p}, "
+                f"{self.nel}x{self.nel} elements, N_t={self.Nt} (levels "
+                f"{mgrit.level_sizes(self.Nt, 4)}), tol 1e-10; {self.cores} independent "
+                f"replica(s), one spawned process per core, BLAS threads 1; setup excluded; "
+                f"CPU: {cpu_model()}")
+
+    def close(self):
+        for q in self.cmds:
+            q.put(None)
+        for pr in self.procs:
+            pr.join(timeout=30)
+
+
+def cpu_baseline_leg():
+    """The oracle on one core and on all host cores (same bounded sample)."""
+    cores = os.cpu_count() or 1
+    one = OracleReplicas(1)
+    t1, _ = one.step()
+    one.close()
+    allc = OracleReplicas(cores)
+    ta, _ = allc.step()
+    desc = allc.desc()
+    units = allc.N * allc.Nt
+    allc.close()
+    return {"value": cores * units / ta, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": desc, "cpu": cpu_model(),
+            "single_thread": {"value": units / t1, "cores": 1, "seconds": round(t1, 3)}}
+
+
+def _oracle_sequential(job):
+    """Sequential backward Euler with sparse direct spatial solves (the result
+    MGRIT converges to, Sec. 3) for one benchmarked problem."""
+    _single_thread_env()
+    import numpy as np
+    from oracle import assembly, geometry, timestep
+    from paper_2107_05337_gb300 import inputs
+    S, C = manufactured()
+    if job[0] == "heat_c2":
+        _, p, nel, Nt = job
+        d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+        return timestep.sequential(d.M, d.K, 1.0, 1.0, Nt, d.project(S), d.load_vector(S), C)
+    w = inputs.WORKLOADS["annulus_c3"]
+    k, l, a = inputs.fourier_modes()
+    u0fn = lambda xi, eta, x, y: sum(a[s] * np.sin(k[s] * np.pi * xi) * np.sin(l[s] * np.pi * eta)
+                                     for s in range(len(a)))
+    d = assembly.Discretisation(w["p"][0], w["nel"], geometry.get(w["geom"]))
+    return timestep.sequential(d.M, d.K, 1.0, w["T"], w["Nt"], d.project(u0fn))
+
+
+def oracle_references(jobs):
+    """Start the oracle's sequential solutions of the benchmarked problems in
+    spawned processes (they run while the GPU is timed and are collected
+    afterwards; nothing of them is timed).  Returns {job: future}."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    _single_thread_env()
+    ex = ProcessPoolExecutor(max_workers=len(jobs), mp_context=mp.get_context("spawn"))
+    return ex, {job: ex.submit(_oracle_sequential, job) for job in jobs}
+
+
+def rel_err(U, ref):
+    import numpy as np
+    return float(np.linalg.norm(U - ref) / np.linalg.norm(ref))
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    # each step = one oracle MGRIT solve of the bounded sample
-    n_units, times, desc = oracle_sample(reps=args.warmup + args.steps, Nt=32)
-    t = sum(times[args.warmup:])
-    v = n_units * args.steps / t
+    # each step = every host core solving the bounded sample once (independent replicas)
+    cores = os.cpu_count() or 1
+    reps = OracleReplicas(cores)
+    for _ in range(args.warmup):
+        reps.step()
+    t = sum(reps.step()[0] for _ in range(args.steps))
+    units = reps.N * reps.Nt * cores
+    desc = reps.desc()
+    reps.close()
+    v = units * args.steps / t
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "heat_c2 bounded sample (p=2, N_t=32)", "nel": 64},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+            "config": {"workload": f"heat_c2 bounded sample (p={SAMPLE['p']}, nel={SAMPLE['nel']}, "
+                                   f"N_t={SAMPLE['Nt']}), {cores} replicas"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -373,21 +514,21 @@ def run_learned(args):
     print(json.dumps(line))
 
 
-def run_annulus(args):
+def annulus_measure(steps, warmup, profile_only=False):
     """annulus_c3: quarter annulus (cubic Bezier arc x radial line), p = 4, 128 x 128
     elements (N = 16900), kappa = 1, T = 1, N_t = 1024, m = 8 (1024 -> 128 -> 16 -> 2),
     f = 0, 8-mode Fourier initial condition (seed 20210712).  Chosen form (FP32
     p-multigrid cycles with FP64 refinement, one cycle per coarse-level solve,
     autotuned sweep layouts) to MGRIT relative residual 1e-10: DOF*timesteps/s over
-    --steps solves after --warmup, and the V-cycle-model GB/s of k_mgrit_sweep from a
+    `steps` solves after `warmup`, and the V-cycle-model GB/s of k_mgrit_sweep from a
     per-launch profiled solve, against the measured HBM bandwidth.  The fine-level
-    iterate is 139 MB (above L2).  --profile-only prints each launch's grid and
-    V-cycles (to pair with ncu's per-launch DRAM counters)."""
+    iterate is 139 MB (above L2).  Returns (result dict, final iterate on the host);
+    profile_only prints each launch's grid and V-cycles (to pair with ncu's
+    per-launch DRAM counters) and returns (None, None)."""
     import numpy as np
     import torch
     from paper_2107_05337_gb300 import binding as B
     from paper_2107_05337_gb300 import inputs
-    torch.cuda.set_device(0)
     w = inputs.WORKLOADS["annulus_c3"]
     p, nel, T, Nt, m = w["p"][0], w["nel"], w["T"], w["Nt"], w["m"]
     k, l, a = inputs.fourier_modes()
@@ -400,7 +541,7 @@ def run_annulus(args):
                 tol=1e-10, max_iter=100, coarse_cycles=1)
     pmg = dict(precision=1, tol=1e-10, autotune=1)
     h = B.MGRIT(prob, **opts, pmg=pmg)
-    if args.profile_only:
+    if profile_only:
         h.run(u0, None, None, U)
         torch.cuda.synchronize()
         hp = B.MGRIT(prob, **opts, pmg=pmg, profile=1, graphs=0)
@@ -408,14 +549,17 @@ def run_annulus(args):
         pr = hp.profile()
         print(json.dumps({"order": p, "N": int(prob.N), "grid": [int(g) for g in pr["grid"]],
                           "cycles": [int(c) for c in pr["cycles"]]}))
-        return
+        return None, None
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    for _ in range(warmup):
         h.run(u0, None, None, U)
     torch.cuda.synchronize()
     ms, st = [], None
     with Clocks(0) as ck:
-        for _ in range(args.steps):
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
@@ -423,6 +567,7 @@ def run_annulus(args):
             e1.record(stream)
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+    Uh = U.cpu().numpy()
     hp = B.MGRIT(prob, **opts, pmg=pmg, profile=1, graphs=0)
     hp.run(u0, None, None, U)
     pr = hp.profile()
@@ -431,17 +576,32 @@ def run_annulus(args):
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
     achieved = byts / (tot_ms * 1e-3) / 1e9
-    print(json.dumps({"workload": "annulus_c3", "metric": "DOF*timesteps/s to MGRIT rel. residual 1e-10",
-                      "value": prob.N * Nt * len(ms) / (sum(ms) * 1e-3), "unit": UNIT,
-                      "ms_per_solve": round(sum(ms) / len(ms), 2), "steps": len(ms),
-                      "warmup": args.warmup, "iters": st["iters"], "levels": st["levels"],
-                      "vcyc_mean": round(st["vcyc_mean"], 3),
-                      "roofline": {"kernel": "k_mgrit_sweep", "bound": "hbm", "achieved": round(achieved, 2),
-                                   "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
-                                   "launches_profiled": len(pr["ms"]),
-                                   "mean_launch_ms": round(tot_ms / len(pr["ms"]), 3),
-                                   "peak_source": "measured" if peaks else "fallback"},
-                      "clocks": ck.summary()}))
+    dram = NCU_DRAM_BYTES_PER_LAUNCH["annulus_c3"]
+    return ({"workload": "annulus_c3: quarter annulus, p=4, nel=128 (N=16900), N_t=1024, T=1, "
+                         "m=8 multilevel FCF MGRIT, f=0, 8-mode initial condition",
+             "form": "chosen (FP32 p-MG cycles with FP64 refinement, one cycle per coarse-level "
+                     "solve, autotuned sweep layouts)",
+             "metric": "DOF*timesteps/s to MGRIT rel. residual 1e-10",
+             "value": prob.N * Nt * len(ms) / (sum(ms) * 1e-3), "unit": UNIT,
+             "ms_per_solve": round(sum(ms) / len(ms), 2), "steps": len(ms),
+             "warmup": warmup, "iters": st["iters"], "levels": st["levels"],
+             "vcyc_mean": round(st["vcyc_mean"], 3),
+             "l2": "flushed (256 MiB write) before every timed solve",
+             "roofline": {"kernel": "k_mgrit_sweep", "bound": "hbm", "achieved": round(achieved, 2),
+                          "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 5),
+                          "traffic": dram,
+                          "launches_profiled": len(pr["ms"]),
+                          "mean_launch_ms": round(tot_ms / len(pr["ms"]), 3),
+                          "peak_source": "measured" if peaks else "fallback"},
+             "clocks": ck.summary()}, Uh)
+
+
+def run_annulus(args):
+    import torch
+    torch.cuda.set_device(0)
+    res, _ = annulus_measure(args.steps, args.warmup, args.profile_only)
+    if res is not None:
+        print(json.dumps(res))
 
 
 def run_spmm(args):
@@ -493,19 +653,28 @@ def main():
         return run_learned(args)
     if args.batch:
         return run_batch(args)
-    import numpy as np
-    import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    orders = [int(x) for x in args.orders.split(",")]
+    T, Nt, nel = 1.0, args.Nt, args.nel
+    # the oracle's sequential solutions of every benchmarked problem, for the
+    # errors of the GPU results (CPU baseline leg; spawned before any GPU use,
+    # collected after the timed regions)
+    refs_ex, refs = None, {}
+    if not args.skip_cpu and rank == 0 and not args.profile_only:
+        jobs = [("heat_c2", p, nel, Nt) for p in orders]
+        if not args.skip_annulus:
+            jobs.append(("annulus_c3",))
+        refs_ex, refs = oracle_references(jobs)
+    import numpy as np
+    import torch
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2107_05337_gb300 import binding as B
     S, C = manufactured()
-    orders = [int(x) for x in args.orders.split(",")]
-    T, Nt, nel = 1.0, args.Nt, args.nel
     fcoef = np.array([C(n * T / Nt) for n in range(Nt + 1)])
     probs, u0s, fhats, Us = {}, {}, {}, {}
     for p in orders:
@@ -514,17 +683,14 @@ def main():
         fhats[p] = probs[p].load_vector(S)
         Us[p] = torch.empty((Nt + 1, probs[p].N), dtype=torch.float64, device="cuda")
     opts = dict(T=T, Nt=Nt, m=4, max_levels=30, min_coarse=4, relax=1, tol=1e-10, max_iter=100)
+    CHOSEN = dict(coarse_cycles=1, pmg=dict(precision=1, tol=1e-10, autotune=1))
     t_setup = time.perf_counter()
     # chosen form: FP32 p-multigrid cycles with FP64 refinement, and one cycle per
     # spatial solve on the coarse time levels (inexact coarse propagator)
-    chosen = {p: B.MGRIT(probs[p], **opts, coarse_cycles=1,
-                         pmg=dict(precision=1, tol=1e-10, autotune=1))
-              for p in orders}
+    chosen = {p: B.MGRIT(probs[p], **opts, **CHOSEN) for p in orders}
     setup_s = time.perf_counter() - t_setup
     units = sum(probs[p].N * Nt for p in orders)
     stream = torch.cuda.current_stream()
-
-    import threading
 
     def step(handles, stats=None, concurrent=True):
         """One MGRIT solve per order.  The orders are independent problems: each
@@ -554,8 +720,7 @@ def main():
         # per-launch V-cycle counts of the same solves (same order of launches),
         # to relate a captured launch's DRAM counters to its units of work
         for p in orders:
-            hp = B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10, autotune=1), profile=1,
-                         graphs=0)
+            hp = B.MGRIT(probs[p], **opts, **CHOSEN, profile=1, graphs=0)
             hp.run(u0s[p], fhats[p], fcoef, Us[p])
             pr = hp.profile()
             print(json.dumps({"order": p, "N": int(probs[p].N), "grid": [int(g) for g in pr["grid"]],
@@ -586,21 +751,31 @@ def main():
                 ms.append(e0.elapsed_time(e1))
         launches = B.kernel_launches() - l0
         total = job_time_ms(sum(ms), world, "cuda")
-        return total, ms, stats, ck.summary(), launches
+        host = {p: Us[p].cpu().numpy() for p in orders}   # the last step's iterates
+        return total, ms, stats, ck.summary(), launches, host
 
-    total, ms, stats, clocks, launches = timed(chosen, args.steps, args.warmup)
+    total, ms, stats, clocks, launches, U_chosen = timed(chosen, args.steps, args.warmup)
     value = job_throughput(units, world, args.steps, total)
 
-    # plain FP64 form, same workload
-    plain = None
+    def side_form(handles, name):
+        k = max(1, min(args.steps, 2))
+        tot, _, st, _, _, host = timed(handles, k, 1)
+        return ({"value": world * units * k / (tot * 1e-3), "ms_per_step": tot / k,
+                 "iters": {p: st[p]["iters"] for p in orders},
+                 "vcyc_mean": {p: round(st[p]["vcyc_mean"], 3) for p in orders}}, host)
+
+    # the mixed-precision form alone (every level solved to 1e-10): splits the
+    # chosen form's speed-up over the plain form into its two parts
+    mixed, U_mixed = None, None
+    plain, U_plain = None, None
     if not args.skip_plain:
-        plain_h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=0, tol=1e-10)) for p in orders}
-        ptot, pms, pstats, _, _ = timed(plain_h, max(1, min(args.steps, 2)), 1)
-        pk = max(1, min(args.steps, 2))
-        plain = {"value": world * units * pk / (ptot * 1e-3), "ms_per_step": ptot / pk,
-                 "iters": {p: pstats[p]["iters"] for p in orders},
-                 "vcyc_mean": {p: round(pstats[p]["vcyc_mean"], 3) for p in orders}}
-        del plain_h
+        h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=1, tol=1e-10, autotune=1))
+             for p in orders}
+        mixed, U_mixed = side_form(h, "mixed")
+        del h
+        h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=0, tol=1e-10)) for p in orders}
+        plain, U_plain = side_form(h, "plain")
+        del h
 
     # end to end through the C ABI with host buffers: H2D of u0, fhat (pinned),
     # solve, D2H of the final time level, every step
@@ -610,6 +785,7 @@ def main():
     du0 = {p: torch.empty_like(u0s[p]) for p in orders}
     dfh = {p: torch.empty_like(fhats[p]) for p in orders}
     e2e_ms = []
+
     def e2e_one(p):
         s = torch.cuda.Stream()
         with torch.cuda.stream(s):
@@ -639,15 +815,13 @@ def main():
 
     # roofline of the dominant kernel (k_mgrit_sweep), one profiled solve per order
     roof = None
-    prof_tot_ms, prof_bytes, prof_launches, prof_units = 0.0, 0.0, 0, 0
+    prof_tot_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
     for p in orders:
-        hp = B.MGRIT(probs[p], **opts, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10, autotune=1), profile=1,
-                     graphs=0)
+        hp = B.MGRIT(probs[p], **opts, **CHOSEN, profile=1, graphs=0)
         hp.run(u0s[p], fhats[p], fcoef, Us[p])
         pr = hp.profile()
         for g, c, t in zip(pr["grid"], pr["cycles"], pr["ms"]):
             prof_bytes += c * probs[p].N * bytes_per_vcycle_dof(p, g)
-            prof_units += c * probs[p].N
             prof_tot_ms += t
             prof_launches += 1
         del hp
@@ -657,14 +831,12 @@ def main():
         peak = peaks["hbm_gbs"] if peaks else 6800.0
         roof = {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 5),
-                "traffic": round(DRAM_BYTES_PER_VCYCLE_DOF * prof_units / prof_launches),
+                "traffic": NCU_DRAM_BYTES_PER_LAUNCH["heat_c2"],
                 "kernel": "k_mgrit_sweep", "launches_profiled": prof_launches,
                 "mean_launch_ms": round(prof_tot_ms / prof_launches, 4),
                 "peak_source": "measured" if peaks else "fallback"}
 
-    # the orders one after another (no overlap), for reference.  (The error of
-    # every order against the oracle's sequential stepping at this size is a
-    # test: tests/test_gpu_fullsize.py.)
+    # the orders one after another (no overlap), for reference
     serial_ms = None
     if not args.skip_check and rank == 0:
         torch.cuda.synchronize()
@@ -676,11 +848,24 @@ def main():
         torch.cuda.synchronize()
         serial_ms = e0.elapsed_time(e1)
 
-    cpu = None
-    if not args.skip_cpu and rank == 0:
-        n_units, times, desc = oracle_sample(reps=1)
-        cpu = {"value": n_units / times[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": desc}
+    # the curved-map workload, where the iterate exceeds L2
+    annulus, U_annulus = None, None
+    if not args.skip_annulus and rank == 0:
+        annulus, U_annulus = annulus_measure(2, 1)
+
+    cpu, errors = None, None
+    if refs:
+        # errors against the oracle's sequential backward Euler (Sec. 3: the
+        # fixed point of MGRIT), every timed form and order
+        seq = {job: f.result() for job, f in refs.items()}
+        refs_ex.shutdown()
+        errors = {}
+        for name, Uf in (("chosen", U_chosen), ("mixed", U_mixed), ("plain_fp64", U_plain)):
+            if Uf is not None:
+                errors[name] = {p: rel_err(Uf[p], seq[("heat_c2", p, nel, Nt)]) for p in orders}
+        if annulus is not None:
+            annulus["error_vs_oracle"] = rel_err(U_annulus, seq[("annulus_c3",)])
+        cpu = cpu_baseline_leg()
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -692,17 +877,24 @@ def main():
                            "chosen_form": "FP32 p-MG cycles with FP64 refinement; one p-MG cycle "
                                           "per coarse-time-level solve (fine level to 1e-10); "
                                           "sweep layouts autotuned at setup",
+                           "mixed_form": "FP32 p-MG cycles with FP64 refinement, every level to 1e-10",
                            "plain_form": "FP64 p-MG on every level to 1e-10",
                            "orders": "solved concurrently, one stream each",
                            "parallelism": f"replicas{world}" if world > 1 else "single GPU",
                            "l2": "flushed (256 MiB write) before every timed step"},
+                "mixed_only": mixed,
                 "plain_fp64": plain,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
+                "speedup_parts": ({"mixed_precision": mixed["value"] / plain["value"],
+                                   "one_cycle_coarse_levels": value / mixed["value"]}
+                                  if plain and mixed else None),
                 "iters": {p: stats[p]["iters"] for p in orders},
                 "vcyc_mean": {p: round(stats[p]["vcyc_mean"], 3) for p in orders},
+                "error_vs_oracle": errors,
                 "setup_s": round(setup_s, 3),
                 "orders_one_after_another_ms": serial_ms,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
+                "annulus_c3": annulus,
                 "clocks": clocks}
         print(json.dumps(line))
     if world > 1:
