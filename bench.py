@@ -457,7 +457,7 @@ def run_learned(args):
     U0, U1 = torch.cat(U0s), torch.cat(U1s)
     npairs = int(U0.shape[0])
     gen_s = time.perf_counter() - t0
-    phic = B.Phic(prob.n, 8, seed=w["seed"])
+    phic = B.Phic(prob.n, 32, seed=w["seed"])
     t0 = time.perf_counter()
     steps = 3000
     loss = phic.train(U0, U1, steps=steps, batch=32, lr=2e-3, seed=1)

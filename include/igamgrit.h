@@ -352,6 +352,11 @@ typedef struct {
                         fine level (default); k > 0 = exactly k p-multigrid cycles (an
                         inexact coarse propagator; the fine level, and with it the
                         converged answer, is unchanged) */
+  int fused;       /* 1 (default): with FCF relaxation, the relaxation phases of one visit
+                      of a level (F, C, F + C-point residual) run as one cooperative launch
+                      of one CTA per interval with a bounded grid-wide barrier between the
+                      phases, when all the level's CTAs can be resident at once (else, and
+                      with 0, one launch per phase); results are identical either way */
 } mgrit_opts;
 
 typedef struct {
@@ -412,17 +417,22 @@ igm_status mgrit_run_batched(int nprob, mgrit_handle* const* mgs, const double* 
 /* ---------------------------------------------------------------------------
  * Learned coarse propagator Phi_c (no counterpart in the paper, whose coarse
  * levels rediscretise the time step, Sec. 3).  A convolutional network on the
- * n x n grid of interior coefficients (zero padding: the homogeneous Dirichlet
- * condition), BF16 weights and activations with FP32 accumulation:
- *   x = u / s, s = max |u|;  Phi_c(u) = u + s * K3 * tanh(K2 * tanh(K1 * x)),
- * K1: 1 -> C, K2: C -> C, K3: C -> 1 channels, 5 x 5 kernels, no biases.
- * Weights (FP32 master copy) in one array [K1 (C,1,5,5) | K2 (C,C,5,5) |
- * K3 (1,C,5,5)] of count = 25 (2C + C^2) floats.
+ * n x n grid of interior coefficients (zero padding: the homogeneous
+ * Dirichlet condition), BF16 weights and activations with FP32 accumulation
+ * (the C -> C layers, their input gradients and weight gradients on the
+ * tensor cores):
+ *   x = u / s, s = max |u|;  h1 = g(K1 * x), h2 = g(K2 * h1), h3 = g(K3 * h2),
+ *   Phi_c(u) = u + s * K4 * h3,  g(z) = z (1 + erf(z / sqrt 2)) / 2 (GELU),
+ * K1: 1 -> C, K2, K3: C -> C, K4: C -> 1 channels, 3 x 3 kernels, no biases.
+ * Weights (FP32 master copy) in one array [K1 (C,1,3,3) | K2 (C,C,3,3) |
+ * K3 (C,C,3,3) | K4 (1,C,3,3)] of count = 9 (2C + 2C^2) floats, the last two
+ * indices the kernel row (eta) and column (xi).
  * ------------------------------------------------------------------------ */
 typedef struct phic_handle phic_handle;
 
-/* n = interior coefficients per direction, channels C in [1, 8]; K1 and K2
- * random (seeded), K3 = 0 (the network starts as the identity). */
+/* n = interior coefficients per direction, channels C = 32 (16 for small
+ * tests); K1, K2, K3 random (seeded), K4 = 0 (the network starts as the
+ * identity). */
 igm_status phic_create(int n, int channels, unsigned long long seed, phic_handle** out);
 void phic_destroy(phic_handle* h);
 /* HOST w[count]; phic_get_weights also returns count (w may be NULL). */
@@ -439,6 +449,14 @@ igm_status phic_apply(phic_handle* h, int nb, const double* u, long ldu, double*
 igm_status phic_train(phic_handle* h, int npairs, const double* U0, const double* U1, long ld,
                       int steps, int batch, double lr, unsigned long long seed, double* loss,
                       igm_stream s);
+/* The loss of phic_train on the nb pairs (U0 row b -> U1 row b, DEVICE, stride
+ * ld, normalised by max |U0_b|) as one minibatch, and its gradient by back
+ * propagation with the current weights: HOST *loss, gw[count] (the weight
+ * gradient, master layout), gx[nb][n*n] (the gradient with respect to the
+ * normalised inputs U0_b / s_b; may be NULL).  No weight update.
+ * Synchronises the stream. */
+igm_status phic_grad(phic_handle* h, int nb, const double* U0, const double* U1, long ld,
+                     double* loss, float* gw, float* gx, igm_stream s);
 /* Use h (NULL: backward Euler again) as the coarse propagator of a two-level
  * MGRIT handle (max_levels = 2), with the FAS coarse equation
  * tau_j = u_{jm} - Phi_c(u_{(j-1)m}) + r_j, v_j = Phi_c(v_{j-1}) + tau_j.  The
@@ -469,6 +487,15 @@ igm_status mgrit_profile(const mgrit_handle* mg, int cap, int* count, int* level
  * returns, and the call returns IGM_ERR_TIMEOUT with the device still usable.
  * Returns IGM_OK only if the wait completed, which would be a fault. */
 igm_status igm_wait_selftest(long spins, igm_stream s);
+
+/* Failure-detection self-test of the grid-wide barrier that separates the
+ * phases of a fused level visit (mgrit_opts.fused): nctas CTAs in one
+ * cooperative launch pass two barriers.  hold = 0: returns IGM_OK.  hold = 1:
+ * CTA 0 does not arrive at the first barrier, so every CTA's bounded wait runs
+ * out after wait_cycles SM clocks; the kernel records the timeout and returns,
+ * and the call returns IGM_ERR_TIMEOUT with the device still usable.
+ * IGM_ERR_ARG for nctas outside [1, 1024] or wait_cycles < 1. */
+igm_status igm_grid_barrier_selftest(int nctas, long long wait_cycles, int hold, igm_stream s);
 
 /* Thread-local text of the last error (empty string if none). */
 const char* igm_last_error(void);

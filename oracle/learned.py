@@ -3,9 +3,15 @@ it, plain FP64 (numpy).
 
 Test infrastructure (see ``oracle/__init__``).  Pinned by
 ``tests/test_oracle_learned.py``:
-  * the back-propagated gradient equals central finite differences of the loss;
-  * Phi_c(0) = 0 and Phi_c(a u) = a Phi_c(u) (the input is normalised by its
-    maximum modulus); with the last layer zero Phi_c is the identity;
+  * the back-propagated gradients (weights and network input) equal central
+    finite differences of the loss;
+  * GELU and its derivative against the closed form at known points and
+    against finite differences;
+  * Phi_c(0) = 0 and Phi_c(a u) = a Phi_c(u) for a > 0 (the input is
+    normalised by its maximum modulus); with the last layer zero Phi_c is the
+    identity;
+  * a network whose kernels are all the centre tap reduces to a pointwise
+    composition of GELUs (checked against the scalar formula);
   * FAS two-level MGRIT with Phi_c = the backward-Euler coarse propagator
     reproduces the correction-scheme two-level iterates (the coarse equations
     coincide for a linear Phi_c);
@@ -19,11 +25,13 @@ Test infrastructure (see ``oracle/__init__``).  Pinned by
 The network (reading; the paper uses only the rediscretised coarse step): on
 the n x n grid of interior coefficients (zero padding = the homogeneous
 Dirichlet condition), x = u / s with s = max |u|,
-    Phi_c(u) = s (x + K3 * tanh(K2 * tanh(K1 * x))),
-with 5 x 5 convolutions K1 (1 -> C), K2 (C -> C), K3 (C -> 1), no biases
-(so Phi_c(0) = 0 and Phi_c is positively homogeneous).  Trained on pairs
-(u_n, u_{n+m}) of the fine stepper by the mean squared error of
-Phi_c(u_n)/s - u_{n+m}/s, Adam.
+    h1 = g(K1 * x),  h2 = g(K2 * h1),  h3 = g(K3 * h2),
+    Phi_c(u) = s (x + K4 * h3),
+four 3 x 3 convolutions K1 (1 -> C), K2, K3 (C -> C), K4 (C -> 1) with C = 32
+channels, no biases (so Phi_c(0) = 0 and Phi_c is positively homogeneous), and
+the GELU g(z) = z Phi(z) = z (1 + erf(z / sqrt 2)) / 2 (Phi the standard
+normal distribution function).  Trained on pairs (u_n, u_{n+m}) of the fine
+stepper by the mean squared error of Phi_c(u_n)/s - u_{n+m}/s, Adam.
 
 FAS two-level cycle (two levels, m fine steps per coarse step, coarse unknowns
 v_j at the C-points t_{jm}): after FCF relaxation of the fine level, with the
@@ -36,14 +44,29 @@ more than the switch ratio (0.5), the iterate before the correction is
 restored and relaxed again, and the backward-Euler coarse propagator is used
 from then on.
 """
-import numpy as np
+import math
 
-KS = 5  # kernel size
+import numpy as np
+from scipy.special import erf
+
+KS = 3  # kernel size
+LAYERS = 4
+
+
+def gelu(z):
+    """z Phi(z) with Phi(z) = (1 + erf(z / sqrt 2)) / 2."""
+    return 0.5 * z * (1.0 + erf(z / math.sqrt(2.0)))
+
+
+def gelu_deriv(z):
+    """d/dz [z Phi(z)] = Phi(z) + z phi(z), phi the standard normal density."""
+    return 0.5 * (1.0 + erf(z / math.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / math.sqrt(2.0 * math.pi)
 
 
 def conv2d(x, w):
     """'Same' convolution with zero padding: x [Cin, n, n], w [Cout, Cin, KS, KS]
-    -> [Cout, n, n]; out[o,i,j] = sum_{c,a,b} w[o,c,a,b] x[c, i+a-2, j+b-2]."""
+    -> [Cout, n, n]; out[o,i,j] = sum_{c,a,b} w[o,c,a,b] x[c, i+a-h, j+b-h],
+    h = KS // 2."""
     cin, n, _ = x.shape
     h = KS // 2
     xp = np.zeros((cin, n + 2 * h, n + 2 * h))
@@ -71,24 +94,28 @@ def conv2d_grads(x, w, gout):
 
 
 class ConvNet:
-    def __init__(self, n, channels=8, seed=0, zero_last=True):
+    def __init__(self, n, channels=32, seed=0, zero_last=True):
         rng = np.random.default_rng(seed)
         c = channels
         self.n = n
-        self.W = [rng.standard_normal((c, 1, KS, KS)) / (KS * 1.0),
+        self.C = c
+        self.W = [rng.standard_normal((c, 1, KS, KS)) / KS,
+                  rng.standard_normal((c, c, KS, KS)) / (KS * np.sqrt(c)),
                   rng.standard_normal((c, c, KS, KS)) / (KS * np.sqrt(c)),
                   np.zeros((1, c, KS, KS)) if zero_last else
                   rng.standard_normal((1, c, KS, KS)) / (KS * np.sqrt(c))]
 
     def forward_normalised(self, x, keep=False):
         """x [n, n] (already normalised) -> network output [n, n]."""
-        a0 = x[None]
-        z1 = conv2d(a0, self.W[0]); a1 = np.tanh(z1)
-        z2 = conv2d(a1, self.W[1]); a2 = np.tanh(z2)
-        z3 = conv2d(a2, self.W[2])
-        y = x + z3[0]
+        a = [x[None]]
+        zs = []
+        for k in range(LAYERS - 1):
+            z = conv2d(a[-1], self.W[k])
+            zs.append(z)
+            a.append(gelu(z))
+        y = x + conv2d(a[-1], self.W[LAYERS - 1])[0]
         if keep:
-            return y, (a0, a1, a2)
+            return y, (a, zs)
         return y
 
     def __call__(self, u):
@@ -99,24 +126,29 @@ class ConvNet:
         x = (u / s).reshape(self.n, self.n)
         return s * self.forward_normalised(x).ravel()
 
-    def loss_and_grads(self, X, Y):
+    def loss_and_grads(self, X, Y, input_grad=False):
         """Mean squared error over a batch of normalised pairs X, Y [B, n, n] and
-        its gradient with respect to the three kernels."""
+        its gradient with respect to the four kernels (and, with input_grad,
+        with respect to every input X_b, as [B, n, n])."""
         G = [np.zeros_like(w) for w in self.W]
+        GX = np.zeros_like(X)
         loss = 0.0
         B = X.shape[0]
         npix = self.n * self.n
-        for x, yt in zip(X, Y):
-            y, (a0, a1, a2) = self.forward_normalised(x, keep=True)
+        for b, (x, yt) in enumerate(zip(X, Y)):
+            y, (a, zs) = self.forward_normalised(x, keep=True)
             d = y - yt
             loss += float(np.sum(d * d)) / (B * npix)
             gy = (2.0 / (B * npix)) * d
-            g2, gw3 = conv2d_grads(a2, self.W[2], gy[None])
-            gz2 = g2 * (1.0 - a2 * a2)
-            g1, gw2 = conv2d_grads(a1, self.W[1], gz2)
-            gz1 = g1 * (1.0 - a1 * a1)
-            _, gw1 = conv2d_grads(a0, self.W[0], gz1)
-            G[0] += gw1; G[1] += gw2; G[2] += gw3
+            gin, gw = conv2d_grads(a[LAYERS - 1], self.W[LAYERS - 1], gy[None])
+            G[LAYERS - 1] += gw
+            for k in range(LAYERS - 2, -1, -1):
+                gz = gin * gelu_deriv(zs[k])
+                gin, gw = conv2d_grads(a[k], self.W[k], gz)
+                G[k] += gw
+            GX[b] = gy + gin[0]          # the skip connection and the network
+        if input_grad:
+            return loss, G, GX
         return loss, G
 
 
@@ -140,7 +172,7 @@ def train(net, X, Y, steps, batch=16, lr=1e-3, seed=0, b1=0.9, b2=0.999, eps=1e-
         idx = rng.integers(0, X.shape[0], size=min(batch, X.shape[0]))
         loss, G = net.loss_and_grads(X[idx], Y[idx])
         hist.append(loss)
-        for k in range(3):
+        for k in range(len(net.W)):
             m[k] = b1 * m[k] + (1 - b1) * G[k]
             v[k] = b2 * v[k] + (1 - b2) * G[k] * G[k]
             mh = m[k] / (1 - b1 ** t)

@@ -39,7 +39,7 @@ class MgritOpts(ctypes.Structure):
                 ("min_coarse", c_int), ("relax", c_int), ("tol", c_double), ("max_iter", c_int),
                 ("pmg", PmgOpts), ("initial_guess", c_int), ("graphs", c_int),
                 ("profile", c_int), ("theta", c_double), ("cycle", c_int),
-                ("priority", c_int), ("coarse_cycles", c_int)]
+                ("priority", c_int), ("coarse_cycles", c_int), ("fused", c_int)]
 
 
 class MgritStats(ctypes.Structure):
@@ -102,12 +102,15 @@ EXPORTS = {
     "phic_apply": (c_int, [c_void_p, c_int, c_void_p, c_long, c_void_p, c_long, c_void_p]),
     "phic_train": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, c_int, c_int, c_double,
                            ctypes.c_ulonglong, POINTER(c_double), c_void_p]),
+    "phic_grad": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_long, POINTER(c_double),
+                          POINTER(ctypes.c_float), POINTER(ctypes.c_float), c_void_p]),
     "mgrit_set_coarse_propagator": (c_int, [c_void_p, c_void_p, c_double]),
     "mgrit_solve": (c_int, [c_void_p, POINTER(MgritOpts), c_void_p, c_void_p, POINTER(c_double),
                             c_void_p, POINTER(MgritStats), c_void_p]),
     "mgrit_profile": (c_int, [c_void_p, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                               POINTER(c_int), POINTER(ctypes.c_float), POINTER(c_long)]),
     "igm_wait_selftest": (c_int, [c_long, c_void_p]),
+    "igm_grid_barrier_selftest": (c_int, [c_int, ctypes.c_longlong, c_int, c_void_p]),
     "igm_last_error": (ctypes.c_char_p, []),
     "igm_kernel_launches": (c_long, []),
 }
@@ -593,10 +596,10 @@ def _ld(T):
 
 
 class Phic:
-    """Learned coarse propagator (phic_*): a 5 x 5 convolutional network on the
-    n x n coefficient grid, BF16 kernels."""
+    """Learned coarse propagator (phic_*): a four-layer 3 x 3 convolutional
+    network with GELU on the n x n coefficient grid, BF16 kernels."""
 
-    def __init__(self, n, channels=8, seed=0):
+    def __init__(self, n, channels=32, seed=0):
         h = c_void_p()
         _check(lib().phic_create(n, channels, seed, ctypes.byref(h)))
         self.h = h
@@ -638,6 +641,22 @@ class Phic:
                                 batch, lr, seed, loss.ctypes.data_as(POINTER(c_double)),
                                 _stream()))
         return loss[:steps]
+
+    def grad(self, U0, U1, input_grad=True):
+        """Loss and back-propagated gradients on the pairs U0[b] -> U1[b] (CUDA
+        float64 [nb, n*n]) as one minibatch: (loss, weight gradient [count],
+        gradient w.r.t. the normalised inputs [nb, n*n] or None)."""
+        assert _ld(U0) == _ld(U1)
+        nb = U0.shape[0]
+        cnt = self.weights.size
+        gw = np.zeros(cnt, dtype=np.float32)
+        gx = np.zeros((nb, self.n * self.n), dtype=np.float32) if input_grad else None
+        loss = c_double()
+        _check(lib().phic_grad(self.h, nb, _dptr(U0), _dptr(U1), _ld(U0), ctypes.byref(loss),
+                               gw.ctypes.data_as(POINTER(ctypes.c_float)),
+                               gx.ctypes.data_as(POINTER(ctypes.c_float)) if input_grad else None,
+                               _stream()))
+        return loss.value, gw, gx
 
 
 def mgrit_run_batched(handles, u0s, fhats=None, fcoefs=None, Us=None, check=True):
@@ -691,6 +710,12 @@ def mgrit_solve(problem, u0, fhat=None, fcoef=None, U=None, check=True, **opts):
 def wait_selftest(spins=1 << 16):
     """Status of igm_wait_selftest (IGM_ERR_TIMEOUT = -5 when the bound works)."""
     return lib().igm_wait_selftest(spins, _stream())
+
+
+def grid_barrier_selftest(nctas=8, wait_cycles=1 << 22, hold=1):
+    """Status of igm_grid_barrier_selftest (IGM_ERR_TIMEOUT = -5 with hold = 1
+    when the bound works, 0 with hold = 0)."""
+    return lib().igm_grid_barrier_selftest(nctas, wait_cycles, hold, _stream())
 
 
 def kernel_launches():

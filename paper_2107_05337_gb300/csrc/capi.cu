@@ -392,6 +392,12 @@ cudaError_t launch_ilut_apply(int prec, const PmgD& P, int grid, long smem, cuda
 cudaError_t launch_mgrit_sweep(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st) {
   return prec ? launch_mgrit_sweep_f32(a, grid, smem, st) : launch_mgrit_sweep_f64(a, grid, smem, st);
 }
+cudaError_t launch_mgrit_level(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st) {
+  return prec ? launch_mgrit_level_f32(a, grid, smem, st) : launch_mgrit_level_f64(a, grid, smem, st);
+}
+int mgrit_sweep_max_resident(int prec, long smem) {
+  return prec ? mgrit_sweep_max_resident_f32(smem) : mgrit_sweep_max_resident_f64(smem);
+}
 cudaError_t set_solver_smem(long bytes) {
   cudaError_t e = set_smem_f32(bytes);
   return e == cudaSuccess ? set_smem_f64(bytes) : e;
@@ -1061,6 +1067,25 @@ extern "C" igm_status igm_wait_selftest(long spins, igm_stream s) {
   return IGM_OK;
 }
 
+extern "C" igm_status igm_grid_barrier_selftest(int nctas, long long wait_cycles, int hold,
+                                                igm_stream s) {
+  if (nctas < 1 || nctas > 1024 || wait_cycles < 1)
+    return fail(IGM_ERR_ARG, "nctas must be in [1, 1024] and wait_cycles >= 1");
+  cudaStream_t st = (cudaStream_t)s;
+  int* dstat = nullptr;
+  CU(cudaMallocAsync(&dstat, 4 * sizeof(unsigned) + sizeof(int), st));
+  unsigned* gbar = (unsigned*)(dstat + 1);
+  CU(cudaMemsetAsync(dstat, 0, 4 * sizeof(unsigned) + sizeof(int), st));
+  CU(launch_barrier_selftest(nctas, wait_cycles, hold ? 1 : 0, gbar, dstat, st));
+  g_launches++;
+  int h = 0;
+  CU(cudaMemcpyAsync(&h, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaFreeAsync(dstat, st));
+  CU(cudaStreamSynchronize(st));
+  if (h == ST_TIMEOUT) return fail(IGM_ERR_TIMEOUT, "bounded grid barrier wait gave up as intended");
+  return IGM_OK;
+}
+
 extern "C" igm_status pmg_trace(pmg_handle* h, long long* out, int reset) {
   if (!h || !out) return fail(IGM_ERR_ARG, "null argument");
   if (!h->d.trace) return fail(IGM_ERR_ARG, "handle was set up without trace");
@@ -1209,18 +1234,22 @@ struct phic_handle {
   PhicTrain train;
   Uploader up;        // weights
   Uploader upw;       // inference work (regrown on demand)
-  Uploader upt;       // training state (per phic_train call)
-  Uploader uptw;      // training activations (per phic_train call)
+  Uploader upt;       // training state (per phic_train / phic_grad call)
+  Uploader uptw;      // training activations (per phic_train / phic_grad call)
 };
 
-static igm_status phic_work(phic_handle* h, Uploader& up, PhicWork& w, int nb) {
-  if (w.cap >= nb) return IGM_OK;
+// Activations for nb images (keep: also the pre-activations, for training).
+static igm_status phic_work(phic_handle* h, Uploader& up, PhicWork& w, int nb, bool keep = false) {
+  if (w.cap >= nb && (!keep || w.z[0])) return IGM_OK;
   const size_t N = (size_t)h->net.n * h->net.n, C = h->net.C;
   up = Uploader();
+  w = PhicWork();
   w.x0 = (__nv_bfloat16*)up.raw(2 * N * nb);
-  w.a1 = (__nv_bfloat16*)up.raw(2 * N * C * nb);
-  w.a2 = (__nv_bfloat16*)up.raw(2 * N * C * nb);
-  w.z3 = (float*)up.raw(4 * N * nb);
+  for (int l = 0; l < 3; ++l) {
+    w.h[l] = (__nv_bfloat16*)up.raw(2 * N * C * nb);
+    if (keep) w.z[l] = (__nv_bfloat16*)up.raw(2 * N * C * nb);
+  }
+  w.z4 = (float*)up.raw(4 * N * nb);
   w.s = (double*)up.raw(8 * (size_t)nb);
   if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
   w.cap = nb;
@@ -1228,28 +1257,33 @@ static igm_status phic_work(phic_handle* h, Uploader& up, PhicWork& w, int nb) {
 }
 
 extern "C" igm_status phic_create(int n, int channels, unsigned long long seed, phic_handle** out) {
-  if (!out || n < 1 || n > 1024 || channels < 1 || channels > kPhicMaxC)
-    return fail(IGM_ERR_ARG, "phic_create: need n in [1, 1024] and channels in [1, 8]");
+  if (!out || n < 1 || n > 1024 || (channels != 16 && channels != 32))
+    return fail(IGM_ERR_ARG, "phic_create: need n in [1, 1024] and channels 16 or 32");
   auto h = std::make_unique<phic_handle>();
   PhicNet& net = h->net;
+  const int C = channels;
   net.n = n;
-  net.C = channels;
-  net.o1 = 0;
-  net.o2 = channels * 25;
-  net.o3 = net.o2 + channels * channels * 25;
-  net.count = net.o3 + channels * 25;
-  // initial weights: K1, K2 normal with standard deviation 1/(5 sqrt(fan-in
-  // channels)), K3 = 0 (the network starts as the identity)
+  net.C = C;
+  net.o[0] = 0;
+  net.o[1] = C * 9;
+  net.o[2] = net.o[1] + C * C * 9;
+  net.o[3] = net.o[2] + C * C * 9;
+  net.count = net.o[3] + C * 9;
+  // initial weights: K1 normal with standard deviation 1/3, K2 and K3 with
+  // 1/(3 sqrt C), K4 = 0 (the network starts as the identity)
   std::vector<float> w(net.count, 0.0f);
   std::mt19937_64 rng(seed);
   std::normal_distribution<double> nd(0.0, 1.0);
-  for (int i = 0; i < net.o2; ++i) w[i] = (float)(nd(rng) / 5.0);
-  for (int i = net.o2; i < net.o3; ++i) w[i] = (float)(nd(rng) / (5.0 * std::sqrt((double)channels)));
+  for (int i = 0; i < net.o[1]; ++i) w[i] = (float)(nd(rng) / 3.0);
+  for (int i = net.o[1]; i < net.o[3]; ++i) w[i] = (float)(nd(rng) / (3.0 * std::sqrt((double)C)));
   net.wall = h->up.put(w);
+  net.wf = (__nv_bfloat16*)h->up.raw(2 * (size_t)2 * C * 9 * C);
+  net.wb = (__nv_bfloat16*)h->up.raw(2 * (size_t)2 * C * 9 * C);
+  net.w1 = (float*)h->up.raw(4 * (size_t)C * 9);
+  net.w4 = (float*)h->up.raw(4 * (size_t)C * 9);
   if (h->up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(h->up.err));
-  net.w1 = net.wall + net.o1;
-  net.w2 = net.wall + net.o2;
-  net.w3 = net.wall + net.o3;
+  CU(phic_refresh(net, 0));
+  CU(cudaStreamSynchronize(0));
   *out = h.release();
   return IGM_OK;
 }
@@ -1259,6 +1293,8 @@ extern "C" void phic_destroy(phic_handle* h) { delete h; }
 extern "C" igm_status phic_set_weights(phic_handle* h, const float* w) {
   if (!h || !w) return fail(IGM_ERR_ARG, "null argument");
   CU(cudaMemcpy(h->net.wall, w, sizeof(float) * h->net.count, cudaMemcpyHostToDevice));
+  CU(phic_refresh(h->net, 0));
+  CU(cudaStreamSynchronize(0));
   return IGM_OK;
 }
 
@@ -1281,6 +1317,39 @@ extern "C" igm_status phic_apply(phic_handle* h, int nb, const double* u, long l
   return IGM_OK;
 }
 
+// Training state for npairs pairs and minibatches of `batch`, the pairs
+// normalised on the device; idx (DEVICE, [nidx]) receives nothing yet.
+static igm_status phic_train_state(phic_handle* h, int npairs, const double* U0, const double* U1,
+                                   long ld, int batch, int nloss, int nidx, int** idx,
+                                   cudaStream_t st) {
+  const long N = (long)h->net.n * h->net.n;
+  const size_t C = h->net.C, cnt = h->net.count;
+  PhicTrain& t = h->train;
+  Uploader& up = h->upt;
+  up = Uploader();
+  t = PhicTrain();
+  t.np = npairs;
+  t.X = (float*)up.raw(4 * (size_t)N * npairs);
+  t.Y = (float*)up.raw(4 * (size_t)N * npairs);
+  t.xf = (float*)up.raw(4 * (size_t)N * batch);
+  t.y = (float*)up.raw(4 * (size_t)N * batch);
+  t.gy = (float*)up.raw(4 * (size_t)N * batch);
+  t.gx = (float*)up.raw(4 * (size_t)N * batch);
+  for (int l = 0; l < 3; ++l) t.gz[l] = (__nv_bfloat16*)up.raw(2 * (size_t)N * C * batch);
+  t.part = (float*)up.raw(4 * cnt * batch);
+  t.gw = (float*)up.raw(4 * cnt);
+  t.m = (float*)up.raw(4 * cnt);
+  t.v = (float*)up.raw(4 * cnt);
+  t.loss = (float*)up.raw(4 * (size_t)std::max(1, nloss));
+  *idx = (int*)up.raw(4 * (size_t)std::max(1, nidx));
+  if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
+  igm_status r = phic_work(h, h->uptw, t.work, batch, true);
+  if (r != IGM_OK) return r;
+  CU(cudaMemsetAsync(t.loss, 0, 4 * (size_t)std::max(1, nloss), st));
+  CU(phic_prepare_pairs(h->net.n, npairs, U0, U1, ld, t.X, t.Y, st));
+  return IGM_OK;
+}
+
 extern "C" igm_status phic_train(phic_handle* h, int npairs, const double* U0, const double* U1,
                                  long ld, int steps, int batch, double lr, unsigned long long seed,
                                  double* loss, igm_stream s) {
@@ -1289,37 +1358,22 @@ extern "C" igm_status phic_train(phic_handle* h, int npairs, const double* U0, c
   if (npairs < 1 || steps < 0 || batch < 1 || ld < N || !(lr > 0.0))
     return fail(IGM_ERR_ARG, "phic_train: need npairs, batch >= 1, steps >= 0, ld >= n*n, lr > 0");
   cudaStream_t st = (cudaStream_t)s;
-  PhicTrain& t = h->train;
-  Uploader& up = h->upt;
-  up = Uploader();
-  t = PhicTrain();
-  const size_t C = h->net.C;
-  t.np = npairs;
-  t.X = (float*)up.raw(4 * (size_t)N * npairs);
-  t.Y = (float*)up.raw(4 * (size_t)N * npairs);
-  t.xf = (float*)up.raw(4 * (size_t)N * batch);
-  t.y = (float*)up.raw(4 * (size_t)N * batch);
-  t.g1 = (float*)up.raw(4 * (size_t)N * C * batch);
-  t.g2 = (float*)up.raw(4 * (size_t)N * C * batch);
-  t.g3 = (float*)up.raw(4 * (size_t)N * batch);
-  t.wf2 = (float*)up.raw(4 * C * C * 25);
-  t.wf3 = (float*)up.raw(4 * C * 25);
-  t.gw = (float*)up.raw(4 * (size_t)h->net.count);
-  t.m = (float*)up.raw(4 * (size_t)h->net.count);
-  t.v = (float*)up.raw(4 * (size_t)h->net.count);
-  t.loss = (float*)up.raw(4 * (size_t)std::max(1, steps));
-  int* idx = (int*)up.raw(4 * (size_t)std::max(1, steps) * batch);
-  if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
-  igm_status r = phic_work(h, h->uptw, t.work, batch);
+  int* idx = nullptr;
+  igm_status r = phic_train_state(h, npairs, U0, U1, ld, batch, steps, std::max(1, steps) * batch,
+                                  &idx, st);
   if (r != IGM_OK) return r;
+  PhicTrain& t = h->train;
+  CU(cudaMemsetAsync(t.m, 0, 4 * (size_t)h->net.count, st));
+  CU(cudaMemsetAsync(t.v, 0, 4 * (size_t)h->net.count, st));
   std::vector<int> hidx((size_t)std::max(1, steps) * batch);
   std::mt19937_64 rng(seed);
   std::uniform_int_distribution<int> ud(0, npairs - 1);
   for (auto& k : hidx) k = ud(rng);
   CU(cudaMemcpyAsync(idx, hidx.data(), sizeof(int) * hidx.size(), cudaMemcpyHostToDevice, st));
-  CU(phic_prepare_pairs(h->net.n, npairs, U0, U1, ld, t.X, t.Y, st));
-  for (int k = 0; k < steps; ++k)
-    CU(phic_train_step(h->net, t, batch, idx + (size_t)k * batch, k, (float)lr, st));
+  for (int k = 0; k < steps; ++k) {
+    CU(phic_backprop(h->net, t, batch, idx + (size_t)k * batch, t.loss + k, false, st));
+    CU(phic_adam(h->net, t, k, (float)lr, st));
+  }
   if (loss && steps > 0) {
     std::vector<float> hl(steps);
     CU(cudaMemcpyAsync(hl.data(), t.loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, st));
@@ -1327,6 +1381,29 @@ extern "C" igm_status phic_train(phic_handle* h, int npairs, const double* U0, c
     for (int k = 0; k < steps; ++k) loss[k] = hl[k];
   }
   CU(cudaStreamSynchronize(st));
+  return IGM_OK;
+}
+
+extern "C" igm_status phic_grad(phic_handle* h, int nb, const double* U0, const double* U1,
+                                long ld, double* loss, float* gw, float* gx, igm_stream s) {
+  if (!h || !U0 || !U1 || !loss || !gw) return fail(IGM_ERR_ARG, "null argument");
+  const long N = (long)h->net.n * h->net.n;
+  if (nb < 1 || ld < N) return fail(IGM_ERR_ARG, "phic_grad: need nb >= 1 and ld >= n*n");
+  cudaStream_t st = (cudaStream_t)s;
+  int* idx = nullptr;
+  igm_status r = phic_train_state(h, nb, U0, U1, ld, nb, 1, nb, &idx, st);
+  if (r != IGM_OK) return r;
+  PhicTrain& t = h->train;
+  std::vector<int> hidx(nb);
+  for (int k = 0; k < nb; ++k) hidx[k] = k;
+  CU(cudaMemcpyAsync(idx, hidx.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+  CU(phic_backprop(h->net, t, nb, idx, t.loss, gx != nullptr, st));
+  float hl = 0.0f;
+  CU(cudaMemcpyAsync(&hl, t.loss, sizeof(float), cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(gw, t.gw, sizeof(float) * h->net.count, cudaMemcpyDeviceToHost, st));
+  if (gx) CU(cudaMemcpyAsync(gx, t.gx, sizeof(float) * (size_t)N * nb, cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  *loss = hl;
   return IGM_OK;
 }
 
@@ -1348,6 +1425,7 @@ extern "C" void mgrit_default_opts(mgrit_opts* o) {
   o->cycle = 0;
   o->priority = 0;
   o->coarse_cycles = 0;
+  o->fused = 1;
 }
 
 struct Level {
@@ -1370,6 +1448,8 @@ struct mgrit_handle {
   std::vector<pmg_handle*> owned;
   Uploader up;
   int max_grid = 1;
+  std::vector<int> max_resident;            // per level: CTAs of a cooperative sweep launch
+  unsigned* gbar = nullptr;                 // grid barrier of the fused level visits
   double* scratch = nullptr;
   double* norms = nullptr;
   unsigned long long* counters = nullptr;   // [0] solves, [1] cycles
@@ -1380,6 +1460,7 @@ struct mgrit_handle {
   // graphs of one iteration: A = fine relaxation + residual + norm copy,
   // B = coarse levels + corrections; captured for one (U, fhat) pair
   cudaGraphExec_t gA = nullptr, gB = nullptr;
+  long gA_launches = 0, gB_launches = 0;    // kernels in each graph
   const double* g_U = nullptr;
   const double* g_fhat = nullptr;
   // the run executes on this stream (graph capture is not allowed on the
@@ -1440,6 +1521,7 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   if (!(o.theta >= 0.0 && o.theta <= 1.0)) return fail(IGM_ERR_ARG, "theta must be in [0, 1]");
   if (o.cycle < 0 || o.cycle > 2) return fail(IGM_ERR_ARG, "cycle must be 0 (V), 1 (F) or 2 (W)");
   if (o.coarse_cycles < 0) return fail(IGM_ERR_ARG, "coarse_cycles must be >= 0");
+  if (o.fused != 0 && o.fused != 1) return fail(IGM_ERR_ARG, "fused must be 0 or 1");
   auto t0 = std::chrono::steady_clock::now();
   auto mg = std::make_unique<mgrit_handle>();
   mg->ops = ops;
@@ -1477,6 +1559,7 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   mg->norms = (double*)up.raw(sizeof(double) * (size_t)mg->max_grid);
   mg->counters = (unsigned long long*)up.raw(sizeof(unsigned long long) * 2);
   mg->status = (int*)up.raw(sizeof(int));
+  mg->gbar = (unsigned*)up.raw(sizeof(unsigned) * 4);
   mg->dfcoef = (double*)up.raw(sizeof(double) * (size_t)(o.Nt + 1));
   if (up.err != cudaSuccess) return fail(IGM_ERR_OOM, cudaGetErrorString(up.err));
   CU(cudaMallocHost(&mg->hnorms, sizeof(double) * mg->max_grid));
@@ -1491,6 +1574,8 @@ extern "C" igm_status mgrit_create(const iga_ops* ops, const mgrit_opts* opts, m
   for (int l = 0; l < nlev; ++l) {
     igm_status r = ensure_arena(L[l].h, mg->max_grid);
     if (r != IGM_OK) return r;
+    mg->max_resident.push_back(
+        o.fused ? mgrit_sweep_max_resident(L[l].h->d.precision, smem_of(L[l].h)) : 0);
   }
   mg->setup_seconds =
       std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1527,9 +1612,11 @@ extern "C" igm_status mgrit_set_coarse_propagator(mgrit_handle* mg, phic_handle*
   return IGM_OK;
 }
 
-// Launch one sweep kernel on level l.
+// Launch one sweep kernel on level l: one mode, or (nmodes > 1) the modes of
+// a level visit in one cooperative launch with grid barriers between them.
 static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm, double* U,
-                        const double* fhat, cudaStream_t st, bool profile) {
+                        const double* fhat, cudaStream_t st, bool profile,
+                        const int* modes = nullptr, int nmodes = 0) {
   const int nlev = (int)mg->L.size();
   std::vector<Level>& L = mg->L;
   SweepArgs a;
@@ -1556,13 +1643,21 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
   a.ncycles = l > 0 ? mg->o.coarse_cycles : 0;
   a.counters = mg->counters;
   a.status = mg->status;
-  ProfRec rec{l, grid, mode, nullptr, nullptr};
+  a.nmodes = nmodes > 1 ? nmodes : 0;
+  for (int q = 0; q < nmodes && q < 3; ++q) a.modes[q] = modes[q];
+  a.gbar = mg->gbar;
+  a.bar_cycles = kWaitCycles;
+  ProfRec rec{l, grid, a.nmodes ? (int)MODE_FUSED : mode, nullptr, nullptr};
+  if (a.nmodes) CU(cudaMemsetAsync(mg->gbar, 0, sizeof(unsigned) * 4, st));
   if (profile) {
     CU(cudaEventCreate(&rec.e0));
     CU(cudaEventCreate(&rec.e1));
     CU(cudaEventRecord(rec.e0, st));
   }
-  CU(launch_mgrit_sweep(a.P.precision, a, grid, smem_of(L[l].h), st));
+  if (a.nmodes)
+    CU(launch_mgrit_level(a.P.precision, a, grid, smem_of(L[l].h), st));
+  else
+    CU(launch_mgrit_sweep(a.P.precision, a, grid, smem_of(L[l].h), st));
   g_launches++;
   if (profile) {
     CU(cudaEventRecord(rec.e1, st));
@@ -1580,13 +1675,29 @@ static igm_status sweep(mgrit_handle* mg, int l, int mode, int grid, double* nrm
     igm_status _r = sweep(mg, l, mode, grid, nrm, U, fhat, st, profile);         \
     if (_r != IGM_OK) return _r;                                                 \
   } while (0)
+#define SWEEP_FUSED(l, modes, nmodes, grid, nrm)                                 \
+  do {                                                                           \
+    igm_status _r = sweep(mg, l, 0, grid, nrm, U, fhat, st, profile, modes, nmodes); \
+    if (_r != IGM_OK) return _r;                                                 \
+  } while (0)
+
+// Whether the relaxation phases of a visit of level l run as one cooperative
+// launch: requested, and all the level's CTAs can be resident at once.
+static bool fused_level(const mgrit_handle* mg, int l) {
+  return mg->o.fused && mg->o.relax == 1 &&
+         f_grid(mg->L[l].Nl, mg->o.m) <= mg->max_resident[l];
+}
 
 // Part A of an iteration: fine-level relaxation (Sec. 3, FCF or F) and the
 // C-point residual, injected into g^(1); copies the per-interval norms.
 static igm_status part_A(mgrit_handle* mg, bool first, double* U, const double* fhat,
                          cudaStream_t st, bool profile) {
   const int nint0 = mg->L[0].Nl / mg->o.m, nf0 = f_grid(mg->L[0].Nl, mg->o.m);
-  if (mg->o.relax == 1) {
+  if (mg->o.relax == 1 && fused_level(mg, 0)) {
+    // one launch: (F,) C, F + residual with grid barriers between them
+    static const int fcf[3] = {MODE_F, MODE_C, MODE_FR};
+    SWEEP_FUSED(0, first ? fcf : fcf + 1, first ? 3 : 2, nf0, mg->norms);
+  } else if (mg->o.relax == 1) {
     // the leading F-relaxation is skipped after the first iteration: the
     // interpolation has just made the F-points Phi-consistent
     if (first) SWEEP(0, MODE_F, nf0, nullptr);
@@ -1615,11 +1726,16 @@ static igm_status visit(mgrit_handle* mg, int l, int kind, double* U, const doub
     return IGM_OK;
   }
   const int ni = L[l].Nl / mg->o.m, nf = f_grid(L[l].Nl, mg->o.m);
-  if (mg->o.relax == 1) {
-    SWEEP(l, MODE_F, nf, nullptr);
-    SWEEP(l, MODE_C, ni, nullptr);
+  if (fused_level(mg, l)) {
+    static const int fcf[3] = {MODE_F, MODE_C, MODE_FR};
+    SWEEP_FUSED(l, fcf, 3, nf, nullptr);
+  } else {
+    if (mg->o.relax == 1) {
+      SWEEP(l, MODE_F, nf, nullptr);
+      SWEEP(l, MODE_C, ni, nullptr);
+    }
+    SWEEP(l, MODE_FR, nf, nullptr);
   }
-  SWEEP(l, MODE_FR, nf, nullptr);
   CU(cudaMemsetAsync(L[l + 1].W, 0, sizeof(double) * (size_t)(L[l + 1].Nl + 1) * N, st));
   const int sub[3][2] = {{0, -1}, {1, 0}, {2, 2}};
   for (int v = 0; v < 2; ++v) {
@@ -1654,7 +1770,12 @@ static igm_status part_B(mgrit_handle* mg, double* U, const double* fhat, cudaSt
 static igm_status capture(mgrit_handle* mg, bool partA, double* U, const double* fhat,
                           cudaStream_t st, cudaGraphExec_t* out) {
   CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  const long before = g_launches.load();
   igm_status r = partA ? part_A(mg, false, U, fhat, st, false) : part_B(mg, U, fhat, st, false);
+  // the captured kernels launch when the graph does
+  const long nk = g_launches.load() - before;
+  g_launches -= nk;
+  (partA ? mg->gA_launches : mg->gB_launches) = nk;
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamEndCapture(st, &g);
   if (r != IGM_OK) { if (g) cudaGraphDestroy(g); return r; }
@@ -1693,7 +1814,7 @@ static igm_status launch_A(mgrit_handle* mg) {
       if (r != IGM_OK) return r;
     }
     CU(cudaGraphLaunch(mg->gA, st));
-    g_launches += (mg->o.relax == 1) ? 2 : 1;
+    g_launches += mg->gA_launches;
   } else {
     igm_status r = part_A(mg, R.it == 0, U, fhat, st, profile);
     if (r != IGM_OK) return r;
@@ -1824,9 +1945,7 @@ static igm_status run_advance(mgrit_handle* mg) {
       if (r != IGM_OK) return r;
     }
     CU(cudaGraphLaunch(mg->gB, st));
-    int nb = 0;
-    for (int l = 1; l < nlev; ++l) nb += (l == nlev - 1) ? 1 : (o.relax == 1 ? 3 : 1);
-    g_launches += nb + (nlev - 1);
+    g_launches += mg->gB_launches;
   } else {
     igm_status r = part_B(mg, U, fhat, st, profile);
     if (r != IGM_OK) return r;

@@ -759,9 +759,10 @@ __device__ bool wave_sweep(int n, const RecSet& R, Pipe& pp, T* v, char* scr, in
 // threads): pre_i = b_i - (E, NW, N, NE couplings) x with the values before
 // the sweep, i.e. the couplings to unknowns that come later in the
 // lexicographic order.  Pass 2: the grid rows in order, warp w taking rows
-// w, w + 16, ...; a warp loads its row's coefficients and pre, waits for the
-// preceding row (row barrier), forms t_r = pre_r - (SW, S, SE couplings) x
-// with that row's new values, and solves the in-row recurrence
+// w, w + 16, ...; a warp loads its row's coefficients and pre and forms the
+// products of the alphas its scan combines, waits for the preceding row (row
+// barrier), forms t_r = pre_r - (SW, S, SE couplings) x with that row's new
+// values, and solves the in-row recurrence
 // x_r = alpha_r x_{r-1} + t_r / a_C,r (alpha = -a_W/a_C) as a warp-wide scan
 // of affine maps, E consecutive unknowns per lane.  Row records hold
 // coefficient q of unknown r = lane * E + e at (q * E + e) * 32 + lane.
@@ -812,6 +813,23 @@ __device__ bool gs_wave(int n, const RecSet& R, Pipe& pp, const T* b, T* x, T* p
       ic[e] = c(G_INVC);
       pr[e] = in ? pre[by * n + r] : (T)0;
     }
+    // the lane's composed factor A = prod alpha and the value it has at each
+    // level of the scan below depend on the coefficients only: formed before
+    // the wait, off the chain through the preceding row
+    T alpha[E];
+    T A = 1;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      alpha[e] = r0 + e < n ? al[e] : (T)0;
+      if (r0 + e < n) A = alpha[e] * A;
+    }
+    T Al[5];
+#pragma unroll
+    for (int o = 0; o < 5; ++o) {
+      Al[o] = A;
+      const T Ap = __shfl_up_sync(0xffffffffu, A, 1 << o);
+      if (lane >= (1 << o)) A = A * Ap;
+    }
     bool ok = true;
     // suspended until the row two back is complete, then polling for the
     // preceding one (at most one warp polls at a time)
@@ -819,11 +837,10 @@ __device__ bool gs_wave(int n, const RecSet& R, Pipe& pp, const T* b, T* x, T* p
     __syncwarp();  // lane 0's acquire of the preceding row, for the whole warp
     if (!__shfl_sync(0xffffffffu, ok, 0)) break;
     const long long tw = (trace && threadIdx.x == 0) ? clock64() : 0;
-    T alpha[E], beta[E];
-    T A = 1, B = 0;
+    T beta[E];
+    T B = 0;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      alpha[e] = 0;
       beta[e] = 0;
       const int r = r0 + e;
       if (r < n) {
@@ -835,21 +852,16 @@ __device__ bool gs_wave(int n, const RecSet& R, Pipe& pp, const T* b, T* x, T* p
           const T sw = r > 0 ? cSW[e] : (T)0, se = r + 1 < n ? cSE[e] : (T)0;
           t -= (sw * xSW + cS[e] * xS) + se * xSE;
         }
-        alpha[e] = al[e];
         beta[e] = ic[e] * t;
         B = alpha[e] * B + beta[e];
-        A = alpha[e] * A;
       }
     }
-    // inclusive scan of the lanes' affine maps x_out = A x_in + B
+    // inclusive scan of the lanes' affine maps x_out = A x_in + B (the A of
+    // each level precomputed above)
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const T Ap = __shfl_up_sync(0xffffffffu, A, o);
-      const T Bp = __shfl_up_sync(0xffffffffu, B, o);
-      if (lane >= o) {
-        B = A * Bp + B;
-        A = A * Ap;
-      }
+    for (int o = 0; o < 5; ++o) {
+      const T Bp = __shfl_up_sync(0xffffffffu, B, 1 << o);
+      if (lane >= (1 << o)) B = Al[o] * Bp + B;
     }
     T xin = __shfl_up_sync(0xffffffffu, B, 1);
     if (lane == 0) xin = 0;

@@ -11,7 +11,8 @@ namespace igm {
 // C-point residual and injection, coarse correction plus F-relaxation (ideal
 // interpolation), sequential stepping on the coarsest level, and the C-point
 // residual alone.
-enum : int { MODE_F = 0, MODE_C = 1, MODE_FR = 2, MODE_CF = 3, MODE_SEQ = 4, MODE_R = 5 };
+enum : int { MODE_F = 0, MODE_C = 1, MODE_FR = 2, MODE_CF = 3, MODE_SEQ = 4, MODE_R = 5,
+             MODE_FUSED = 6 /* profile records of a fused level visit */ };
 
 struct SweepArgs {
   PmgD P;
@@ -31,6 +32,12 @@ struct SweepArgs {
   int ncycles;
   unsigned long long* counters;  // [0] solves, [1] cycles
   int* status;
+  // fused level visit (one cooperative launch): the modes run in this order
+  // with a bounded grid barrier between consecutive ones; nmodes = 0: `mode` alone
+  int nmodes;
+  int modes[3];
+  unsigned* gbar;         // [0] arrivals, [1] generation, [2] abort; zeroed before the launch
+  long long bar_cycles;   // bound of one barrier wait in SM clocks
 };
 
 // prec: 0 = FP64 form, 1 = mixed form.  Each returns cudaGetLastError().
@@ -40,6 +47,17 @@ cudaError_t launch_pmg_solve(int prec, const PmgD& P, int grid, long smem, cudaS
 cudaError_t launch_ilut_apply(int prec, const PmgD& P, int grid, long smem, cudaStream_t st,
                               const double* r, double* z, long ld, char* garena, int* status);
 cudaError_t launch_mgrit_sweep(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st);
+// The same kernel launched cooperatively (all CTAs resident at once), for a
+// fused level visit (a.nmodes > 1).
+cudaError_t launch_mgrit_level(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st);
+// CTAs of the sweep kernel that can be resident at once on the current device
+// with `smem` bytes of dynamic shared memory (0 on error).
+int mgrit_sweep_max_resident(int prec, long smem);
+// Failure-detection self-test of the grid barrier: nctas CTAs (cooperative
+// launch) pass two barriers; with hold, CTA 0 never arrives at the first, so
+// every CTA's wait runs out after `cycles` SM clocks and records ST_TIMEOUT.
+cudaError_t launch_barrier_selftest(int nctas, long long cycles, int hold, unsigned* gbar,
+                                    int* status, cudaStream_t st);
 cudaError_t launch_apply_op(const PmgD& P, int which, int nrhs, const double* x, double* y, long ld,
                             double* scratch, cudaStream_t st);
 // One CTA waits (bounded by `spins` polls) on an mbarrier that no copy or
@@ -59,6 +77,10 @@ cudaError_t launch_ilut_apply_f64(const PmgD&, int, long, cudaStream_t, const do
                                   char*, int*);
 cudaError_t launch_mgrit_sweep_f32(const SweepArgs&, int, long, cudaStream_t);
 cudaError_t launch_mgrit_sweep_f64(const SweepArgs&, int, long, cudaStream_t);
+cudaError_t launch_mgrit_level_f32(const SweepArgs&, int, long, cudaStream_t);
+cudaError_t launch_mgrit_level_f64(const SweepArgs&, int, long, cudaStream_t);
+int mgrit_sweep_max_resident_f32(long smem);
+int mgrit_sweep_max_resident_f64(long smem);
 cudaError_t set_smem_f32(long bytes);
 cudaError_t set_smem_f64(long bytes);
 

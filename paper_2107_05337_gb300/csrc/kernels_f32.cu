@@ -21,6 +21,30 @@ cudaError_t launch_mgrit_sweep_f32(const SweepArgs& a, int grid, long smem, cuda
   return cudaGetLastError();
 }
 
+cudaError_t launch_mgrit_level_f32(const SweepArgs& a, int grid, long smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mgrit_sweep<1>, a);
+}
+
+int mgrit_sweep_max_resident_f32(long smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgrit_sweep<1>, kBlock,
+                                                    (size_t)smem) != cudaSuccess)
+    return 0;
+  return per * sms;
+}
+
 cudaError_t set_smem_f32(long bytes) {
   cudaError_t e = cudaFuncSetAttribute((const void*)k_pmg_solve<1>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);

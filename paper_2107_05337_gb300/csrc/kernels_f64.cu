@@ -21,6 +21,30 @@ cudaError_t launch_mgrit_sweep_f64(const SweepArgs& a, int grid, long smem, cuda
   return cudaGetLastError();
 }
 
+cudaError_t launch_mgrit_level_f64(const SweepArgs& a, int grid, long smem, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_mgrit_sweep<0>, a);
+}
+
+int mgrit_sweep_max_resident_f64(long smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_mgrit_sweep<0>, kBlock,
+                                                    (size_t)smem) != cudaSuccess)
+    return 0;
+  return per * sms;
+}
+
 cudaError_t set_smem_f64(long bytes) {
   cudaError_t e = cudaFuncSetAttribute((const void*)k_pmg_solve<0>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -65,6 +89,27 @@ __global__ void k_wait_selftest(long spins, int* status) {
   __syncthreads();
   const bool got = mbar_wait(&bar, 0u, spins);
   if (!got && threadIdx.x == 0) atomicMin(status, ST_TIMEOUT);
+}
+
+// Failure-detection self-test of the grid barrier of the fused level visits:
+// two barriers; with hold, CTA 0 does not arrive at the first one.
+__global__ void k_barrier_selftest(long long cycles, int hold, unsigned* gbar, int* status) {
+  if (!grid_barrier(gbar, (int)gridDim.x, cycles, status, hold && blockIdx.x == 0)) return;
+  grid_barrier(gbar, (int)gridDim.x, cycles, status, false);
+}
+
+cudaError_t launch_barrier_selftest(int nctas, long long cycles, int hold, unsigned* gbar,
+                                    int* status, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)nctas);
+  cfg.blockDim = dim3(32);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_barrier_selftest, cycles, hold, gbar, status);
 }
 
 cudaError_t launch_wait_selftest(long spins, int* status, cudaStream_t st) {

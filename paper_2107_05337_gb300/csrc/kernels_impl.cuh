@@ -94,21 +94,62 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
   }
 }
 
-// One CTA per interval j of the level (or one CTA for the sequential coarsest
-// level).  Every mode is a run of consecutive steps n0..n1 of one interval,
-// the last of which may be the C-point residual.  When m does not divide N_l,
-// CTA j = nint (launched in the F-relaxation modes only) owns the partial last
-// interval: steps nint*m + 1 .. N_l, all F-points.
+// Bounded barrier over all CTAs of a cooperatively launched kernel (the
+// phases of one MGRIT level visit, Sec. 3).  gb[0] counts arrivals, gb[1] is
+// the generation, gb[2] an abort flag; the host zeroes them before the
+// launch.  Thread 0 of each CTA arrives, then waits (suspended for short
+// periods, at most `cycles` SM clocks) for the generation to change; a CTA
+// that gives up records ST_TIMEOUT and raises the abort flag, so that the
+// others stop waiting as well.  hold: this CTA does not arrive (the
+// failure-detection self-test).  Returns false on a timeout (CTA-uniform).
+__device__ inline bool grid_barrier(unsigned* gb, int nctas, long long cycles, int* status,
+                                    bool hold) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    volatile unsigned* vgb = gb;
+    const unsigned gen = vgb[1];
+    __threadfence();  // this CTA's writes before its arrival
+    bool released = false;
+    if (!hold && atomicAdd(gb, 1u) == (unsigned)nctas - 1) {
+      atomicExch(gb, 0u);
+      __threadfence();
+      atomicAdd(gb + 1, 1u);
+      released = true;
+    }
+    if (!released) {
+      const long long t0 = clock64();
+      while (vgb[1] == gen) {
+        if (vgb[2] != 0u || clock64() - t0 > cycles) {
+          atomicExch(gb + 2, 1u);
+          if (status) atomicMin(status, ST_TIMEOUT);
+          s_ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();  // the other CTAs' writes before this CTA goes on
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// The work of CTA j in one sweep mode.  Every mode is a run of consecutive
+// steps n0..n1 of one interval, the last of which may be the C-point
+// residual.  When m does not divide N_l, CTA j = nint owns the partial last
+// interval (steps nint*m + 1 .. N_l, all F-points) in the F-relaxation modes
+// and has nothing to do in the C-point modes.
 template <int PREC>
-__global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
-  __shared__ double red[32];
-  Pipe pp;
-  char* arena = cta_setup(a.P, a.garena, pp);
+__device__ __forceinline__ void sweep_mode(const SweepArgs& a, Pipe& pp, char* arena, double* red,
+                                           int mode) {
   const int j = blockIdx.x, m = a.m, N = a.P.N;
   const bool tail = j == a.nint;
+  if (tail && (mode == MODE_C || mode == MODE_R)) return;
   int n0 = j * m + 1, n1 = tail ? a.Nl : j * m + m - 1;
   bool resid = false;
-  switch (a.mode) {
+  switch (mode) {
     case MODE_C: n0 = n1 = (j + 1) * m; break;
     case MODE_R: n0 = n1 = (j + 1) * m; resid = true; break;
     case MODE_FR:
@@ -139,6 +180,26 @@ __global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
     default: break;  // MODE_F
   }
   for (int n = n0; n <= n1; ++n) mgrit_step<PREC>(a, pp, arena, red, n, resid && n == n1, j);
+}
+
+// One CTA per interval j of the level (or one CTA for the sequential coarsest
+// level), running one sweep mode; or, launched cooperatively with
+// a.nmodes > 1, the modes of one level visit in turn (F, C, F + residual:
+// Sec. 3's FCF relaxation and C-point residual) with a grid barrier between
+// them, so that a level visit is one launch.
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
+  __shared__ double red[32];
+  Pipe pp;
+  char* arena = cta_setup(a.P, a.garena, pp);
+  if (a.nmodes <= 0) {
+    sweep_mode<PREC>(a, pp, arena, red, a.mode);
+    return;
+  }
+  for (int q = 0; q < a.nmodes; ++q) {
+    if (q > 0 && !grid_barrier(a.gbar, (int)gridDim.x, a.bar_cycles, a.status, false)) return;
+    sweep_mode<PREC>(a, pp, arena, red, a.modes[q]);
+  }
 }
 
 }  // namespace igm

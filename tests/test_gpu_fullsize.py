@@ -88,3 +88,43 @@ def test_annulus_c3_full_size(B):
     mg = B.MGRIT(prob, T=T, Nt=Nt, m=8, tol=1e-12, pmg=dict(precision=0, tol=1e-13))
     U, st, _ = mg.run(u0)
     assert _rel(U.cpu().numpy(), seq) < 1e-10, st
+
+
+def test_grid_barrier_selftest_times_out_and_device_stays_usable(B):
+    """The grid-wide barrier of a fused level visit (one cooperative launch for
+    the F, C and F + residual phases): all CTAs pass it; when one CTA holds
+    back (a host-set flag), every wait gives up after its bound, the call
+    returns IGM_ERR_TIMEOUT, and the context still runs a fused solve."""
+    assert B.grid_barrier_selftest(nctas=16, hold=0) == 0
+    assert B.grid_barrier_selftest(nctas=16, wait_cycles=1 << 22, hold=1) == -5
+    assert "gave up" in B.lib().igm_last_error().decode()
+    prob = B.Problem(2, 8)
+    u0 = prob.project(S)
+    U, st, status = B.mgrit_solve(prob, u0, T=0.25, Nt=16, m=4, tol=1e-10, fused=1)
+    assert status == 0 and st["iters"] >= 1
+
+
+@pytest.mark.parametrize("p,precision", [(3, 0), (4, 1)])
+def test_fused_level_visits_equal_separate_launches(B, p, precision):
+    """Fused level visits (one cooperative launch per visit, grid barriers
+    between the phases) give bit-identical iterates, iteration counts and
+    residual histories to one launch per phase (Sec. 3's FCF relaxation),
+    on a level count with a partial interval, with and without graphs; and
+    fewer kernel launches."""
+    nel, T, Nt = 16, 1.0, 100
+    prob = B.Problem(p, nel)
+    u0, fhat = prob.project(S), prob.load_vector(S)
+    fc = np.array([C(n * T / Nt) for n in range(Nt + 1)])
+    out = {}
+    for fused in (0, 1):
+        for graphs in (0, 1):
+            mg = B.MGRIT(prob, T=T, Nt=Nt, m=4, tol=1e-10, fused=fused, graphs=graphs,
+                         pmg=dict(precision=precision, tol=1e-10))
+            U, st, _ = mg.run(u0, fhat, fc)
+            out[(fused, graphs)] = (U.cpu().numpy(), st)
+    ref_U, ref_st = out[(0, 0)]
+    for key, (U, st) in out.items():
+        assert np.array_equal(U, ref_U), key
+        assert st["iters"] == ref_st["iters"], key
+        assert np.array_equal(np.asarray(st["res_hist"]), np.asarray(ref_st["res_hist"])), key
+    assert out[(1, 1)][1]["launches"] < out[(0, 1)][1]["launches"]

@@ -8,14 +8,18 @@ S = lambda xi, eta, x, y: np.sin(np.pi * x) * np.sin(np.pi * y) + 0.3 * np.sin(3
 
 
 def test_gradient_matches_finite_differences():
+    """Back-propagation through the four 3 x 3 layers and three GELUs: the
+    weight gradients of every layer and the gradient with respect to the
+    network input equal central differences of the loss."""
     n = 7
     net = learned.ConvNet(n, channels=2, seed=3, zero_last=False)
     rng = np.random.default_rng(4)
     X = rng.standard_normal((2, n, n))
     Y = rng.standard_normal((2, n, n))
-    _, G = net.loss_and_grads(X, Y)
+    _, G, GX = net.loss_and_grads(X, Y, input_grad=True)
     h = 1e-6
-    for k, idx in ((0, (1, 0, 2, 3)), (1, (0, 1, 4, 0)), (2, (0, 1, 2, 2)), (1, (1, 1, 0, 4))):
+    for k, idx in ((0, (1, 0, 2, 1)), (1, (0, 1, 0, 0)), (2, (1, 0, 1, 2)), (3, (0, 1, 2, 2)),
+                   (1, (1, 1, 1, 1)), (3, (0, 0, 0, 1))):
         w0 = net.W[k][idx]
         net.W[k][idx] = w0 + h
         lp, _ = net.loss_and_grads(X, Y)
@@ -24,6 +28,45 @@ def test_gradient_matches_finite_differences():
         net.W[k][idx] = w0
         fd = (lp - lm) / (2 * h)
         assert abs(fd - G[k][idx]) <= 1e-7 * max(1.0, abs(fd)), (k, idx, fd, G[k][idx])
+    for idx in ((0, 3, 3), (1, 0, 6), (1, 4, 2)):
+        x0 = X[idx]
+        X[idx] = x0 + h
+        lp, _ = net.loss_and_grads(X, Y)
+        X[idx] = x0 - h
+        lm, _ = net.loss_and_grads(X, Y)
+        X[idx] = x0
+        fd = (lp - lm) / (2 * h)
+        assert abs(fd - GX[idx]) <= 1e-7 * max(1.0, abs(fd)), (idx, fd, GX[idx])
+
+
+def test_gelu_closed_form_and_derivative():
+    """g(z) = z Phi(z): g(0) = 0, g(1) = Phi(1), g(-1) = -(1 - Phi(1)) with the
+    tabulated Phi(1) = 0.8413447460685429; g(z) -> z and g(-z) -> 0 for large
+    z; g'(0) = 1/2 and g' against central differences."""
+    phi1 = 0.8413447460685429
+    z = np.array([0.0, 1.0, -1.0, 8.0, -8.0])
+    np.testing.assert_allclose(learned.gelu(z), [0.0, phi1, -(1.0 - phi1), 8.0, 0.0],
+                               rtol=1e-14, atol=1e-13)
+    assert learned.gelu_deriv(np.array(0.0)) == 0.5
+    zz = np.linspace(-4, 4, 17)
+    h = 1e-6
+    fd = (learned.gelu(zz + h) - learned.gelu(zz - h)) / (2 * h)
+    np.testing.assert_allclose(learned.gelu_deriv(zz), fd, rtol=0, atol=1e-8)
+
+
+def test_centre_tap_network_is_pointwise():
+    """With every kernel zero except its centre tap and one channel, the
+    convolutions are pointwise products and Phi_c(u)/s = x + w4 g(w3 g(w2
+    g(w1 x))) at every grid point."""
+    n = 5
+    net = learned.ConvNet(n, channels=1, seed=0, zero_last=False)
+    w = [0.7, -1.3, 0.9, 1.1]
+    for k in range(4):
+        net.W[k][:] = 0.0
+        net.W[k][0, 0, 1, 1] = w[k]
+    x = np.random.default_rng(5).uniform(-1, 1, (n, n))
+    want = x + w[3] * learned.gelu(w[2] * learned.gelu(w[1] * learned.gelu(w[0] * x)))
+    np.testing.assert_allclose(net.forward_normalised(x), want, rtol=1e-15, atol=1e-15)
 
 
 def test_zero_homogeneity_and_identity_start():
