@@ -395,6 +395,11 @@ cudaError_t launch_mgrit_sweep(int prec, const SweepArgs& a, int grid, long smem
 cudaError_t launch_mgrit_level(int prec, const SweepArgs& a, int grid, long smem, cudaStream_t st) {
   return prec ? launch_mgrit_level_f32(a, grid, smem, st) : launch_mgrit_level_f64(a, grid, smem, st);
 }
+cudaError_t launch_mgrit_batch(int prec, const BatchMember* mem, BatchState* st, int nmem,
+                               unsigned long long* ctl, int grid, long smem, cudaStream_t s) {
+  return prec ? launch_mgrit_batch_f32(mem, st, nmem, ctl, grid, smem, s)
+              : launch_mgrit_batch_f64(mem, st, nmem, ctl, grid, smem, s);
+}
 int mgrit_sweep_max_resident(int prec, long smem) {
   return prec ? mgrit_sweep_max_resident_f32(smem) : mgrit_sweep_max_resident_f64(smem);
 }

@@ -40,6 +40,56 @@ struct SweepArgs {
   long long bar_cycles;   // bound of one barrier wait in SM clocks
 };
 
+// ---------------------------------------------------------------------------
+// Device-scheduled batch of MGRIT solves (one persistent launch for many
+// independent problems).  Each member's run is a program of phases: A0 (the
+// first fine-level part), then B (coarse levels and the fine correction) and
+// A (a later fine-level part) repeated; every A-part ends with the stopping
+// test.  A phase is `grid` tasks (one per interval) of one sweep mode on one
+// level, the zeroing of a level's iterate, or the test.  Persistent CTAs
+// claim tasks of the members' current phases; the CTA that completes a
+// phase's last task moves the member to its next phase.
+// ---------------------------------------------------------------------------
+enum : int { BOP_SWEEP = 0, BOP_ZERO = 1, BOP_TEST = 2 };
+constexpr int kBatchHist = 256;   // residual norms kept per member
+
+struct BatchPhase {
+  int level, mode, grid, op;
+};
+
+struct BatchMember {
+  const SweepArgs* lv;     // [levels] arguments of every level's sweeps
+  const BatchPhase* prog;  // [nA0 + nB + nA]: A0, then B, then A
+  int nA0, nB, nA;
+  int nint0;               // fine-level C-intervals: entries of norms
+  const double* norms;     // [nint0] ||r_j||^2 written by the fine-level residual phase
+  double tol;
+  int max_iter;
+};
+
+struct BatchState {
+  unsigned long long word;   // (phase << 32) | next task of the phase
+  int done;                  // tasks of the current phase completed
+  int it;                    // coarse corrections done
+  int finished;
+  int nhist;
+  unsigned long long t_end;  // globaltimer (ns) at the end of the member's run
+  double hist[kBatchHist];
+};
+
+// Run the batch: nmem members (in the order of `mem`, which is also the order
+// in which idle CTAs look for work), `grid` persistent CTAs with `smem` bytes
+// of dynamic shared memory.  ctl: [0] progress count, [1] abort flag, [2]
+// start time (globaltimer ns); zeroed by the caller.  A CTA that finds no
+// work for kWaitCycles SM clocks while no task anywhere completes raises the
+// abort flag and every CTA returns.
+cudaError_t launch_mgrit_batch(int prec, const BatchMember* mem, BatchState* st, int nmem,
+                               unsigned long long* ctl, int grid, long smem, cudaStream_t st_);
+cudaError_t launch_mgrit_batch_f32(const BatchMember*, BatchState*, int, unsigned long long*, int,
+                                   long, cudaStream_t);
+cudaError_t launch_mgrit_batch_f64(const BatchMember*, BatchState*, int, unsigned long long*, int,
+                                   long, cudaStream_t);
+
 // prec: 0 = FP64 form, 1 = mixed form.  Each returns cudaGetLastError().
 cudaError_t launch_pmg_solve(int prec, const PmgD& P, int grid, long smem, cudaStream_t st,
                              const double* b, double* x, long ld, int ncycles, int* cycles_out,

@@ -35,6 +35,12 @@ cudaError_t launch_mgrit_level_f32(const SweepArgs& a, int grid, long smem, cuda
   return cudaLaunchKernelEx(&cfg, k_mgrit_sweep<1>, a);
 }
 
+cudaError_t launch_mgrit_batch_f32(const BatchMember* mem, BatchState* st, int nmem,
+                                   unsigned long long* ctl, int grid, long smem, cudaStream_t s) {
+  k_mgrit_batch<1><<<grid, kBlock, smem, s>>>(mem, st, nmem, ctl);
+  return cudaGetLastError();
+}
+
 int mgrit_sweep_max_resident_f32(long smem) {
   int dev = 0, sms = 0, per = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
@@ -53,6 +59,9 @@ cudaError_t set_smem_f32(long bytes) {
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute((const void*)k_mgrit_sweep<1>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute((const void*)k_mgrit_batch<1>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   return e;
 }

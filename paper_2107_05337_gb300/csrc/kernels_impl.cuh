@@ -10,14 +10,16 @@ namespace igm {
 
 // Dynamic shared memory: [record ring][mbarriers] then the CTA's arena when it
 // fits; otherwise the arena is this CTA's slice of the global scratch.
-__device__ __forceinline__ char* cta_setup(const PmgD& P, char* garena, Pipe& pp) {
+__device__ __forceinline__ char* cta_setup(const PmgD& P, char* garena, Pipe& pp,
+                                           int slot = -1) {
   extern __shared__ __align__(128) char dyn_smem[];
   pp.ring = dyn_smem;
   pp.bar = (uint64_t*)(dyn_smem + (size_t)P.nstage * P.slot_bytes);
   pp.nstage = P.nstage;
   pp.slot = P.slot_bytes;
   pipe_init(pp);
-  return P.arena_smem ? dyn_smem + P.ring_bytes : garena + (size_t)blockIdx.x * P.arena_bytes;
+  if (slot < 0) slot = (int)blockIdx.x;
+  return P.arena_smem ? dyn_smem + P.ring_bytes : garena + (size_t)slot * P.arena_bytes;
 }
 
 template <int PREC>
@@ -57,7 +59,7 @@ __device__ __forceinline__ void mgrit_step(const SweepArgs& a, Pipe& pp, char* a
                                            int n, bool residual, int j) {
   const PmgD& P = a.P;
   const int N = P.N;
-  double* rhs = a.scratch + (size_t)blockIdx.x * 2 * N;
+  double* rhs = a.scratch + (size_t)j * 2 * N;
   double* xr = rhs + N;
   double* tm = (PREC == 0) ? (double*)arena + P.o_u : (double*)((float*)arena + P.o_d);
   const double* u = a.W + (size_t)(n - 1) * N;
@@ -143,8 +145,8 @@ __device__ inline bool grid_barrier(unsigned* gb, int nctas, long long cycles, i
 // and has nothing to do in the C-point modes.
 template <int PREC>
 __device__ __forceinline__ void sweep_mode(const SweepArgs& a, Pipe& pp, char* arena, double* red,
-                                           int mode) {
-  const int j = blockIdx.x, m = a.m, N = a.P.N;
+                                           int mode, int j) {
+  const int m = a.m, N = a.P.N;
   const bool tail = j == a.nint;
   if (tail && (mode == MODE_C || mode == MODE_R)) return;
   int n0 = j * m + 1, n1 = tail ? a.Nl : j * m + m - 1;
@@ -193,12 +195,134 @@ __global__ void __launch_bounds__(kBlock) k_mgrit_sweep(SweepArgs a) {
   Pipe pp;
   char* arena = cta_setup(a.P, a.garena, pp);
   if (a.nmodes <= 0) {
-    sweep_mode<PREC>(a, pp, arena, red, a.mode);
+    sweep_mode<PREC>(a, pp, arena, red, a.mode, (int)blockIdx.x);
     return;
   }
   for (int q = 0; q < a.nmodes; ++q) {
     if (q > 0 && !grid_barrier(a.gbar, (int)gridDim.x, a.bar_cycles, a.status, false)) return;
-    sweep_mode<PREC>(a, pp, arena, red, a.modes[q]);
+    sweep_mode<PREC>(a, pp, arena, red, a.modes[q], (int)blockIdx.x);
+  }
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Phase pc of a member's program: A0, then B, A, B, A, ...
+__device__ __forceinline__ BatchPhase phase_at(const BatchMember& M, int pc) {
+  if (pc < M.nA0) return M.prog[pc];
+  return M.prog[M.nA0 + (pc - M.nA0) % (M.nB + M.nA)];
+}
+
+// Persistent CTAs of a device-scheduled batch of MGRIT solves.  Thread 0
+// looks for work: for each unfinished member in order it reads the member's
+// (phase, next task) word and claims the task by compare-and-swap while the
+// phase has tasks left.  The CTA runs the task (a sweep of one interval, a
+// slice of zeroing, or nothing for the stopping test); the CTA that completes
+// the last task of a phase advances the member: after the stopping test it
+// records the residual norm and either ends the member's run or counts the
+// coarse correction that follows.  No task waits for another: a CTA without
+// work polls (sleeping briefly) and gives up after kWaitCycles clocks in
+// which no task completed anywhere.
+template <int PREC>
+__global__ void __launch_bounds__(kBlock) k_mgrit_batch(const BatchMember* mem, BatchState* st,
+                                                        int nmem, unsigned long long* ctl) {
+  __shared__ double red[32];
+  __shared__ int s_m, s_pc, s_task;
+  volatile unsigned long long* vctl = ctl;
+  if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&ctl[2], 0ull, global_ns());
+  long long idle_since = -1;
+  unsigned long long seen = 0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_m = -1;
+      bool alive = false;
+      for (int i = 0; i < nmem && s_m < 0; ++i) {
+        if (*(volatile int*)&st[i].finished) continue;
+        alive = true;
+        unsigned long long w = *(volatile unsigned long long*)&st[i].word;
+        for (;;) {
+          const int pc = (int)(w >> 32), tk = (int)(w & 0xffffffffull);
+          if (tk >= phase_at(mem[i], pc).grid) break;
+          const unsigned long long old = atomicCAS(&st[i].word, w, w + 1ull);
+          if (old == w) {
+            s_m = i;
+            s_pc = pc;
+            s_task = tk;
+            break;
+          }
+          w = old;
+        }
+      }
+      if (s_m >= 0) {
+        idle_since = -1;
+        __threadfence();  // the results of the member's earlier phases
+      } else if (!alive || vctl[1] != 0ull) {
+        s_m = -2;
+      } else {
+        const unsigned long long pr = vctl[0];
+        const long long now = clock64();
+        if (idle_since < 0 || pr != seen) {
+          seen = pr;
+          idle_since = now;
+        } else if (now - idle_since > kWaitCycles) {
+          atomicExch(&ctl[1], 1ull);
+          s_m = -2;
+        }
+        if (s_m == -1) __nanosleep(500);
+      }
+    }
+    __syncthreads();
+    const int mi = s_m, pc = s_pc, task = s_task;
+    __syncthreads();
+    if (mi == -2) return;
+    if (mi < 0) continue;
+    const BatchMember& M = mem[mi];
+    const BatchPhase ph = phase_at(M, pc);
+    if (ph.op == BOP_SWEEP) {
+      const SweepArgs& a = M.lv[ph.level];
+      Pipe pp;
+      char* arena = cta_setup(a.P, a.garena, pp, task);
+      sweep_mode<PREC>(a, pp, arena, red, ph.mode, task);
+    } else if (ph.op == BOP_ZERO) {
+      const SweepArgs& a = M.lv[ph.level];
+      const size_t N = (size_t)a.P.N;
+      for (int row = task; row <= a.Nl; row += ph.grid) {
+        double* w = a.W + (size_t)row * N;
+        for (size_t i = threadIdx.x; i < N; i += blockDim.x) w[i] = 0.0;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();  // this task's results before its completion is counted
+      BatchState& S = st[mi];
+      if (atomicAdd(&S.done, 1) + 1 == ph.grid) {
+        bool finish = false;
+        if (ph.op == BOP_TEST) {
+          double rr = 0.0;
+          for (int j = 0; j < M.nint0; ++j) rr += M.norms[j];
+          const double rho = sqrt(rr);
+          if (S.nhist < kBatchHist) S.hist[S.nhist] = rho;
+          const double rho0 = S.nhist == 0 ? rho : S.hist[0];
+          S.nhist += 1;
+          finish = !(rho == rho) || rho == 0.0 || rho <= M.tol * rho0 || S.it >= M.max_iter;
+          if (!finish) S.it += 1;
+        }
+        S.done = 0;
+        __threadfence();
+        if (finish) {
+          S.t_end = global_ns();
+          __threadfence();
+          atomicExch(&S.finished, 1);
+        } else {
+          atomicExch(&S.word, (unsigned long long)(pc + 1) << 32);
+        }
+      }
+      atomicAdd(&ctl[0], 1ull);
+    }
+    __syncthreads();
   }
 }
 
