@@ -414,6 +414,26 @@ igm_status mgrit_run_batched(int nprob, mgrit_handle* const* mgs, const double* 
                              double* const* U, mgrit_stats* stats, float* latency_ms,
                              igm_stream s);
 
+/* The same batch as mgrit_run_batched in ONE persistent kernel launch, with
+ * no host scheduler: each member's run is a program of phases (the sweeps of
+ * Sec. 3's relaxation, residual, coarse visits and correction, and the
+ * stopping test after every fine-level residual), and one CTA per SM
+ * repeatedly claims a task (one interval of the current phase of a member;
+ * members are scanned in array order, so put the short ones first for
+ * shortest-job-first service); the CTA that completes a phase's last task
+ * moves that member on, and the stopping test runs on the device from the
+ * device-side residual norms.  No task waits for another; an idle CTA gives
+ * up (IGM_ERR_TIMEOUT) after about a second in which no task completed.
+ * Results are bit-identical to mgrit_run of each member.  All members must
+ * use the same precision and no learned coarse propagator.  latency_ms: per
+ * member, the time from the launch's start to the end of its run (device
+ * clock).  stats[i].launches = 1 (the batch's single launch).  There is no
+ * counterpart in the paper. */
+igm_status mgrit_run_batched_device(int nprob, mgrit_handle* const* mgs, const double* const* u0,
+                                    const double* const* fhat, const double* const* fcoef,
+                                    double* const* U, mgrit_stats* stats, float* latency_ms,
+                                    igm_stream s);
+
 /* ---------------------------------------------------------------------------
  * Learned coarse propagator Phi_c (no counterpart in the paper, whose coarse
  * levels rediscretise the time step, Sec. 3).  A convolutional network on the

@@ -95,6 +95,9 @@ EXPORTS = {
     "mgrit_run_batched": (c_int, [c_int, POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
                                   POINTER(c_void_p), POINTER(c_void_p), c_void_p,
                                   POINTER(ctypes.c_float), c_void_p]),
+    "mgrit_run_batched_device": (c_int, [c_int, POINTER(c_void_p), POINTER(c_void_p),
+                                         POINTER(c_void_p), POINTER(c_void_p), POINTER(c_void_p),
+                                         c_void_p, POINTER(ctypes.c_float), c_void_p]),
     "phic_create": (c_int, [c_int, c_int, ctypes.c_ulonglong, POINTER(c_void_p)]),
     "phic_destroy": (None, [c_void_p]),
     "phic_set_weights": (c_int, [c_void_p, POINTER(ctypes.c_float)]),
@@ -659,11 +662,13 @@ class Phic:
         return loss.value, gw, gx
 
 
-def mgrit_run_batched(handles, u0s, fhats=None, fcoefs=None, Us=None, check=True):
-    """Concurrent MGRIT solves of independent problems (mgrit_run_batched).
-    handles: MGRIT objects; u0s, fhats: CUDA float64 [N_i] (fhats entries may
-    be None); fcoefs: host arrays [Nt_i+1] or None.  Returns (Us, stats list,
-    latencies in ms, status)."""
+def mgrit_run_batched(handles, u0s, fhats=None, fcoefs=None, Us=None, check=True, device=False):
+    """Concurrent MGRIT solves of independent problems: mgrit_run_batched
+    (streams and a host scheduler), or with device=True
+    mgrit_run_batched_device (one persistent launch).  handles: MGRIT
+    objects; u0s, fhats: CUDA float64 [N_i] (fhats entries may be None);
+    fcoefs: host arrays [Nt_i+1] or None.  Returns (Us, stats list, latencies
+    in ms, status)."""
     torch = _torch()
     k = len(handles)
     if Us is None:
@@ -681,7 +686,8 @@ def mgrit_run_batched(handles, u0s, fhats=None, fcoefs=None, Us=None, check=True
         fc = arr([None if f is None else f.ctypes.data for f in keep])
     st = (MgritStats * k)()
     lat = (ctypes.c_float * k)()
-    status = lib().mgrit_run_batched(k, hs, u0p, fh, fc, Up, st, lat, _stream())
+    fn = lib().mgrit_run_batched_device if device else lib().mgrit_run_batched
+    status = fn(k, hs, u0p, fh, fc, Up, st, lat, _stream())
     if check:
         _check(status)
     return Us, [_stats(x) for x in st], np.array(lat[:], dtype=np.float64), status

@@ -2080,6 +2080,234 @@ extern "C" igm_status mgrit_run_batched(int nprob, mgrit_handle* const* mgs,
   return first;
 }
 
+// ---------------------------------------------------------------------------
+// Device-scheduled batch (one persistent launch): each member's run as a
+// program of phases, the same launches part_A / part_B / visit issue.
+// ---------------------------------------------------------------------------
+static void prog_partA(const mgrit_handle* mg, bool first, std::vector<BatchPhase>& v) {
+  const int m = mg->o.m, nint0 = mg->L[0].Nl / m, nf0 = f_grid(mg->L[0].Nl, m);
+  if (mg->o.relax == 1) {
+    if (first) v.push_back({0, MODE_F, nf0, BOP_SWEEP});
+    v.push_back({0, MODE_C, nint0, BOP_SWEEP});
+    v.push_back({0, MODE_FR, nf0, BOP_SWEEP});
+  } else {
+    v.push_back(first ? BatchPhase{0, MODE_FR, nf0, BOP_SWEEP} : BatchPhase{0, MODE_R, nint0, BOP_SWEEP});
+  }
+  v.push_back({0, 0, 1, BOP_TEST});
+}
+
+static void prog_zero(const mgrit_handle* mg, int l, std::vector<BatchPhase>& v) {
+  v.push_back({l, 0, std::min(64, mg->L[l].Nl + 1), BOP_ZERO});
+}
+
+static void prog_visit(const mgrit_handle* mg, int l, int kind, std::vector<BatchPhase>& v) {
+  const int nlev = (int)mg->L.size(), m = mg->o.m;
+  if (l == nlev - 1) {
+    v.push_back({l, MODE_SEQ, 1, BOP_SWEEP});
+    return;
+  }
+  const int ni = mg->L[l].Nl / m, nf = f_grid(mg->L[l].Nl, m);
+  if (mg->o.relax == 1) {
+    v.push_back({l, MODE_F, nf, BOP_SWEEP});
+    v.push_back({l, MODE_C, ni, BOP_SWEEP});
+  }
+  v.push_back({l, MODE_FR, nf, BOP_SWEEP});
+  prog_zero(mg, l + 1, v);
+  const int sub[3][2] = {{0, -1}, {1, 0}, {2, 2}};
+  for (int q = 0; q < 2; ++q) {
+    const int k = sub[kind][q];
+    if (k < 0 || (q == 1 && l + 1 == nlev - 1)) break;
+    prog_visit(mg, l + 1, k, v);
+  }
+  v.push_back({l, MODE_CF, nf, BOP_SWEEP});
+}
+
+static void prog_partB(const mgrit_handle* mg, std::vector<BatchPhase>& v) {
+  const int nlev = (int)mg->L.size(), kind = mg->o.cycle;
+  prog_zero(mg, 1, v);
+  for (int q = 0; q < 2; ++q) {
+    const int k = q == 0 ? kind : (kind == 1 ? 0 : (kind == 2 ? 2 : -1));
+    if (k < 0 || (q == 1 && nlev == 2)) break;
+    prog_visit(mg, 1, k, v);
+  }
+  v.push_back({0, MODE_CF, f_grid(mg->L[0].Nl, mg->o.m), BOP_SWEEP});
+}
+
+// The arguments of level l's sweeps (the mode is given per phase).
+static SweepArgs level_args(mgrit_handle* mg, int l, double* U, const double* fhat) {
+  const int nlev = (int)mg->L.size();
+  std::vector<Level>& L = mg->L;
+  SweepArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.P = L[l].h->d;
+  a.m = mg->o.m;
+  a.Nl = L[l].Nl;
+  a.nint = L[l].Nl / mg->o.m;
+  a.W = l == 0 ? U : L[l].W;
+  a.g = l > 0 ? L[l].g : nullptr;
+  if (l + 1 < nlev) {
+    a.Wc = L[l + 1].W;
+    a.gc = L[l + 1].g;
+    a.gnext = L[l + 1].g;
+  }
+  a.norms = l == 0 ? mg->norms : nullptr;
+  a.fhat = l == 0 ? fhat : nullptr;
+  a.fcoef = mg->dfcoef;
+  a.dt0 = L[0].dt;
+  a.theta = mg->o.theta;
+  a.scratch = mg->scratch;
+  a.garena = L[l].h->garena;
+  a.ncycles = l > 0 ? mg->o.coarse_cycles : 0;
+  a.counters = mg->counters;
+  a.status = mg->status;
+  return a;
+}
+
+extern "C" igm_status mgrit_run_batched_device(int nprob, mgrit_handle* const* mgs,
+                                               const double* const* u0, const double* const* fhat,
+                                               const double* const* fcoef, double* const* U,
+                                               mgrit_stats* stats, float* latency_ms,
+                                               igm_stream s) {
+  if (nprob < 0 || (nprob > 0 && (!mgs || !u0 || !U))) return fail(IGM_ERR_ARG, "null argument");
+  if (nprob == 0) return IGM_OK;
+  for (int i = 0; i < nprob; ++i) {
+    if (!mgs[i] || !u0[i] || !U[i]) return fail(IGM_ERR_ARG, "null member");
+    for (int k = 0; k < i; ++k)
+      if (mgs[i] == mgs[k]) return fail(IGM_ERR_ARG, "a handle appears twice in the batch");
+    if (mgs[i]->phic) return fail(IGM_ERR_ARG, "the device-scheduled batch has no learned coarse propagator");
+    if (mgs[i]->L[0].h->d.precision != mgs[0]->L[0].h->d.precision)
+      return fail(IGM_ERR_ARG, "all members of a device-scheduled batch need the same precision");
+  }
+  const int prec = mgs[0]->L[0].h->d.precision;
+  cudaStream_t st = (cudaStream_t)s;
+  auto t0 = std::chrono::steady_clock::now();
+  // every member's run starts as mgrit_run does: initial guess, source factors, counters
+  std::vector<BatchMember> hm(nprob);
+  std::vector<std::vector<SweepArgs>> args(nprob);
+  std::vector<std::vector<BatchPhase>> progs(nprob);
+  long smem = 0;
+  size_t nargs = 0, nph = 0;
+  for (int i = 0; i < nprob; ++i) {
+    mgrit_handle* mg = mgs[i];
+    const mgrit_opts& o = mg->o;
+    const int N = mg->ops->hi.N, nlev = (int)mg->L.size();
+    const double* fh = fhat ? fhat[i] : nullptr;
+    const double* fc = fcoef ? fcoef[i] : nullptr;
+    if (fh && !fc) return fail(IGM_ERR_ARG, "fhat given without fcoef");
+    if (!fc) fh = nullptr;
+    if (fh) CU(cudaMemcpyAsync(mg->dfcoef, fc, sizeof(double) * (o.Nt + 1), cudaMemcpyHostToDevice, st));
+    CU(cudaMemsetAsync(mg->counters, 0, 2 * sizeof(unsigned long long), st));
+    CU(cudaMemsetAsync(mg->status, 0, sizeof(int), st));
+    CU(cudaMemcpyAsync(U[i], u0[i], sizeof(double) * N, cudaMemcpyDeviceToDevice, st));
+    if (!o.initial_guess) CU(cudaMemsetAsync(U[i] + N, 0, sizeof(double) * (size_t)o.Nt * N, st));
+    for (int l = 0; l < nlev; ++l) {
+      args[i].push_back(level_args(mg, l, U[i], fh));
+      smem = std::max(smem, smem_of(mg->L[l].h));
+    }
+    std::vector<BatchPhase>& v = progs[i];
+    int nA0 = 0, nB = 0, nA = 0;
+    if (nlev == 1) {
+      v.push_back({0, MODE_SEQ, 1, BOP_SWEEP});
+      v.push_back({0, 0, 1, BOP_TEST});
+      nA0 = 2;
+    } else {
+      prog_partA(mg, true, v);
+      nA0 = (int)v.size();
+      prog_partB(mg, v);
+      nB = (int)v.size() - nA0;
+      prog_partA(mg, false, v);
+      nA = (int)v.size() - nA0 - nB;
+    }
+    hm[i].nA0 = nA0;
+    hm[i].nB = nB;
+    hm[i].nA = nA;
+    hm[i].nint0 = nlev == 1 ? 0 : mg->L[0].Nl / o.m;
+    hm[i].norms = mg->norms;
+    hm[i].tol = o.tol;
+    hm[i].max_iter = o.max_iter;
+    nargs += args[i].size();
+    nph += v.size();
+  }
+  // one upload: [members][states][level arguments][programs][control]
+  const size_t o_st = ((sizeof(BatchMember) * nprob + 255) / 256) * 256;
+  const size_t o_args = o_st + ((sizeof(BatchState) * nprob + 255) / 256) * 256;
+  const size_t o_prog = o_args + ((sizeof(SweepArgs) * nargs + 255) / 256) * 256;
+  const size_t o_ctl = o_prog + ((sizeof(BatchPhase) * nph + 255) / 256) * 256;
+  const size_t total = o_ctl + 256;
+  char* dbuf = nullptr;
+  CU(cudaMallocAsync((void**)&dbuf, total, st));
+  std::vector<char> hbuf(total, 0);
+  {
+    SweepArgs* da = (SweepArgs*)(dbuf + o_args);
+    BatchPhase* dp = (BatchPhase*)(dbuf + o_prog);
+    size_t ka = 0, kp = 0;
+    for (int i = 0; i < nprob; ++i) {
+      hm[i].lv = da + ka;
+      hm[i].prog = dp + kp;
+      std::memcpy(hbuf.data() + o_args + sizeof(SweepArgs) * ka, args[i].data(),
+                  sizeof(SweepArgs) * args[i].size());
+      std::memcpy(hbuf.data() + o_prog + sizeof(BatchPhase) * kp, progs[i].data(),
+                  sizeof(BatchPhase) * progs[i].size());
+      ka += args[i].size();
+      kp += progs[i].size();
+    }
+    std::memcpy(hbuf.data(), hm.data(), sizeof(BatchMember) * nprob);
+  }
+  CU(cudaMemcpyAsync(dbuf, hbuf.data(), total, cudaMemcpyHostToDevice, st));
+  // one persistent CTA per SM (a CTA of the solver holds a whole SM's registers)
+  int dev = 0, sms = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = std::max(1, sms);
+  BatchState* dst = (BatchState*)(dbuf + o_st);
+  unsigned long long* ctl = (unsigned long long*)(dbuf + o_ctl);
+  CU(launch_mgrit_batch(prec, (const BatchMember*)dbuf, dst, nprob, ctl, grid, smem, st));
+  g_launches++;
+  std::vector<BatchState> hs(nprob);
+  unsigned long long hctl[3] = {0, 0, 0};
+  CU(cudaMemcpyAsync(hs.data(), dst, sizeof(BatchState) * nprob, cudaMemcpyDeviceToHost, st));
+  CU(cudaMemcpyAsync(hctl, ctl, sizeof(hctl), cudaMemcpyDeviceToHost, st));
+  CU(cudaFreeAsync(dbuf, st));
+  CU(cudaStreamSynchronize(st));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  igm_status first = IGM_OK;
+  for (int i = 0; i < nprob; ++i) {
+    mgrit_handle* mg = mgs[i];
+    const int nlev = (int)mg->L.size();
+    unsigned long long hc[2] = {0, 0};
+    int hstat = 0;
+    CU(cudaMemcpy(hc, mg->counters, sizeof(hc), cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(&hstat, mg->status, sizeof(int), cudaMemcpyDeviceToHost));
+    const BatchState& S = hs[i];
+    const int nh = std::min(S.nhist, kBatchHist);
+    if (stats) {
+      mgrit_stats& t = stats[i];
+      std::memset(&t, 0, sizeof(t));
+      t.iters = S.it;
+      t.levels = nlev;
+      if (nlev > 1)
+        for (int k = 0; k < nh && k < 256; ++k) t.res_hist[k] = S.hist[k];
+      t.solves = (long)hc[0];
+      t.vcycles = (long)hc[1];
+      t.vcyc_mean = hc[0] ? (double)hc[1] / (double)hc[0] : 0.0;
+      t.seconds = secs;
+      t.setup_seconds = mg->setup_seconds;
+      t.launches = 1;
+    }
+    if (latency_ms) latency_ms[i] = S.finished ? (float)((double)(S.t_end - hctl[2]) * 1e-6) : -1.0f;
+    igm_status r = IGM_OK;
+    if (!S.finished || hctl[1]) r = fail(IGM_ERR_TIMEOUT, "the batch scheduler gave up waiting for work");
+    else if (hstat == ST_NUMERIC || (nh > 0 && !(S.hist[nh - 1] == S.hist[nh - 1])))
+      r = fail(IGM_ERR_NUMERIC, "NaN in a residual");
+    else if (hstat == ST_TIMEOUT) r = fail(IGM_ERR_TIMEOUT, "a bounded device wait gave up");
+    else if (hstat == ST_NOT_CONVERGED) r = fail(IGM_ERR_NOT_CONVERGED, "a spatial solve hit max_cycles");
+    else if (nlev > 1 && nh > 0 && !(S.hist[nh - 1] <= mg->o.tol * S.hist[0]) && S.hist[nh - 1] != 0.0)
+      r = fail(IGM_ERR_NOT_CONVERGED, "MGRIT hit max_iter");
+    if (first == IGM_OK && r != IGM_OK) first = r;
+  }
+  return first;
+}
+
 extern "C" igm_status mgrit_profile(const mgrit_handle* mg, int cap, int* count, int* level,
                                     int* grid, int* mode, float* ms, long* cycles) {
   if (!mg || !count) return fail(IGM_ERR_ARG, "null argument");
