@@ -88,10 +88,11 @@ def manufactured():
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# dominant kernel, averaged over the launches of one chosen-form solve of the
-# workload at its full size, from one ncu capture of that solve (the launch
-# list's metric pass); None until captured on the current kernel.
-NCU_DRAM_BYTES_PER_LAUNCH = {"heat_c2": None, "annulus_c3": None}
+# dominant kernel, averaged over the launches of one chosen-form solve per
+# order of the workload at its full size (the per-launch profiled solves of
+# --profile-only), from one single-pass ncu capture of that command.  Must be
+# re-captured whenever k_mgrit_sweep changes.
+NCU_DRAM_BYTES_PER_LAUNCH = {"heat_c2": 9.538e6, "annulus_c3": 1.077e9}
 
 
 def bytes_per_vcycle_dof(p, B):
@@ -796,6 +797,14 @@ def main():
         h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=0, tol=1e-10)) for p in orders}
         plain, U_plain = side_form(h, "plain")
         del h
+    # the chosen form with the p = 1 W-cycle in FP64 instead of FP32 (the
+    # alternative reading of which part of the cycle stays FP64)
+    w64, U_w64 = None, None
+    if not args.skip_plain:
+        h = {p: B.MGRIT(probs[p], **opts, coarse_cycles=1,
+                        pmg=dict(precision=1, tol=1e-10, autotune=1, hmg_fp64=1)) for p in orders}
+        w64, U_w64 = side_form(h, "w64")
+        del h
 
     # end to end through the C ABI with host buffers: H2D of u0, fhat (pinned),
     # solve, D2H of the final time level, every step
@@ -880,7 +889,8 @@ def main():
         seq = {job: f.result() for job, f in refs.items()}
         refs_ex.shutdown()
         errors = {}
-        for name, Uf in (("chosen", U_chosen), ("mixed", U_mixed), ("plain_fp64", U_plain)):
+        for name, Uf in (("chosen", U_chosen), ("mixed", U_mixed), ("plain_fp64", U_plain),
+                         ("chosen_fp64_w_cycle", U_w64)):
             if Uf is not None:
                 errors[name] = {p: rel_err(Uf[p], seq[("heat_c2", p, nel, Nt)]) for p in orders}
         if annulus is not None:
@@ -898,12 +908,14 @@ def main():
                                           "per coarse-time-level solve (fine level to 1e-10); "
                                           "sweep layouts autotuned at setup",
                            "mixed_form": "FP32 p-MG cycles with FP64 refinement, every level to 1e-10",
+                           "chosen_fp64_w_cycle_form": "the chosen form with the p=1 W-cycle in FP64",
                            "plain_form": "FP64 p-MG on every level to 1e-10",
                            "orders": "solved concurrently, one stream each",
                            "parallelism": f"replicas{world}" if world > 1 else "single GPU",
                            "l2": "flushed (256 MiB write) before every timed step"},
                 "mixed_only": mixed,
                 "plain_fp64": plain,
+                "chosen_fp64_w_cycle": w64,
                 "speedup_vs_plain": (value / plain["value"]) if plain else None,
                 "speedup_parts": ({"mixed_precision": mixed["value"] / plain["value"],
                                    "one_cycle_coarse_levels": value / mixed["value"]}

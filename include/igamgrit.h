@@ -186,6 +186,10 @@ typedef struct {
                              the working vectors in global memory (2, 5), or everything in
                              global memory (3, 6); pmg_setup returns IGM_ERR_ARG when the
                              forced layout does not fit in shared memory */
+  int hmg_fp64;           /* precision 1 only: 0 (default) the p = 1 W-cycle (Gauss--Seidel,
+                             residuals, bilinear transfers) in FP32 like the rest of the cycle,
+                             with the coarsest direct solve in FP64; 1 the whole W-cycle in
+                             FP64 (the order-p <-> order-1 transfers stay FP32) */
 } pmg_opts;
 
 typedef struct pmg_handle pmg_handle;

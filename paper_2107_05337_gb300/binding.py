@@ -31,7 +31,8 @@ class PmgOpts(ctypes.Structure):
     _fields_ = [("nu1", c_int), ("nu2", c_int), ("ilut_droptol", c_double),
                 ("ilut_fill", c_double), ("hmg_coarsest_nel", c_int), ("precision", c_int),
                 ("inner_cycles", c_int), ("tol", c_double), ("max_cycles", c_int),
-                ("trace", c_int), ("solver", c_int), ("autotune", c_int), ("layout", c_int)]
+                ("trace", c_int), ("solver", c_int), ("autotune", c_int), ("layout", c_int),
+                ("hmg_fp64", c_int)]
 
 
 class MgritOpts(ctypes.Structure):

@@ -427,6 +427,7 @@ extern "C" void pmg_default_opts(pmg_opts* o) {
   o->solver = 0;
   o->autotune = 0;
   o->layout = 0;
+  o->hmg_fp64 = 0;
 }
 
 static void gen_wcycle(int k, int last, std::vector<int>& ops) {
@@ -616,6 +617,7 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   if (!(o.tol >= 0.0)) return fail(IGM_ERR_ARG, "tol must be >= 0");
   if (o.solver != 0 && o.solver != 1) return fail(IGM_ERR_ARG, "solver must be 0 or 1");
   if (o.layout < 0 || o.layout > 6) return fail(IGM_ERR_ARG, "layout must be in [0, 6]");
+  if (o.hmg_fp64 != 0 && o.hmg_fp64 != 1) return fail(IGM_ERR_ARG, "hmg_fp64 must be 0 or 1");
   if (o.solver == 1) h->opts.precision = 0;  // CG runs in FP64
   h->c = kappa_dt;
   const Discretisation& hi = ops->hi;
@@ -725,7 +727,8 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
   for (int k = 0; k < d.nh; ++k) {
     const int nk = H[k].n;
     const int E = nk <= 32 ? 1 : (nk <= 64 ? 2 : (nk <= 128 ? 4 : 8));  // lanes' width in gs_sweep
-    const int es_g = o.precision == 0 ? 8 : 4;
+    const bool g64 = o.precision == 0 || o.hmg_fp64;   // GS coefficients in FP64
+    const int es_g = g64 ? 8 : 4;
     const int rec_bytes = G_NCOEF * E * 32 * es_g;  // multiple of 128
     std::vector<char> recs((size_t)rec_bytes * nk, 0);
     for (int by = 0; by < nk; ++by) {
@@ -741,7 +744,7 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
         const int lane = r / E, e = r % E;
         for (int q = 0; q < G_NCOEF; ++q) {
           const size_t idx = (size_t)(q * E + e) * 32 + lane;
-          if (o.precision == 0) ((double*)rec)[idx] = g[q];
+          if (g64) ((double*)rec)[idx] = g[q];
           else ((float*)rec)[idx] = (float)g[q];
         }
       }
@@ -784,7 +787,24 @@ static igm_status pmg_setup_ex(const iga_ops* ops, double kappa_dt, double expl_
     d.h[k].ot = d.o_u + hsum; hsum = align4(hsum + H[k].n * H[k].n);
   }
   d.o_tr = d.o_u + hsum;
-  off += std::max(std::max(align4(2 * N) + align4(N), hsum + align4(n * lo.n)),
+  int coarse_part = hsum + align4(n * lo.n);
+  d.hmg64 = (o.precision == 1 && o.hmg_fp64) ? 1 : 0;
+  if (d.hmg64) {
+    // the h-level vectors in doubles (offsets in doubles from the arena's
+    // start; o_u is a multiple of 4 floats), then the FP32 transfer
+    // temporary and the order-1 vector between transfers and W-cycle
+    int hd = 0;
+    for (int k = 0; k < d.nh; ++k) {
+      const int nk2 = H[k].n * H[k].n;
+      d.h[k].ox = d.o_u / 2 + hd; hd = align4(hd + nk2);
+      d.h[k].ob = d.o_u / 2 + hd; hd = align4(hd + nk2);
+      d.h[k].ot = d.o_u / 2 + hd; hd = align4(hd + nk2);
+    }
+    d.o_tr = d.o_u + 2 * hd;
+    d.o_c1 = d.o_tr + align4(n * lo.n);
+    coarse_part = 2 * hd + align4(n * lo.n) + align4(lo.N);
+  }
+  off += std::max(std::max(align4(2 * N) + align4(N), coarse_part),
                   o.solver == 1 ? 4 * align4(N) : 0);  // CG: p, q and two operator temporaries
   h->arena_bytes = (long)off * es;
   d.arena_bytes = h->arena_bytes;

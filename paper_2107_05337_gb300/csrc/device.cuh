@@ -88,6 +88,11 @@ struct PmgD {
   double tol;
   // arena layout (element offsets in the smoothing precision)
   int o_r, o_d, o_t, o_u, o_tr;  // o_tr: transfer temporary
+  // mixed form with the p = 1 W-cycle in FP64 (hmg64 = 1): the h-level
+  // offsets ox, ob, ot are in doubles from the arena's start, the GS records
+  // and the W-cycle run in FP64, and o_c1 (floats) holds the order-1
+  // vector between the FP32 transfers and the FP64 W-cycle
+  int hmg64, o_c1;
   long arena_bytes;
   // dynamic shared memory: [record ring: nstage * slot_bytes][mbarriers: ring slots
   // (kMaxStage), sweep row completion (kRowBars)]

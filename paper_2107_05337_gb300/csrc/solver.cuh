@@ -138,28 +138,73 @@ __device__ bool wcycle(const PmgD& P, Pipe& pp, T* A, int* status) {
   return true;
 }
 
-// r_1 = (M_1^L)^{-1} P^T t into h-level 0's b, and x_0 = 0 (Sec. 4, step 2).
+// r_1 = (M_1^L)^{-1} P^T t into r1 (Sec. 4, step 2).
+template <typename T>
+__device__ void restrict_p1_to(const PmgD& P, const T* t, T* A, T* r1) {
+  if (P.tp)
+    transfer_tp<T, false>(P.n, P.n1, P.wP, P.PTis, Prec<T>::PTb(P), Prec<T>::M1L(P), t, A + P.o_tr,
+                          r1);
+  else
+    csr_scaled<T, false>(P.N1, P.PTptr, P.PTcol, Prec<T>::PTv(P), Prec<T>::M1L(P), t, r1);
+}
+
+// r_1 into h-level 0's b, and x_0 = 0.
 template <typename T>
 __device__ void restrict_p1(const PmgD& P, const T* t, T* A) {
   const HLevelD& H0 = P.h[0];
-  if (P.tp)
-    transfer_tp<T, false>(P.n, P.n1, P.wP, P.PTis, Prec<T>::PTb(P), Prec<T>::M1L(P), t, A + P.o_tr,
-                          A + H0.ob);
-  else
-    csr_scaled<T, false>(P.N1, P.PTptr, P.PTcol, Prec<T>::PTv(P), Prec<T>::M1L(P), t, A + H0.ob);
+  restrict_p1_to<T>(P, t, A, A + H0.ob);
   IGM_FOR_CTA(i, P.N1) A[H0.ox + i] = 0;
   __syncthreads();
 }
 
-// x += (M_p^L)^{-1} P e_1 with e_1 = h-level 0's x (Sec. 4, step 4).
+// x += (M_p^L)^{-1} P e_1 (Sec. 4, step 4).
+template <typename T>
+__device__ void prolong_p1_from(const PmgD& P, T* x, T* A, const T* e1) {
+  if (P.tp)
+    transfer_tp<T, true>(P.n1, P.n, P.wP, P.Pjs, Prec<T>::Pb(P), Prec<T>::MpL(P), e1, A + P.o_tr,
+                         x);
+  else
+    csr_scaled<T, true>(P.N, P.Pptr, P.Pcol, Prec<T>::Pv(P), Prec<T>::MpL(P), e1, x);
+}
+
+// with e_1 = h-level 0's x
 template <typename T>
 __device__ void prolong_p1(const PmgD& P, T* x, T* A) {
+  prolong_p1_from<T>(P, x, A, A + P.h[0].ox);
+}
+
+// Steps 2-4 of the mixed form's cycle with the W-cycle in FP64 (hmg64): the
+// FP32 restriction into the order-1 buffer, then h-level 0's b (FP64) from
+// it and x_0 = 0, the FP64 W-cycle, and the FP32 prolongation of its result.
+__device__ inline bool coarse_correction_fp64(const PmgD& P, Pipe& pp, const float* t, float* x,
+                                              float* A, int* status) {
   const HLevelD& H0 = P.h[0];
-  if (P.tp)
-    transfer_tp<T, true>(P.n1, P.n, P.wP, P.Pjs, Prec<T>::Pb(P), Prec<T>::MpL(P), A + H0.ox,
-                         A + P.o_tr, x);
-  else
-    csr_scaled<T, true>(P.N, P.Pptr, P.Pcol, Prec<T>::Pv(P), Prec<T>::MpL(P), A + H0.ox, x);
+  double* A64 = (double*)A;
+  float* c1 = A + P.o_c1;
+  {
+    PhaseClock pc(P.trace);
+    restrict_p1_to<float>(P, t, A, c1);
+    IGM_FOR_CTA(i, P.N1) {
+      A64[H0.ob + i] = (double)c1[i];
+      A64[H0.ox + i] = 0.0;
+    }
+    __syncthreads();
+    pc.stop(3);
+  }
+  {
+    PhaseClock pc(P.trace);
+    const bool ok = wcycle<double>(P, pp, A64, status);
+    pc.stop(4);
+    if (!ok) return false;
+  }
+  {
+    PhaseClock pc(P.trace);
+    IGM_FOR_CTA(i, P.N1) c1[i] = (float)A64[H0.ox + i];
+    __syncthreads();
+    prolong_p1_from<float>(P, x, A, c1);
+    pc.stop(5);
+  }
+  return true;
 }
 
 // One p-multigrid cycle (Sec. 4, steps 1-5) on A x = b in precision T.
@@ -197,6 +242,10 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
     residualT<T>(P, b, x, t, tm, tk);
     pc.stop(1);
   }
+  if (sizeof(T) == 4 && P.hmg64) {
+    // steps 2-4 with the W-cycle in FP64
+    if (!coarse_correction_fp64(P, pp, (const float*)t, (float*)x, (float*)A, status)) return false;
+  } else {
   {
     PhaseClock pc(P.trace);
     restrict_p1<T>(P, t, A);
@@ -214,6 +263,7 @@ __device__ bool pmg_cycle(const PmgD& P, Pipe& pp, const T* b, T* x, T* A, bool 
     PhaseClock pc(P.trace);
     prolong_p1<T>(P, x, A);
     pc.stop(5);
+  }
   }
   // step 5: post-smoothing
   for (int s = 0; s < P.nu2; ++s) {

@@ -288,3 +288,41 @@ def test_batched_fp32_apply_rejects_curved_map(B):
     prob = B.Problem(2, 8, "quarter_annulus")
     with pytest.raises(B.IgmError):
         prob.apply_f32("M", torch.zeros((1, prob.N), dtype=torch.float32, device="cuda"))
+
+
+@pytest.mark.parametrize("geom,p,nel", [("unit_square", 4, 64), ("quarter_annulus", 3, 16)])
+def test_mixed_form_with_fp64_w_cycle(B, geom, p, nel):
+    """pmg_opts.hmg_fp64: the mixed form with the whole p = 1 W-cycle in FP64
+    (Sec. 4, step 3; the transfers stay FP32).  One refinement step equals the
+    oracle's FP64 cycle to FP32 rounding, converged solves equal the direct
+    solution to 1e-10, and an MGRIT run equals sequential stepping."""
+    import scipy.sparse as sp
+    import torch
+    from scipy.sparse.linalg import splu
+    from oracle import pmg as opmg
+    from paper_2107_05337_gb300 import inputs
+    _cuda = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    c = 1.0 / 256
+    prob = B.Problem(p, nel, geom)
+    hi, lo = assembly.problem(p, nel, geometry.get(geom))
+    P = opmg.PMG(hi, lo, c)
+    g = B.PMG(prob, c, precision=1, tol=1e-12, hmg_fp64=1)
+    Bm = inputs.random_block(71, prob.N, 2)
+    X = _cuda(np.zeros_like(Bm))
+    g.solve(_cuda(Bm), X, ncycles=1)
+    X = X.cpu().numpy()
+    for k in range(2):
+        x, _ = P.solve(Bm[k], np.zeros(prob.N), ncycles=1)
+        assert _rel(X[k], x) < 2e-5, k
+    X = _cuda(np.zeros_like(Bm))
+    g.solve(_cuda(Bm), X)
+    X = X.cpu().numpy()
+    lu = splu(sp.csc_matrix(P.A))
+    for k in range(2):
+        assert _rel(X[k], lu.solve(Bm[k])) < 1e-10, k
+    if geom == "unit_square":
+        d = assembly.Discretisation(p, 16, geometry.UnitSquare())
+        seq = timestep.sequential(d.M, d.K, 1.0, 1.0, 64, d.project(S), d.load_vector(S), C)
+        U, st = _gpu(B, p, 16, 1.0, 64, m=4, tol=1e-12,
+                     pmg=dict(tol=1e-13, precision=1, hmg_fp64=1))
+        assert _rel(U, seq) < 1e-10, st
