@@ -26,7 +26,8 @@ Other modes (one JSON line each): --annulus (the curved-map workload annulus_c3)
 --batch (the uneven 64-problem batch, latency percentiles), --learned (two-level
 MGRIT with the trained coarse propagator against backward Euler and the plain
 form), --spmm (the batched FP32 operator apply against the HBM copy bandwidth),
---profile-only (per-launch grids and V-cycles, to pair with ncu), and
+--trace (the per-phase clock split of one p-multigrid cycle), --profile-only (per-launch grids
+and V-cycles, to pair with ncu), and
 --impl reference (the oracle timed on the host cores).
 """
 import argparse
@@ -63,6 +64,9 @@ def parse():
                     help="skip the annulus_c3 sub-measurement of the default run")
     ap.add_argument("--sjf", type=int, default=1,
                     help="--batch: 1 = shortest-job-first stream priorities (default), 0 = equal")
+    ap.add_argument("--batch-order", default="shortest", choices=["shortest", "longest"],
+                    help="--batch: the order in which the persistent launch's idle CTAs look "
+                         "for work (shortest first: low latency; longest first: short makespan)")
     ap.add_argument("--learned", action="store_true",
                     help="learned_c4: two-level MGRIT with the learned coarse propagator against "
                          "backward Euler on the coarse level, one JSON line (not the headline)")
@@ -75,6 +79,9 @@ def parse():
     ap.add_argument("--batch", action="store_true",
                     help="the uneven 64-problem batch (batch_c5): per-problem latency p50/p99 "
                          "and batch throughput, one JSON line (not the headline metric)")
+    ap.add_argument("--trace", action="store_true",
+                    help="per-phase clock split of one p-multigrid cycle (pmg_trace) at 64 x 64 "
+                         "elements, p = 2..5, both forms, with the untraced cycle time")
     ap.add_argument("--profile-only", action="store_true",
                     help="one chosen-form solve per order and exit (for ncu launch lists)")
     return ap.parse_args()
@@ -405,7 +412,7 @@ def run_batch(args):
 
     # one persistent launch for the whole batch (members in shortest-first
     # order, the order in which idle CTAs look for work)
-    dev_order = order
+    dev_order = order if args.batch_order == "shortest" else order[::-1]
     lat_d, span_d, iters_d = measure(True, [handles[i] for i in dev_order],
                                      [u0s[i] for i in dev_order], [Us[i] for i in dev_order])
     # streams and a host scheduler, with shortest-job-first stream priorities
@@ -427,8 +434,8 @@ def run_batch(args):
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "makespan_ms": makespan, "setup_s": round(setup_s, 2),
-            "scheduling": "one persistent launch (device work claiming, members scanned shortest "
-                          "first, device-side stopping tests)",
+            "scheduling": f"one persistent launch (device work claiming, members scanned "
+                          f"{args.batch_order} first, device-side stopping tests)",
             "host_scheduled": host_sched,
             "form": "mixed precision, one p-MG cycle per coarse-level solve, autotuned sweep layouts",
             "iters": {"min": int(min(iters)), "max": int(max(iters))}, "members": len(members)}
@@ -625,6 +632,46 @@ def run_annulus(args):
         print(json.dumps(res))
 
 
+def run_trace(args):
+    """One right-hand side on 64 x 64 elements, c = 1/256 (a heat_c2 fine-level step), p = 2..5,
+    mixed and FP64 forms: the microseconds per cycle of every solver phase from pmg_trace
+    (SM clocks of thread 0 at the maximum SM clock, 10 fixed cycles after 2 untimed), and the
+    cycle time without tracing (CUDA events).  One JSON line per order and form."""
+    import torch
+    from paper_2107_05337_gb300 import binding as B
+    from paper_2107_05337_gb300 import inputs
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    mhz = peaks["sm_max_mhz"] if peaks else 2070.0
+    for p in (2, 3, 4, 5):
+        prob = B.Problem(p, 64)
+        for prec in (1, 0):
+            g = B.PMG(prob, 1.0 / 256, precision=prec, trace=1, autotune=1)
+            g2 = B.PMG(prob, 1.0 / 256, precision=prec, autotune=1)
+            Bm = torch.as_tensor(inputs.random_block(1, prob.N, 1), dtype=torch.float64,
+                                 device="cuda")
+            X = torch.zeros_like(Bm)
+            g.solve(Bm, X, ncycles=2)
+            g.trace(reset=True)
+            X.zero_()
+            g.solve(Bm, X, ncycles=10)
+            tr = g.trace(reset=True)
+            X.zero_()
+            g2.solve(Bm, X, ncycles=10)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            X.zero_()
+            e0.record()
+            g2.solve(Bm, X, ncycles=10)
+            e1.record()
+            torch.cuda.synchronize()
+            print(json.dumps({"p": p, "form": "mixed" if prec else "fp64", "layout": g2.layout(),
+                              "us_per_cycle": round(e0.elapsed_time(e1) * 1e3 / 10, 1),
+                              "trace_us_per_cycle": {k: round(v / mhz / 10, 1)
+                                                     for k, v in tr.items() if v}}))
+
+
 def run_spmm(args):
     """(M + c K) applied to 8192 FP32 columns of the 64 x 64-element unit square
     (one column per time point of a long interval), p = 2..5: bytes moved
@@ -668,6 +715,8 @@ def main():
         return run_reference(args)
     if args.spmm:
         return run_spmm(args)
+    if args.trace:
+        return run_trace(args)
     if args.annulus:
         return run_annulus(args)
     if args.learned:
