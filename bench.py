@@ -684,9 +684,10 @@ def run_spmm(args):
     torch.cuda.set_device(0)
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    ncol = 8192
-    for p in (2, 3, 4, 5):
-        prob = B.Problem(p, 64)
+    for nel, p in [(64, q) for q in (2, 3, 4, 5)] + [(128, q) for q in (2, 3, 4, 5)]:
+        # h = 1/128 (n > 84 grid lines): the row-strip form; fewer columns, same bytes order
+        ncol = 8192 if nel == 64 else 2048
+        prob = B.Problem(p, nel)
         ld = (prob.N + 3) // 4 * 4   # 16-byte aligned columns: the streamed path
         X = [torch.randn((ncol, ld), dtype=torch.float32, device="cuda") for _ in range(2)]
         for _ in range(3):
@@ -702,7 +703,9 @@ def run_spmm(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         gbs = 2 * 4 * prob.N * ncol / (ms * 1e-3) / 1e9
-        print(json.dumps({"kernel": "k_spmm32 (iga_apply_f32)", "p": p, "N": prob.N, "columns": ncol,
+        print(json.dumps({"kernel": "k_spmm32 (iga_apply_f32)" if prob.n <= 84 else
+                          "k_spmm32_strip (iga_apply_f32, row strips)", "p": p, "nel": nel,
+                          "N": prob.N, "columns": ncol,
                           "ms_per_call": round(ms, 4), "achieved_gbs": round(gbs, 1),
                           "peak_gbs": peak, "frac": round(gbs / peak, 3),
                           "peak_source": "measured" if peaks else "fallback",

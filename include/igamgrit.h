@@ -141,9 +141,11 @@ igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, d
  * group streams a column in and contracts along xi while the other contracts
  * the previous column along eta).  The operator of Eq. (los) applied to a
  * block of right-hand sides such as the time points of an interval.
- * IGM_ERR_ARG on the curved map, or when the n x n grid (n = N^(1/2)) does not
- * fit the shared-memory layouts (n > 84, or a device with less shared memory
- * than the plan needs; iga_apply_f32_layout reports the plan). */
+ * Grids the persistent layouts do not hold (n > 84; iga_apply_f32_layout
+ * reports the plan) are applied by a row-strip form instead: each CTA stages
+ * a strip of grid rows with p halo rows above and below for a group of
+ * columns (lower throughput; the h = 1/128 grids).  IGM_ERR_ARG on the curved
+ * map, or when not even one grid row fits in shared memory. */
 igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x, float* y,
                          long ld, igm_stream s);
 

@@ -1237,10 +1237,16 @@ extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs,
   if (which == 1) cf = SpmmCoef{1, 0, 0, 1, 0, 1, 1, 0};
   if (which == 2) cf = SpmmCoef{1, 0, 0, 1, 1, cf32, cf32, 0};
   const size_t smem_max = (size_t)dev_smem_optin();
-  if (spmm32_slots(n, p, smem_max) < 2) return fail(IGM_ERR_ARG, "grid too large for iga_apply_f32");
   int sms = 0, dev = 0;
   CU(cudaGetDevice(&dev));
   CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (spmm32_slots(n, p, smem_max) < 2) {
+    // grids beyond the persistent layouts: the row-strip form
+    if (spmm32_strip_rows(n, p, smem_max) < 1) return fail(IGM_ERR_ARG, "grid too large for iga_apply_f32");
+    CU(launch_spmm32_strip(n, p, nrhs, ops->bM32, ops->bK32, cf, x, y, ld, sms, smem_max, st));
+    g_launches++;
+    return IGM_OK;
+  }
   const int grid = std::min(nrhs, sms);
   CU(launch_spmm32(n, p, nrhs, ops->bM32, ops->bK32, cf, x, y, ld, grid, smem_max, st));
   g_launches++;

@@ -27,6 +27,7 @@
 // tap is an immediate address offset.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <type_traits>
 
 #include "device.cuh"
@@ -247,6 +248,104 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------------------
+// Row-strip form for grids the persistent layouts do not hold (n > 84, e.g.
+// h = 1/128): CTA (s, c) takes grid rows [s SR, s SR + SR) of columns c,
+// c + gridDim.y, ...; per column it stages the strip's rows plus p halo rows
+// above and below (zero outside the grid and in p padding columns each
+// side), forms (tm, tk) for all of them along xi, then y for the strip's
+// rows along eta.  The halo rows' (tm, tk) are recomputed by the
+// neighbouring strips (factor (SR + 2p) / SR of stage-1 work).
+// ---------------------------------------------------------------------------
+constexpr int kStripThreads = 256;
+
+template <int W>
+__global__ void __launch_bounds__(kStripThreads) k_spmm32_strip(int n, int nrhs, int SR,
+                                                                const float* __restrict__ M1,
+                                                                const float* __restrict__ K1,
+                                                                SpmmCoef cf,
+                                                                const float* __restrict__ x,
+                                                                float* __restrict__ y, long ld) {
+  constexpr int p = (W - 1) / 2;
+  extern __shared__ __align__(16) float sm[];
+  const int RS = SR + 2 * p, XW = n + 2 * p;
+  float* xs = sm;                               // [RS][XW]: x[r0 - p + q][ix - p] at [q][ix]
+  float2* tt = (float2*)(sm + ((RS * XW + 1) & ~1));  // [RS][n]: (tm, tk)
+  const int r0 = blockIdx.x * SR;
+  const int rows = min(SR, n - r0);
+  for (int b = blockIdx.y; b < nrhs; b += gridDim.y) {
+    const float* xb = x + (size_t)b * ld;
+    for (int i = threadIdx.x; i < RS * XW; i += kStripThreads) {
+      const int q = i / XW, c = i % XW;
+      const int iy = r0 - p + q, ix = c - p;
+      xs[i] = (iy >= 0 && iy < n && ix >= 0 && ix < n) ? xb[(size_t)iy * n + ix] : 0.0f;
+    }
+    __syncthreads();
+    // stage 1 (along xi) for every staged row
+    for (int i = threadIdx.x; i < RS * n; i += kStripThreads) {
+      const int q = i / n, ix = i % n;
+      const float* xr = xs + q * XW + ix;   // x[.][ix - p + o] at xr[o]
+      float am = 0.0f, ak = 0.0f;
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        const float m = M1[ix * W + o], kv = K1[ix * W + o];
+        am = fmaf(fmaf(cf.xk, kv, cf.xm * m), xr[o], am);
+        ak = fmaf(fmaf(cf.wk, kv, cf.wm * m), xr[o], ak);
+      }
+      tt[i] = make_float2(am, ak);
+    }
+    __syncthreads();
+    // stage 2 (along eta) for the strip's rows
+    float* yb = y + (size_t)b * ld;
+    for (int i = threadIdx.x; i < rows * n; i += kStripThreads) {
+      const int j = i / n, ix = i % n, iy = r0 + j;
+      float acc = 0.0f;
+#pragma unroll
+      for (int o = 0; o < W; ++o) {
+        const float m = M1[iy * W + o], kv = K1[iy * W + o];
+        const float2 t = tt[(j + o) * n + ix];   // row iy - p + o of the grid
+        acc = fmaf(fmaf(cf.yk, kv, cf.ym * m), t.x, acc);
+        acc = fmaf(fmaf(cf.zk, kv, cf.zm * m), t.y, acc);
+      }
+      yb[(size_t)iy * n + ix] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// strip height and shared bytes of the strip form (SR = 0: does not fit)
+int strip_plan(int n, int p, size_t smem_max, size_t* bytes) {
+  const size_t budget = smem_max < (size_t)96 * 1024 ? smem_max : (size_t)96 * 1024;
+  const int W = 2 * p + 1;
+  for (int SR = 64; SR >= 1; SR /= 2) {
+    const size_t RS = SR + 2 * p, XW = n + 2 * p;
+    const size_t b = 4 * (((RS * XW + 1) & ~(size_t)1) + 2 * RS * (size_t)n);
+    if (b <= budget) {
+      *bytes = b;
+      return W > 0 ? SR : 0;
+    }
+  }
+  *bytes = 0;
+  return 0;
+}
+
+template <int W>
+cudaError_t launch_strip_w(int n, int nrhs, const float* M1, const float* K1, SpmmCoef cf,
+                           const float* x, float* y, long ld, int sms, size_t smem_max,
+                           cudaStream_t st) {
+  size_t bytes = 0;
+  const int SR = strip_plan(n, (W - 1) / 2, smem_max, &bytes);
+  if (!SR) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_spmm32_strip<W>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return e;
+  const int strips = (n + SR - 1) / SR;
+  const int cg = std::max(1, std::min(nrhs, (2 * sms + strips - 1) / strips));
+  k_spmm32_strip<W><<<dim3(strips, cg), kStripThreads, bytes, st>>>(n, nrhs, SR, M1, K1, cf, x,
+                                                                     y, ld);
+  return cudaGetLastError();
+}
+
 constexpr int kCaps[] = {68, 84};  // J*G limits of the two layouts
 
 template <int W, int NC>
@@ -342,6 +441,26 @@ int spmm32_slots(int n, int p, size_t smem_max) {
     case 8: return slots_w<17>(n, smem_max);
     default: return 0;
   }
+}
+
+cudaError_t launch_spmm32_strip(int n, int p, int nrhs, const float* M1, const float* K1,
+                                SpmmCoef cf, const float* x, float* y, long ld, int sms,
+                                size_t smem_max, cudaStream_t st) {
+  switch (p) {
+    case 2: return launch_strip_w<5>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    case 3: return launch_strip_w<7>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    case 4: return launch_strip_w<9>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    case 5: return launch_strip_w<11>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    case 6: return launch_strip_w<13>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    case 7: return launch_strip_w<15>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    case 8: return launch_strip_w<17>(n, nrhs, M1, K1, cf, x, y, ld, sms, smem_max, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+int spmm32_strip_rows(int n, int p, size_t smem_max) {
+  size_t bytes = 0;
+  return (p >= 2 && p <= 8 && n >= 1) ? strip_plan(n, p, smem_max, &bytes) : 0;
 }
 
 cudaError_t launch_spmm32(int n, int p, int nrhs, const float* M1, const float* K1, SpmmCoef cf,

@@ -21,6 +21,13 @@ cudaError_t launch_spmm32(int n, int p, int nrhs, const float* M1, const float* 
                           cudaStream_t st);
 // copy ring depth the kernel would use for an n x n grid (0: does not fit)
 int spmm32_slots(int n, int p, size_t smem_max);
+// The row-strip form for grids the persistent layouts do not hold: strips of
+// spmm32_strip_rows(n, p, smem_max) grid rows (0: does not fit either), a grid
+// of strips x column groups sized from the SM count `sms`.
+cudaError_t launch_spmm32_strip(int n, int p, int nrhs, const float* M1, const float* K1,
+                                SpmmCoef cf, const float* x, float* y, long ld, int sms,
+                                size_t smem_max, cudaStream_t st);
+int spmm32_strip_rows(int n, int p, size_t smem_max);
 // The shared-memory plan for an n x n grid: out[7] = {grid-line cap of the
 // layout (0: does not fit), ring depth, grid lines per thread J, padded x row
 // stride, (tm, tk) row stride in pairs, (tm, tk) rows, dynamic shared bytes}.

@@ -326,3 +326,26 @@ def test_mixed_form_with_fp64_w_cycle(B, geom, p, nel):
         U, st = _gpu(B, p, 16, 1.0, 64, m=4, tol=1e-12,
                      pmg=dict(tol=1e-13, precision=1, hmg_fp64=1))
         assert _rel(U, seq) < 1e-10, st
+
+
+@pytest.mark.parametrize("p,nel", [(5, 128), (2, 100)])
+def test_batched_fp32_apply_row_strips_beyond_84_lines(B, p, nel):
+    """Grids the persistent layouts do not hold (n = nel + p - 2 > 84: the
+    h = 1/128 grids of batch_c5) go through the row-strip form; every column
+    against the oracle's assembled M + c K (Sec. 2, Eq. (los)), a ragged last
+    strip and more columns than column groups."""
+    import torch
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    assert d.n > 84
+    c = 1.0 / 512
+    X = np.random.default_rng(9).standard_normal((5, d.N))
+    want = ((d.M + c * d.K) @ X.T).T
+    prob = B.Problem(p, nel)
+    Y = prob.apply_f32("A", torch.as_tensor(X, dtype=torch.float32, device="cuda"), c=c)
+    got = Y.double().cpu().numpy()
+    err = np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)
+    assert err.max() < 2e-6, err
+    for which, A in (("M", d.M), ("K", d.K)):
+        Y = prob.apply_f32(which, torch.as_tensor(X[:2], dtype=torch.float32, device="cuda"))
+        w = (A @ X[:2].T).T
+        assert np.linalg.norm(Y.double().cpu().numpy() - w) / np.linalg.norm(w) < 2e-6, which
