@@ -673,21 +673,25 @@ def run_trace(args):
 
 
 def run_spmm(args):
-    """(M + c K) applied to 8192 FP32 columns of the 64 x 64-element unit square
-    (one column per time point of a long interval), p = 2..5: bytes moved
-    (one read of x, one write of y) over the CUDA-event time, against the
-    measured HBM copy bandwidth.  286 MB in and out per call at p = 4, far above
-    L2; the timed calls alternate between two input blocks.  Columns are padded to
-    a multiple of four floats (the streamed kernel needs 16-byte aligned columns)."""
+    """(M + c K) applied to a block of FP32 columns (one column per time point of a
+    long interval), p = 2..5, on the unit square and on the quarter annulus with
+    64 x 64 elements (8192 columns) and 128 x 128 elements (2048 columns): bytes
+    moved (one read of x, one write of y; on the annulus also the FP32 stencils)
+    over the CUDA-event time, against the measured HBM copy bandwidth.  286 MB in
+    and out per call at p = 4, h = 1/64, far above L2; the timed calls alternate
+    between two input blocks.  Columns are padded to a multiple of four floats."""
     import torch
     from paper_2107_05337_gb300 import binding as B
     torch.cuda.set_device(0)
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
-    for nel, p in [(64, q) for q in (2, 3, 4, 5)] + [(128, q) for q in (2, 3, 4, 5)]:
-        # h = 1/128 (n > 84 grid lines): the row-strip form; fewer columns, same bytes order
+    cases = [("unit_square", nel, q) for nel in (64, 128) for q in (2, 3, 4, 5)]
+    cases += [("quarter_annulus", nel, q) for nel in (64, 128) for q in (2, 3, 4, 5)]
+    for geom, nel, p in cases:
+        # h = 1/128: fewer columns (same order of bytes per call); on the unit square
+        # n > 84 grid lines take the row-strip form
         ncol = 8192 if nel == 64 else 2048
-        prob = B.Problem(p, nel)
+        prob = B.Problem(p, nel, geom)
         ld = (prob.N + 3) // 4 * 4   # 16-byte aligned columns: the streamed path
         X = [torch.randn((ncol, ld), dtype=torch.float32, device="cuda") for _ in range(2)]
         for _ in range(3):
@@ -702,14 +706,21 @@ def run_spmm(args):
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
-        gbs = 2 * 4 * prob.N * ncol / (ms * 1e-3) / 1e9
-        print(json.dumps({"kernel": "k_spmm32 (iga_apply_f32)" if prob.n <= 84 else
-                          "k_spmm32_strip (iga_apply_f32, row strips)", "p": p, "nel": nel,
+        Q = (2 * p + 1) ** 2
+        curved = geom != "unit_square"
+        # x read and y written per column; on the curved map also the FP32 M and K
+        # stencils (read once per call)
+        nbytes = 2 * 4 * prob.N * ncol + (2 * 4 * Q * prob.N if curved else 0)
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        kern = ("k_spmm32_curved (iga_apply_f32, assembled stencils)" if curved else
+                "k_spmm32 (iga_apply_f32)" if prob.n <= 84 else
+                "k_spmm32_strip (iga_apply_f32, row strips)")
+        print(json.dumps({"kernel": kern, "geometry": geom, "p": p, "nel": nel,
                           "N": prob.N, "columns": ncol,
                           "ms_per_call": round(ms, 4), "achieved_gbs": round(gbs, 1),
                           "peak_gbs": peak, "frac": round(gbs / peak, 3),
                           "peak_source": "measured" if peaks else "fallback",
-                          "flops_per_unknown": 4 * (2 * p + 1) * 2}))
+                          "flops_per_unknown": 2 * Q if curved else 4 * (2 * p + 1) * 2}))
 
 
 def main():

@@ -133,19 +133,24 @@ igm_status iga_project(const iga_ops* ops, const double* fq, double* out, igm_st
 igm_status iga_apply(const iga_ops* ops, int which, int nrhs, const double* x, double* y,
                      long ld, igm_stream s);
 
-/* Batched FP32 apply on the affine map (the unit square): y_b = M x_b
- * (which = 0), K x_b (1) or (M + c K) x_b (2) for b < nrhs, x, y DEVICE
- * [nrhs][ld] FP32, ld >= N, any alignment; c is rounded to FP32.  Sum
- * factorisation (Sec. 2: M = M1 (x) M1, K = K1 (x) M1 + M1 (x) K1) in
- * shared memory: one persistent CTA per SM pipelines its columns (one warp
- * group streams a column in and contracts along xi while the other contracts
- * the previous column along eta).  The operator of Eq. (los) applied to a
- * block of right-hand sides such as the time points of an interval.
- * Grids the persistent layouts do not hold (n > 84; iga_apply_f32_layout
- * reports the plan) are applied by a row-strip form instead: each CTA stages
- * a strip of grid rows with p halo rows above and below for a group of
- * columns (lower throughput; the h = 1/128 grids).  IGM_ERR_ARG on the curved
- * map, or when not even one grid row fits in shared memory. */
+/* Batched FP32 apply: y_b = M x_b (which = 0), K x_b (1) or (M + c K) x_b
+ * (2) for b < nrhs, x, y DEVICE [nrhs][ld] FP32, ld >= N, any alignment, x
+ * and y not overlapping; c is rounded to FP32.  The operator of Eq. (los)
+ * applied to a block of right-hand sides such as the time points of an
+ * interval.
+ * Affine map (the unit square): sum factorisation (Sec. 2: M = M1 (x) M1,
+ * K = K1 (x) M1 + M1 (x) K1) in shared memory: one persistent CTA per SM
+ * pipelines its columns (one warp group streams a column in and contracts
+ * along xi while the other contracts the previous column along eta).  Grids
+ * the persistent layouts do not hold (n > 84; iga_apply_f32_layout reports
+ * the plan) are applied by a row-strip form instead: each CTA stages a strip
+ * of grid rows with p halo rows above and below for a group of columns (the
+ * h = 1/128 grids); IGM_ERR_ARG when not even one grid row fits in shared
+ * memory.
+ * Curved map (a B-spline geometry, Sec. 2: M and K assembled): the
+ * (2p+1)^2-point stencils of every grid point, held in FP32 on the device
+ * since iga_assemble, coefficients of cm M + ck K formed once per CTA and
+ * applied to four columns at a time. */
 igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x, float* y,
                          long ld, igm_stream s);
 

@@ -400,7 +400,7 @@ class Problem:
 
     def apply_f32(self, which, X, c=0.0):
         """Y = M X, K X or (M + c K) X (which = 'M', 'K', 'A') on FP32 columns X [nrhs, N]
-        (unit square only)."""
+        (sum factorisation on the unit square, assembled stencils on a curved map)."""
         torch = _torch()
         if X.dim() != 2:
             raise ValueError("apply_f32: X must be [nrhs, ld] with ld >= N")

@@ -102,6 +102,7 @@ struct iga_ops {
   // device copies
   double *bM64 = nullptr, *bK64 = nullptr, *sM64 = nullptr, *sK64 = nullptr;
   float *bM32 = nullptr, *bK32 = nullptr;
+  float *sMq32 = nullptr, *sKq32 = nullptr;   // curved map: FP32 stencils, [(2p+1)^2][N]
   std::vector<double> qpts, qwdet;
 };
 
@@ -289,6 +290,18 @@ extern "C" igm_status iga_assemble(const iga_desc* desc, iga_ops** out) {
   }
   ops->sM64 = up.put(ops->hi.M.val);
   ops->sK64 = up.put(ops->hi.K.val);
+  if (!g.affine) {
+    // the batched FP32 apply reads coefficient q of all points contiguously
+    const int N = ops->hi.N, Q = ops->hi.M.width() * ops->hi.M.width();
+    std::vector<float> tm((size_t)Q * N), tk((size_t)Q * N);
+    for (int i = 0; i < N; ++i)
+      for (int q = 0; q < Q; ++q) {
+        tm[(size_t)q * N + i] = (float)ops->hi.M.val[(size_t)i * Q + q];
+        tk[(size_t)q * N + i] = (float)ops->hi.K.val[(size_t)i * Q + q];
+      }
+    ops->sMq32 = up.put(tm);
+    ops->sKq32 = up.put(tk);
+  }
   if (up.err != cudaSuccess) return fail(IGM_ERR_CUDA, cudaGetErrorString(up.err));
   *out = ops.release();
   return IGM_OK;
@@ -1226,10 +1239,20 @@ extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs,
                                     float* y, long ld, igm_stream s) {
   if (!ops || (nrhs > 0 && (!x || !y))) return fail(IGM_ERR_ARG, "null argument");
   if (which < 0 || which > 2 || nrhs < 0 || ld < ops->hi.N) return fail(IGM_ERR_ARG, "bad which/nrhs/ld");
-  if (!ops->geom.affine) return fail(IGM_ERR_ARG, "iga_apply_f32 needs the affine (unit square) map");
   if (nrhs == 0) return IGM_OK;
   const int n = ops->hi.n, p = ops->hi.p;
   cudaStream_t st = (cudaStream_t)s;
+  int sms = 0, dev = 0;
+  CU(cudaGetDevice(&dev));
+  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  if (!ops->geom.affine) {
+    // curved map: the assembled stencils, y = (cm M + ck K) x
+    const float cm = which == 1 ? 0.0f : 1.0f, ck = which == 0 ? 0.0f : which == 1 ? 1.0f : (float)c;
+    CU(launch_spmm32_curved(n, p, nrhs, which == 1 ? nullptr : ops->sMq32,
+                            which == 0 ? nullptr : ops->sKq32, cm, ck, x, y, ld, sms, st));
+    g_launches++;
+    return IGM_OK;
+  }
   // y = (Y2 (x) X1 + Z2 (x) W1) x with each factor a M1 + b K1:
   //   M = M1 (x) M1;  K = K1 (x) M1 + M1 (x) K1;  M + c K = (M1 + c K1) (x) M1 + c M1 (x) K1
   const float cf32 = (float)c;
@@ -1237,9 +1260,6 @@ extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs,
   if (which == 1) cf = SpmmCoef{1, 0, 0, 1, 0, 1, 1, 0};
   if (which == 2) cf = SpmmCoef{1, 0, 0, 1, 1, cf32, cf32, 0};
   const size_t smem_max = (size_t)dev_smem_optin();
-  int sms = 0, dev = 0;
-  CU(cudaGetDevice(&dev));
-  CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   if (spmm32_slots(n, p, smem_max) < 2) {
     // grids beyond the persistent layouts: the row-strip form
     if (spmm32_strip_rows(n, p, smem_max) < 1) return fail(IGM_ERR_ARG, "grid too large for iga_apply_f32");

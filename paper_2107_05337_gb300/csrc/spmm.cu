@@ -58,6 +58,12 @@ __device__ __forceinline__ void cp_async4_if(uint32_t dst, const float* src, int
       "{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q cp.async.ca.shared.global [%0], [%1], 4;\n}"
       ::"r"(dst), "l"(src), "r"(on) : "memory");
 }
+// 4-byte copy, zero-filled when on == 0 (src-size 0: nothing is read)
+__device__ __forceinline__ void cp_async4_zfill(uint32_t dst, const float* src, int on) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src),
+               "r"(on ? 4 : 0)
+               : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -250,79 +256,107 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // ---------------------------------------------------------------------------
 // Row-strip form for grids the persistent layouts do not hold (n > 84, e.g.
-// h = 1/128): CTA (s, c) takes grid rows [s SR, s SR + SR) of columns c,
-// c + gridDim.y, ...; per column it stages the strip's rows plus p halo rows
-// above and below (zero outside the grid and in p padding columns each
-// side), forms (tm, tk) for all of them along xi, then y for the strip's
-// rows along eta.  The halo rows' (tm, tk) are recomputed by the
-// neighbouring strips (factor (SR + 2p) / SR of stage-1 work).
+// h = 1/128): CTA (s, g) takes grid rows [s SR, s SR + SR) of columns g,
+// g + gridDim.y, ...  Per column it stages the strip's rows plus p halo rows
+// above and below (zero outside the grid, p zero padding columns each side;
+// two stages, the next column copied by 4-byte cp.async while the current one
+// is contracted).  Thread t owns grid column ix = t (+ blockDim, ...) and walks
+// the staged rows q: stage 1 turns row q into the pair (tm, tk) at ix with the
+// (X1, W1) band pair of ix in registers; the pairs of the last 2p + 1 rows sit
+// in a register window, and once it is full stage 2 forms y of grid row
+// r0 + q - 2p with the (Y2, Z2) band pairs of that row (shared-memory
+// broadcasts).  Both stages use packed FMAs.  The halo rows' pairs are
+// recomputed by the neighbouring strips (a factor (SR + 2p) / SR on stage 1).
 // ---------------------------------------------------------------------------
-constexpr int kStripThreads = 256;
-
 template <int W>
-__global__ void __launch_bounds__(kStripThreads) k_spmm32_strip(int n, int nrhs, int SR,
-                                                                const float* __restrict__ M1,
-                                                                const float* __restrict__ K1,
-                                                                SpmmCoef cf,
-                                                                const float* __restrict__ x,
-                                                                float* __restrict__ y, long ld) {
+__global__ void __launch_bounds__(512) k_spmm32_strip(int n, int nrhs, int SR,
+                                                      const float* __restrict__ M1,
+                                                      const float* __restrict__ K1, SpmmCoef cf,
+                                                      const float* __restrict__ x,
+                                                      float* __restrict__ y, long ld) {
   constexpr int p = (W - 1) / 2;
   extern __shared__ __align__(16) float sm[];
-  const int RS = SR + 2 * p, XW = n + 2 * p;
-  float* xs = sm;                               // [RS][XW]: x[r0 - p + q][ix - p] at [q][ix]
-  float2* tt = (float2*)(sm + ((RS * XW + 1) & ~1));  // [RS][n]: (tm, tk)
+  const int RS = SR + 2 * p, XW = n + 2 * p, STAGE = RS * XW;
+  float2* c2 = (float2*)sm;                 // [SR][W]: (Y2, Z2) of grid row r0 + j, tap o
+  float* xs = sm + 2 * SR * W;              // [2][RS][XW]: x[r0 - p + q][c - p] at [q][c]
   const int r0 = blockIdx.x * SR;
   const int rows = min(SR, n - r0);
-  for (int b = blockIdx.y; b < nrhs; b += gridDim.y) {
+  const int T = blockDim.x;
+  for (int i = threadIdx.x; i < SR * W; i += T) {
+    const int j = i / W, o = i - j * W, iy = min(r0 + j, n - 1);
+    const float m = M1[iy * W + o], k = K1[iy * W + o];
+    c2[i] = make_float2(fmaf(cf.yk, k, cf.ym * m), fmaf(cf.zk, k, cf.zm * m));
+  }
+  const uint32_t xbase = (uint32_t)__cvta_generic_to_shared(xs);
+  auto stage = [&](int b, int s) {
     const float* xb = x + (size_t)b * ld;
-    for (int i = threadIdx.x; i < RS * XW; i += kStripThreads) {
-      const int q = i / XW, c = i % XW;
+    const uint32_t base = xbase + 4u * (uint32_t)(s * STAGE);
+    for (int i = threadIdx.x; i < STAGE; i += T) {
+      const int q = i / XW, c = i - q * XW;
       const int iy = r0 - p + q, ix = c - p;
-      xs[i] = (iy >= 0 && iy < n && ix >= 0 && ix < n) ? xb[(size_t)iy * n + ix] : 0.0f;
+      const int on = iy >= 0 && iy < n && ix >= 0 && ix < n;
+      cp_async4_zfill(base + 4u * (uint32_t)i, on ? xb + (size_t)iy * n + ix : x, on);
     }
+  };
+  int b = blockIdx.y;
+  if (b < nrhs) stage(b, 0);
+  cp_async_commit();
+  for (int t = 0; b < nrhs; b += gridDim.y, ++t) {
+    if (b + (int)gridDim.y < nrhs) stage(b + gridDim.y, (t + 1) & 1);
+    cp_async_commit();
+    cp_async_wait<1>();
     __syncthreads();
-    // stage 1 (along xi) for every staged row
-    for (int i = threadIdx.x; i < RS * n; i += kStripThreads) {
-      const int q = i / n, ix = i % n;
-      const float* xr = xs + q * XW + ix;   // x[.][ix - p + o] at xr[o]
-      float am = 0.0f, ak = 0.0f;
-#pragma unroll
-      for (int o = 0; o < W; ++o) {
-        const float m = M1[ix * W + o], kv = K1[ix * W + o];
-        am = fmaf(fmaf(cf.xk, kv, cf.xm * m), xr[o], am);
-        ak = fmaf(fmaf(cf.wk, kv, cf.wm * m), xr[o], ak);
-      }
-      tt[i] = make_float2(am, ak);
-    }
-    __syncthreads();
-    // stage 2 (along eta) for the strip's rows
+    const float* xq = xs + (t & 1) * STAGE;
     float* yb = y + (size_t)b * ld;
-    for (int i = threadIdx.x; i < rows * n; i += kStripThreads) {
-      const int j = i / n, ix = i % n, iy = r0 + j;
-      float acc = 0.0f;
+    for (int ix0 = 0; ix0 < n; ix0 += T) {
+      const int ix = min(ix0 + (int)threadIdx.x, n - 1);
+      const bool mine = ix0 + (int)threadIdx.x < n;
+      float2 a1[W];   // (X1, W1) of grid column ix, tap o
 #pragma unroll
       for (int o = 0; o < W; ++o) {
-        const float m = M1[iy * W + o], kv = K1[iy * W + o];
-        const float2 t = tt[(j + o) * n + ix];   // row iy - p + o of the grid
-        acc = fmaf(fmaf(cf.yk, kv, cf.ym * m), t.x, acc);
-        acc = fmaf(fmaf(cf.zk, kv, cf.zm * m), t.y, acc);
+        const float m = M1[ix * W + o], k = K1[ix * W + o];
+        a1[o] = make_float2(fmaf(cf.xk, k, cf.xm * m), fmaf(cf.wk, k, cf.wm * m));
       }
-      yb[(size_t)iy * n + ix] = acc;
+      float2 win[W];  // (tm, tk) of staged row q at win[q % W]
+      for (int q0 = 0; q0 < RS; q0 += W) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+          const int q = q0 + k;
+          if (q < RS) {
+            const float* xr = xq + q * XW + ix;   // x[.][ix - p + o] at xr[o]
+            float2 acc = __fmul2_rn(a1[0], make_float2(xr[0], xr[0]));
+#pragma unroll
+            for (int o = 1; o < W; ++o) acc = __ffma2_rn(a1[o], make_float2(xr[o], xr[o]), acc);
+            win[k] = acc;
+            const int j = q - 2 * p;   // output row r0 + j needs staged rows j .. j + 2p
+            if (j >= 0 && j < rows) {
+              const float2* cj = c2 + j * W;
+              float2 s2 = __fmul2_rn(cj[0], win[(k + 1) % W]);
+#pragma unroll
+              for (int o = 1; o < W; ++o) s2 = __ffma2_rn(cj[o], win[(k + 1 + o) % W], s2);
+              if (mine) yb[(size_t)(r0 + j) * n + ix] = s2.x + s2.y;
+            }
+          }
+        }
+      }
     }
     __syncthreads();
   }
+  cp_async_wait<0>();
 }
 
-// strip height and shared bytes of the strip form (SR = 0: does not fit)
-int strip_plan(int n, int p, size_t smem_max, size_t* bytes) {
-  const size_t budget = smem_max < (size_t)96 * 1024 ? smem_max : (size_t)96 * 1024;
+// strip height, threads and shared bytes of the strip form (SR = 0: does not fit)
+int strip_plan(int n, int p, size_t smem_max, size_t* bytes, int* threads) {
   const int W = 2 * p + 1;
-  for (int SR = 64; SR >= 1; SR /= 2) {
-    const size_t RS = SR + 2 * p, XW = n + 2 * p;
-    const size_t b = 4 * (((RS * XW + 1) & ~(size_t)1) + 2 * RS * (size_t)n);
-    if (b <= budget) {
-      *bytes = b;
-      return W > 0 ? SR : 0;
+  *threads = std::min(512, (n + 31) / 32 * 32);
+  for (const size_t budget : {std::min(smem_max, (size_t)100 * 1024), smem_max}) {
+    for (int SR = 32; SR >= 1; SR /= 2) {
+      const size_t RS = SR + 2 * p, XW = n + 2 * p;
+      const size_t b = 4 * (2 * (size_t)SR * W + 2 * RS * XW);
+      if (b <= budget) {
+        *bytes = b;
+        return SR;
+      }
     }
   }
   *bytes = 0;
@@ -334,15 +368,138 @@ cudaError_t launch_strip_w(int n, int nrhs, const float* M1, const float* K1, Sp
                            const float* x, float* y, long ld, int sms, size_t smem_max,
                            cudaStream_t st) {
   size_t bytes = 0;
-  const int SR = strip_plan(n, (W - 1) / 2, smem_max, &bytes);
+  int threads = 0;
+  const int SR = strip_plan(n, (W - 1) / 2, smem_max, &bytes, &threads);
   if (!SR) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_spmm32_strip<W>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
   if (e != cudaSuccess) return e;
   const int strips = (n + SR - 1) / SR;
-  const int cg = std::max(1, std::min(nrhs, (2 * sms + strips - 1) / strips));
-  k_spmm32_strip<W><<<dim3(strips, cg), kStripThreads, bytes, st>>>(n, nrhs, SR, M1, K1, cf, x,
-                                                                     y, ld);
+  // about four CTAs per SM over the launch
+  const int cg = std::max(1, std::min(nrhs, (4 * sms + strips - 1) / strips));
+  k_spmm32_strip<W><<<dim3(strips, cg), threads, bytes, st>>>(n, nrhs, SR, M1, K1, cf, x, y, ld);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Curved map (an assembled (2p+1)^2 stencil per grid point, Sec. 2: M and K
+// of a B-spline geometry are not Kronecker products).  CTA (tile, g) takes an
+// 8 x 32 tile of grid points; each thread owns one point and keeps its
+// (2p+1)^2 FP32 coefficients a = cm M + ck K in registers (p <= 5; read from
+// global memory per tap above that), loaded once and reused for every column
+// the CTA visits.  Columns go four at a time, interleaved in shared memory as
+// float4 over the tile plus p halo rows and columns (zero outside the grid),
+// so one 128-bit load feeds four FMAs; the next group of four is staged by
+// 4-byte cp.async while the current one is contracted (two stages).
+// ---------------------------------------------------------------------------
+constexpr int kCurvTR = 8, kCurvTC = 32, kCurvThreads = kCurvTR * 32;
+
+
+template <int W>
+__global__ void __launch_bounds__(kCurvThreads) k_spmm32_curved(
+    int n, int nrhs, const float* __restrict__ Mq, const float* __restrict__ Kq, float cm,
+    float ck, const float* __restrict__ x, float* __restrict__ y, long ld) {
+  constexpr int p = (W - 1) / 2, Q = W * W;
+  constexpr bool kReg = Q <= 121;
+  constexpr int HR = kCurvTR + 2 * p, HC = kCurvTC + 2 * p, STAGE = HR * HC;
+  extern __shared__ __align__(16) float4 xs4[];   // [2][HR][HC]: (iy0 - p + r, ix0 - p + c)
+  const int tilesx = (n + kCurvTC - 1) / kCurvTC;
+  const int ix0 = (blockIdx.x % tilesx) * kCurvTC, iy0 = (blockIdx.x / tilesx) * kCurvTR;
+  const int lane = threadIdx.x & 31, wr = threadIdx.x >> 5;
+  const int ix = ix0 + lane, iy = iy0 + wr;
+  const bool mine = ix < n && iy < n;
+  const size_t N = (size_t)n * n;
+  const size_t pt = mine ? (size_t)iy * n + ix : 0;
+  // coefficient q (entry (q / W, q % W) of the point's stencil) of cm M + ck K
+  auto coef = [&](int q) {
+    float a = 0.0f;
+    if (Mq) a = cm * __ldg(Mq + q * N + pt);
+    if (Kq) a = fmaf(ck, __ldg(Kq + q * N + pt), a);
+    return a;
+  };
+  float v[kReg ? Q : 1];
+  if constexpr (kReg) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) v[q] = coef(q);
+  }
+  const int ngroups = (nrhs + 3) / 4;
+  const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(xs4);
+  auto stage = [&](int g, int s) {
+    const uint32_t base = sbase + (uint32_t)(s * STAGE) * 16u;
+    for (int e = threadIdx.x; e < 4 * STAGE; e += kCurvThreads) {
+      const int b = e & 3, pos = e >> 2, r = pos / HC, c = pos - r * HC;
+      const int jy = iy0 - p + r, jx = ix0 - p + c, col = 4 * g + b;
+      const int on = jy >= 0 && jy < n && jx >= 0 && jx < n && col < nrhs;
+      const float* src = on ? x + (size_t)col * ld + (size_t)jy * n + jx : x;
+      cp_async4_zfill(base + 4u * (uint32_t)e, src, on);
+    }
+  };
+  int g = blockIdx.y;
+  if (g < ngroups) stage(g, 0);
+  cp_async_commit();
+  for (int t = 0; g < ngroups; g += gridDim.y, ++t) {
+    if (g + (int)gridDim.y < ngroups) stage(g + gridDim.y, (t + 1) & 1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const float4* xt = xs4 + (t & 1) * STAGE + wr * HC + lane;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if constexpr (!kReg) {
+      // coefficients from global memory: one stencil row at a time
+#pragma unroll 1
+      for (int dy = 0; dy < W; ++dy) {
+#pragma unroll
+        for (int dx = 0; dx < W; ++dx) {
+          const float a = coef(dy * W + dx);
+          const float4 u = xt[dy * HC + dx];
+          acc.x = fmaf(a, u.x, acc.x);
+          acc.y = fmaf(a, u.y, acc.y);
+          acc.z = fmaf(a, u.z, acc.z);
+          acc.w = fmaf(a, u.w, acc.w);
+        }
+      }
+    }
+#pragma unroll
+    for (int dy = 0; dy < W; ++dy) {
+#pragma unroll
+      for (int dx = 0; dx < W; ++dx) {
+        if constexpr (kReg) {
+          const float a = v[dy * W + dx];
+          const float4 u = xt[dy * HC + dx];
+          acc.x = fmaf(a, u.x, acc.x);
+          acc.y = fmaf(a, u.y, acc.y);
+          acc.z = fmaf(a, u.z, acc.z);
+          acc.w = fmaf(a, u.w, acc.w);
+        }
+      }
+    }
+    if (mine) {
+      const float r[4] = {acc.x, acc.y, acc.z, acc.w};
+#pragma unroll
+      for (int b = 0; b < 4; ++b)
+        if (4 * g + b < nrhs) y[(size_t)(4 * g + b) * ld + pt] = r[b];
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+}
+
+template <int W>
+cudaError_t launch_curved_w(int n, int nrhs, const float* Mq, const float* Kq, float cm, float ck,
+                            const float* x, float* y, long ld, int sms, cudaStream_t st) {
+  constexpr int p = (W - 1) / 2;
+  const size_t bytes = 2 * sizeof(float4) * (size_t)(kCurvTR + 2 * p) * (kCurvTC + 2 * p);
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_spmm32_curved<W>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+  }
+  const int tiles = ((n + kCurvTC - 1) / kCurvTC) * ((n + kCurvTR - 1) / kCurvTR);
+  const int ngroups = (nrhs + 3) / 4;
+  // about four CTAs per SM over the launch; each loads its coefficients once
+  const int cg = std::max(1, std::min(ngroups, (4 * sms + tiles - 1) / tiles));
+  k_spmm32_curved<W><<<dim3(tiles, cg), kCurvThreads, bytes, st>>>(n, nrhs, Mq, Kq, cm, ck, x, y,
+                                                                   ld);
   return cudaGetLastError();
 }
 
@@ -460,7 +617,24 @@ cudaError_t launch_spmm32_strip(int n, int p, int nrhs, const float* M1, const f
 
 int spmm32_strip_rows(int n, int p, size_t smem_max) {
   size_t bytes = 0;
-  return (p >= 2 && p <= 8 && n >= 1) ? strip_plan(n, p, smem_max, &bytes) : 0;
+  int threads = 0;
+  return (p >= 2 && p <= 8 && n >= 1) ? strip_plan(n, p, smem_max, &bytes, &threads) : 0;
+}
+
+cudaError_t launch_spmm32_curved(int n, int p, int nrhs, const float* Mq, const float* Kq,
+                                 float cm, float ck, const float* x, float* y, long ld, int sms,
+                                 cudaStream_t st) {
+  if (n < 1 || (long)n * n > ld) return cudaErrorInvalidValue;
+  switch (p) {
+    case 2: return launch_curved_w<5>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    case 3: return launch_curved_w<7>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    case 4: return launch_curved_w<9>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    case 5: return launch_curved_w<11>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    case 6: return launch_curved_w<13>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    case 7: return launch_curved_w<15>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    case 8: return launch_curved_w<17>(n, nrhs, Mq, Kq, cm, ck, x, y, ld, sms, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_spmm32(int n, int p, int nrhs, const float* M1, const float* K1, SpmmCoef cf,

@@ -28,6 +28,13 @@ cudaError_t launch_spmm32_strip(int n, int p, int nrhs, const float* M1, const f
                                 SpmmCoef cf, const float* x, float* y, long ld, int sms,
                                 size_t smem_max, cudaStream_t st);
 int spmm32_strip_rows(int n, int p, size_t smem_max);
+// The curved map: assembled stencils in FP32, coefficient q of point i at
+// Mq[q N + i] (q = (dy + p)(2p + 1) + dx + p, N = n*n; the [N][(2p+1)^2]
+// stencil transposed), y_b = (cm M + ck K) x_b; Mq or Kq may be null (that
+// term left out).  x, y [nrhs][ld], any alignment; p in [2, 8].
+cudaError_t launch_spmm32_curved(int n, int p, int nrhs, const float* Mq, const float* Kq,
+                                 float cm, float ck, const float* x, float* y, long ld, int sms,
+                                 cudaStream_t st);
 // The shared-memory plan for an n x n grid: out[7] = {grid-line cap of the
 // layout (0: does not fit), ring depth, grid lines per thread J, padded x row
 // stride, (tm, tk) row stride in pairs, (tm, tk) rows, dynamic shared bytes}.

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import assembly, geometry, mgrit, timestep
+from stencil_rows import unit_square_row
 
 pytestmark = pytest.mark.gpu
 
@@ -283,11 +284,94 @@ def test_batched_fp32_apply_full_size_sampled(B):
     assert err.max() < 2e-6
 
 
-def test_batched_fp32_apply_rejects_curved_map(B):
+@pytest.mark.parametrize("p,nel", [(2, 1024), (3, 512)])
+def test_batched_fp32_apply_row_strips_largest_grid(B, p, nel):
+    """The largest grid a descriptor allows (1024 x 1024 elements, n = 1024 grid
+    lines) and n = 513 at p = 3: more grid columns than a CTA has threads, so
+    threads walk two of them (at n = 513 one thread alone takes the second).
+    Sampled outputs at the edges, the corners,
+    the strip boundaries and the thread-chunk boundary, against stencil rows
+    taken from the oracle's small problem by translation and scaling."""
     import torch
-    prob = B.Problem(2, 8, "quarter_annulus")
-    with pytest.raises(B.IgmError):
-        prob.apply_f32("M", torch.zeros((1, prob.N), dtype=torch.float32, device="cuda"))
+    nel_s, ncol = 4 * p + 2, 3
+    ds = assembly.Discretisation(p, nel_s, geometry.UnitSquare())
+    prob = B.Problem(p, nel)
+    n = prob.n
+    c = 1.0 / 4096
+    g = torch.Generator(device="cuda").manual_seed(15)
+    Xd = torch.randn((ncol, prob.N), dtype=torch.float32, device="cuda", generator=g)
+    Y = prob.apply_f32("A", Xd, c=c).double().cpu().numpy().reshape(ncol, n, n)
+    X = Xd.double().cpu().numpy().reshape(ncol, n, n)
+    rng = np.random.default_rng(16)
+    pts = {(0, 0), (0, n - 1), (n - 1, 0), (n - 1, n - 1), (31, 511), (32, 512),
+           (n // 2, 1), (2, n - 3), (n - 2 * p, 2 * p - 1), (63, n - 1), (64, 0)}
+    pts |= {tuple(v) for v in rng.integers(0, n, (24, 2)).tolist()}
+    got, want = [], []
+    for iy, ix in sorted(pts):
+        st = unit_square_row(ds, nel_s, nel, p, n, iy, ix)
+        for b in range(ncol):
+            w = sum((m + c * k) * X[b, iy + dy, ix + dx] for (dy, dx), (m, k) in st.items())
+            got.append(Y[b, iy, ix])
+            want.append(w)
+    got, want = np.array(got), np.array(want)
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 2e-6
+
+
+def _curved_bound(d, which, c, X32):
+    """Elementwise bound on the FP32 apply of an assembled stencil (Sec. 2, M and
+    K on the curved map): each coefficient a = fl(cm M + ck K) is within
+    3u (|M| + |c| |K|) of the exact value (rounding of M, K, c and of the
+    FMA), and the Q-term FMA chain adds at most gamma_Q < (Q + 1) u of
+    sum |a_i x_i| (u = 2^-24, Q = (2p+1)^2; x is taken as its FP32 value)."""
+    absM, absK = abs(d.M), abs(d.K)
+    mag = {"M": absM, "K": absK, "A": absM + abs(c) * absK}[which]
+    Q = (2 * d.p + 1) ** 2
+    return (Q + 4) * 2.0 ** -24 * (mag @ np.abs(X32).T).T
+
+
+@pytest.mark.parametrize("p,nel,nrhs,pad", [(2, 40, 7, 0), (3, 64, 101, 3), (4, 36, 13, 1),
+                                            (5, 12, 250, 2), (6, 10, 9, 0)])
+@pytest.mark.parametrize("which", ["M", "K", "A"])
+def test_batched_fp32_apply_curved_map(B, p, nel, nrhs, pad, which):
+    """The curved-map form of iga_apply_f32 on the quarter annulus against the
+    oracle's assembled M, K (FP64) on the same FP32 inputs, element by element
+    within the rounding bound of the arithmetic: ragged 8 x 32 tiles (n = 40,
+    38, 15), a column count that is not a multiple of four, several column
+    groups per CTA (n = 65, 101 columns), a padded leading dimension, and
+    p = 6 (coefficients read from global memory instead of registers)."""
+    import torch
+    d = assembly.Discretisation(p, nel, geometry.QuarterAnnulus())
+    c = 0.37
+    A = {"M": d.M, "K": d.K, "A": d.M + c * d.K}[which]
+    X = np.random.default_rng(12).standard_normal((nrhs, d.N + pad))
+    Xd = torch.as_tensor(X, dtype=torch.float32, device="cuda")
+    X32 = Xd[:, :d.N].double().cpu().numpy()
+    want = (A @ X32.T).T
+    prob = B.Problem(p, nel, "quarter_annulus")
+    Y = prob.apply_f32(which, Xd, c=c)
+    got = Y[:, :d.N].double().cpu().numpy()
+    bound = _curved_bound(d, which, c, X32)
+    assert np.all(np.abs(got - want) <= bound), np.max(np.abs(got - want) / bound)
+    assert torch.equal(Xd, torch.as_tensor(X, dtype=torch.float32, device="cuda"))
+
+
+def test_batched_fp32_apply_curved_full_size_sampled(B):
+    """The annulus_c3 grid (p = 4, 128 x 128 elements, n = 130) with 1024 columns
+    in one launch: sampled columns, including the first and last, against the
+    oracle's assembled M + c K within the rounding bound."""
+    import torch
+    p, nel, ncol = 4, 128, 1024
+    d = assembly.Discretisation(p, nel, geometry.QuarterAnnulus())
+    c = 1.0 / 1024
+    g = torch.Generator(device="cuda").manual_seed(13)
+    Xd = torch.randn((ncol, d.N), dtype=torch.float32, device="cuda", generator=g)
+    Y = B.Problem(p, nel, "quarter_annulus").apply_f32("A", Xd, c=c)
+    cols = sorted({0, 1, 3, 4, ncol // 2, ncol - 1}
+                  | set(np.random.default_rng(14).integers(0, ncol, 10).tolist()))
+    X32 = Xd[cols].double().cpu().numpy()
+    want = ((d.M + c * d.K) @ X32.T).T
+    got = Y[cols].double().cpu().numpy()
+    assert np.all(np.abs(got - want) <= _curved_bound(d, "A", c, X32))
 
 
 @pytest.mark.parametrize("geom,p,nel", [("unit_square", 4, 64), ("quarter_annulus", 3, 16)])
@@ -328,17 +412,17 @@ def test_mixed_form_with_fp64_w_cycle(B, geom, p, nel):
         assert _rel(U, seq) < 1e-10, st
 
 
-@pytest.mark.parametrize("p,nel", [(5, 128), (2, 100)])
-def test_batched_fp32_apply_row_strips_beyond_84_lines(B, p, nel):
+@pytest.mark.parametrize("p,nel,nrhs", [(5, 128, 5), (2, 100, 700), (3, 90, 9)])
+def test_batched_fp32_apply_row_strips_beyond_84_lines(B, p, nel, nrhs):
     """Grids the persistent layouts do not hold (n = nel + p - 2 > 84: the
     h = 1/128 grids of batch_c5) go through the row-strip form; every column
     against the oracle's assembled M + c K (Sec. 2, Eq. (los)), a ragged last
-    strip and more columns than column groups."""
+    strip, and (700 columns) several columns per CTA through both copy stages."""
     import torch
     d = assembly.Discretisation(p, nel, geometry.UnitSquare())
     assert d.n > 84
     c = 1.0 / 512
-    X = np.random.default_rng(9).standard_normal((5, d.N))
+    X = np.random.default_rng(9).standard_normal((nrhs, d.N))
     want = ((d.M + c * d.K) @ X.T).T
     prob = B.Problem(p, nel)
     Y = prob.apply_f32("A", torch.as_tensor(X, dtype=torch.float32, device="cuda"), c=c)

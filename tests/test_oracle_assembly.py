@@ -4,6 +4,7 @@ import pytest
 import scipy.sparse.linalg as sla
 
 from oracle import assembly, bspline, geometry
+from stencil_rows import unit_square_row
 
 
 def test_q1_textbook_stencils():
@@ -59,3 +60,28 @@ def test_dirichlet_sizes():
         knots = bspline.open_uniform_knots(p, nel)
         n = bspline.num_basis(knots, p) - 2
         assert n * n == N
+
+
+@pytest.mark.parametrize("p,nel", [(2, 23), (3, 19), (5, 25)])
+def test_unit_square_rows_translate_and_scale(p, nel):
+    """On the unit square with open uniform knots (Sec. 2) every row of M and K
+    whose coupled basis functions have uniform knot spans is one translated
+    stencil; M scales with h^2 and K not at all; rows near an edge repeat those
+    of a small problem at the same distance from the edge.  Every row of the
+    oracle's nel x nel matrices against the rows mapped from a (4p + 2)^2
+    problem: a wrong quadrature weight, basis index or Jacobian factor in the
+    assembly breaks the relation."""
+    nel_s = 4 * p + 2
+    ds = assembly.Discretisation(p, nel_s, geometry.UnitSquare())
+    d = assembly.Discretisation(p, nel, geometry.UnitSquare())
+    n = d.n
+    for iy in range(n):
+        for ix in range(n):
+            st = unit_square_row(ds, nel_s, nel, p, n, iy, ix)
+            r = iy * n + ix
+            for k, mat in enumerate((d.M, d.K)):
+                row = mat.getrow(r)
+                got = {(j // n - iy, j % n - ix): v for j, v in zip(row.indices, row.data)}
+                scale = np.abs(row.data).max()
+                for key in set(got) | set(st):
+                    assert abs(got.get(key, 0.0) - st.get(key, (0.0, 0.0))[k]) <= 1e-12 * scale
