@@ -345,7 +345,9 @@ __global__ void __launch_bounds__(512) k_spmm32_strip(int n, int nrhs, int SR,
   cp_async_wait<0>();
 }
 
-// strip height, threads and shared bytes of the strip form (SR = 0: does not fit)
+// strip height, threads and shared bytes of the strip form (SR = 0: does not fit):
+// the tallest strip (at most 32 rows) in 100 KB, else in all of smem_max.  (Shorter
+// strips for more CTAs per SM measured slower: the halo rows' stage-1 work grows.)
 int strip_plan(int n, int p, size_t smem_max, size_t* bytes, int* threads) {
   const int W = 2 * p + 1;
   *threads = std::min(512, (n + 31) / 32 * 32);
@@ -395,8 +397,11 @@ cudaError_t launch_strip_w(int n, int nrhs, const float* M1, const float* K1, Sp
 constexpr int kCurvTR = 8, kCurvTC = 32, kCurvThreads = kCurvTR * 32;
 
 
+// register caps: the coefficients of one point in registers, and 4 / 3 / 2 / 1 CTAs per SM
+// for p = 2 / 3 / 4 / 5 (p >= 6 reads coefficients from global memory)
 template <int W>
-__global__ void __launch_bounds__(kCurvThreads) k_spmm32_curved(
+__global__ void __maxnreg__(W <= 5 ? 56 : W <= 7 ? 80 : W <= 9 ? 128 : W <= 11 ? 168 : 64)
+    k_spmm32_curved(
     int n, int nrhs, const float* __restrict__ Mq, const float* __restrict__ Kq, float cm,
     float ck, const float* __restrict__ x, float* __restrict__ y, long ld) {
   constexpr int p = (W - 1) / 2, Q = W * W;
