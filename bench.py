@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true",
                     help="skip the CPU baseline leg (oracle timings and the errors against it)")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="leave the learned_c4 and batch_c5 sub-objects out of the default run")
     ap.add_argument("--skip-annulus", action="store_true",
                     help="skip the annulus_c3 sub-measurement of the default run")
     ap.add_argument("--sjf", type=int, default=1,
@@ -356,12 +358,16 @@ def run_reference(args):
 
 
 def run_batch(args):
+    print(json.dumps(batch_measure(args.steps, args.warmup, args.sjf, args.batch_order)))
+
+
+def batch_measure(steps, warmup, sjf=1, batch_order="shortest", host_arm=True):
     """batch_c5: 64 independent problems (inputs.batch_members) in the chosen
     (mixed) form, solved in one persistent launch (mgrit_run_batched_device)
-    and, beside it, by streams with a host scheduler (mgrit_run_batched).
-    Reports the per-problem latency distribution from the batch start and the
-    batch throughput sum(N * N_t) / makespan.  L2 is flushed before every
-    timed batch."""
+    and, beside it (host_arm), by streams with a host scheduler
+    (mgrit_run_batched).  Reports the per-problem latency distribution from the
+    batch start and the batch throughput sum(N * N_t) / makespan.  L2 is
+    flushed before every timed batch."""
     import numpy as np
     import torch
     from concurrent.futures import ThreadPoolExecutor
@@ -383,7 +389,7 @@ def run_batch(args):
     order = sorted(range(len(members)), key=lambda i: work[i])
     prio = [0] * len(members)
     for r, i in enumerate(order):
-        prio[i] = 5 - (6 * r) // len(members) if args.sjf else 0
+        prio[i] = 5 - (6 * r) // len(members) if sjf else 0
     t0 = time.perf_counter()
     # (fused = 0: a fused visit's cooperative launch needs all its CTAs resident at
     # once, which serialises members running on concurrent streams; the
@@ -399,12 +405,12 @@ def run_batch(args):
     units = sum(pr.N * mb["Nt"] for pr, mb in zip(probs, members))
     def measure(device, hs, u0l, Ul):
         lats, spans, iters = [], [], []
-        for rep in range(args.warmup + args.steps):
+        for rep in range(warmup + steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             _, stats, lat, status = B.mgrit_run_batched(hs, u0l, Us=Ul, device=device)
             torch.cuda.synchronize()
-            if rep >= args.warmup:
+            if rep >= warmup:
                 lats.extend(lat.tolist())
                 spans.append(float(lat.max()))
                 iters = [st["iters"] for st in stats]
@@ -412,20 +418,22 @@ def run_batch(args):
 
     # one persistent launch for the whole batch (members in shortest-first
     # order, the order in which idle CTAs look for work)
-    dev_order = order if args.batch_order == "shortest" else order[::-1]
+    dev_order = order if batch_order == "shortest" else order[::-1]
     lat_d, span_d, iters_d = measure(True, [handles[i] for i in dev_order],
                                      [u0s[i] for i in dev_order], [Us[i] for i in dev_order])
     # streams and a host scheduler, with shortest-job-first stream priorities
-    lat, makespan, iters = measure(False, handles, u0s, Us)
-    host_sched = {"value": units / (makespan * 1e-3), "makespan_ms": makespan,
-                  "latency_ms": {"p50": float(np.percentile(lat, 50)),
-                                 "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
-                  "scheduling": "streams + host scheduler, shortest job first (stream priorities)"
-                  if args.sjf else "streams + host scheduler, equal priorities"}
+    host_sched = None
+    if host_arm:
+        lat, makespan, iters = measure(False, handles, u0s, Us)
+        host_sched = {"value": units / (makespan * 1e-3), "makespan_ms": makespan,
+                      "latency_ms": {"p50": float(np.percentile(lat, 50)),
+                                     "p99": float(np.percentile(lat, 99)), "max": float(lat.max())},
+                      "scheduling": "streams + host scheduler, shortest job first (stream priorities)"
+                      if sjf else "streams + host scheduler, equal priorities"}
     lat, makespan, iters = lat_d, span_d, iters_d
     line = {"metric": "DOF*timesteps/s of an uneven 64-problem batch to MGRIT rel. residual 1e-10",
             "value": units / (makespan * 1e-3), "unit": "DOF*timesteps/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "higher_is_better": True,
             "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "batch_c5: 64 problems, h in {1/32,1/64,1/128}, p in 2..5, "
                                    "N_t in {128..2048}, kappa log-uniform [0.1,10], f=0, m=4, "
@@ -435,21 +443,27 @@ def run_batch(args):
                            "max": float(lat.max())},
             "makespan_ms": makespan, "setup_s": round(setup_s, 2),
             "scheduling": f"one persistent launch (device work claiming, members scanned "
-                          f"{args.batch_order} first, device-side stopping tests)",
+                          f"{batch_order} first, device-side stopping tests)",
             "host_scheduled": host_sched,
             "form": "mixed precision, one p-MG cycle per coarse-level solve, autotuned sweep layouts",
             "iters": {"min": int(min(iters)), "max": int(max(iters))}, "members": len(members)}
-    print(json.dumps(line))
+    del handles, Us, flush
+    return line
 
 
 def run_learned(args):
+    print(json.dumps(learned_measure(args.steps)))
+
+
+def learned_measure(steps, plain_arm=True):
     """learned_c4: unit square, p = 3, 64 x 64 elements, N_t = 4096, T = 4,
     two-level MGRIT with m = 8, f = 0.  Training pairs (u_n, u_{n+8}) come from
     the fine stepper (sequential backward Euler through the library) on five
     16-mode random initial conditions; the network is trained with the BF16
     kernels; then the same two-level MGRIT (chosen form) is timed on a sixth
     initial condition with the learned coarse propagator and with backward
-    Euler on the coarse level, and the plain FP64 form with backward Euler."""
+    Euler on the coarse level, and (plain_arm) the plain FP64 form with
+    backward Euler."""
     import numpy as np
     import torch
     from paper_2107_05337_gb300 import binding as B
@@ -503,7 +517,7 @@ def run_learned(args):
         ms = []
         st = None
         status = 0
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, steps)):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -518,9 +532,11 @@ def run_learned(args):
     learned = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
     learned.set_coarse_propagator(phic, 0.5)
     be = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
-    plain = B.MGRIT(prob, **common, pmg=dict(precision=0, tol=1e-10))
+    arms = [("learned", learned), ("backward_euler", be)]
+    if plain_arm:
+        arms.append(("plain_fp64", B.MGRIT(prob, **common, pmg=dict(precision=0, tol=1e-10))))
     res = {}
-    for name, h in (("learned", learned), ("backward_euler", be), ("plain_fp64", plain)):
+    for name, h in arms:
         ms, st, err, status = timed(h)
         hist = st["res_hist"]
         res[name] = {"value": units / (ms * 1e-3), "ms": ms, "iters": st["iters"],
@@ -535,11 +551,14 @@ def run_learned(args):
                                    "two levels, f=0, 16-mode random initial conditions"},
             "runs": res,
             "speedup_vs_backward_euler_coarse": res["learned"]["value"] / res["backward_euler"]["value"],
-            "speedup_vs_plain_fp64": res["learned"]["value"] / res["plain_fp64"]["value"],
+            "speedup_vs_plain_fp64": (res["learned"]["value"] / res["plain_fp64"]["value"]
+                                      if plain_arm else None),
             "training": {"pairs": npairs, "steps": steps, "batch": 32,
                          "seconds": round(train_s, 2), "data_seconds": round(gen_s, 2),
-                         "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-20:]))}}
-    print(json.dumps(line))
+                         "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-20:]))},
+            "steps": max(1, steps)}
+    del learned, be, arms, phic, seq, stepper, X, X0, Uref
+    return line
 
 
 def annulus_measure(steps, warmup, profile_only=False):
@@ -945,6 +964,16 @@ def main():
     if not args.skip_annulus and rank == 0:
         annulus, U_annulus = annulus_measure(2, 1)
 
+    # the learned coarse propagator (learned_c4, without its plain FP64 arm) and the
+    # uneven batch in one persistent launch (batch_c5, device scheduling only):
+    # one timed run each
+    learned_c4, batch_c5 = None, None
+    if not args.skip_extra and rank == 0:
+        learned_c4 = learned_measure(1, plain_arm=False)
+        torch.cuda.empty_cache()
+        batch_c5 = batch_measure(1, 1, host_arm=False)
+        torch.cuda.empty_cache()
+
     cpu, errors = None, None
     if refs:
         # errors against the oracle's sequential backward Euler (Sec. 3: the
@@ -990,6 +1019,8 @@ def main():
                 "orders_one_after_another_ms": serial_ms,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
                 "annulus_c3": annulus,
+                "learned_c4": learned_c4,
+                "batch_c5": batch_c5,
                 "clocks": clocks}
         print(json.dumps(line))
     if world > 1:
