@@ -47,6 +47,15 @@ METRIC = "DOF*timesteps/s to MGRIT rel. residual 1e-10, chosen vs plain FP64 for
 UNIT = "DOF*timesteps/s"
 
 
+_T0 = time.perf_counter()
+
+
+def log(msg):
+    """Progress of the run on stderr (the JSON line stays alone on stdout)."""
+    sys.stderr.write(f"[bench +{time.perf_counter() - _T0:7.1f} s] {msg}\n")
+    sys.stderr.flush()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -60,8 +69,8 @@ def parse():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true",
                     help="skip the CPU baseline leg (oracle timings and the errors against it)")
-    ap.add_argument("--skip-extra", action="store_true",
-                    help="leave the learned_c4 and batch_c5 sub-objects out of the default run")
+    ap.add_argument("--extra", action="store_true",
+                    help="add the learned_c4 and batch_c5 sub-objects to the default run")
     ap.add_argument("--skip-annulus", action="store_true",
                     help="skip the annulus_c3 sub-measurement of the default run")
     ap.add_argument("--sjf", type=int, default=1,
@@ -400,6 +409,7 @@ def batch_measure(steps, warmup, sjf=1, batch_order="shortest", host_arm=True):
     with ThreadPoolExecutor(max_workers=16) as ex:
         handles = list(ex.map(mk, range(len(members))))
     setup_s = time.perf_counter() - t0
+    log(f"batch_c5: {len(handles)} members set up in {setup_s:.1f} s")
     Us = [torch.empty((h.Nt + 1, h.problem.N), dtype=torch.float64, device="cuda") for h in handles]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     units = sum(pr.N * mb["Nt"] for pr, mb in zip(probs, members))
@@ -410,6 +420,8 @@ def batch_measure(steps, warmup, sjf=1, batch_order="shortest", host_arm=True):
             torch.cuda.synchronize()
             _, stats, lat, status = B.mgrit_run_batched(hs, u0l, Us=Ul, device=device)
             torch.cuda.synchronize()
+            log(f"batch_c5: {'device' if device else 'host'}-scheduled run {rep}, "
+                f"makespan {float(lat.max()):.0f} ms")
             if rep >= warmup:
                 lats.extend(lat.tolist())
                 spans.append(float(lat.max()))
@@ -499,12 +511,14 @@ def learned_measure(steps, plain_arm=True):
     U0, U1 = torch.cat(U0s), torch.cat(U1s)
     npairs = int(U0.shape[0])
     gen_s = time.perf_counter() - t0
+    log(f"learned_c4: {npairs} training pairs in {gen_s:.1f} s")
     phic = B.Phic(prob.n, 32, seed=w["seed"])
     t0 = time.perf_counter()
     steps = 3000
     loss = phic.train(U0, U1, steps=steps, batch=32, lr=2e-3, seed=1)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    log(f"learned_c4: trained in {train_s:.1f} s")
     del U0, U1, U0s, U1s
     u0 = ic(w["seed"] + 100)
     Uref, _, _ = seq.run(u0)
@@ -538,6 +552,7 @@ def learned_measure(steps, plain_arm=True):
     res = {}
     for name, h in arms:
         ms, st, err, status = timed(h)
+        log(f"learned_c4: {name} {ms:.0f} ms, {st['iters']} iterations")
         hist = st["res_hist"]
         res[name] = {"value": units / (ms * 1e-3), "ms": ms, "iters": st["iters"],
                      "status": status, "coarse_fallback": st["coarse_fallback"],
@@ -857,6 +872,7 @@ def main():
         host = {p: Us[p].cpu().numpy() for p in orders}   # the last step's iterates
         return total, ms, stats, ck.summary(), launches, host
 
+    log("heat_c2: chosen form")
     total, ms, stats, clocks, launches, U_chosen = timed(chosen, args.steps, args.warmup)
     value = job_throughput(units, world, args.steps, total)
 
@@ -874,6 +890,7 @@ def main():
     if not args.skip_plain:
         h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=1, tol=1e-10, autotune=1))
              for p in orders}
+        log("heat_c2: mixed-only and plain FP64 forms")
         mixed, U_mixed = side_form(h, "mixed")
         del h
         h = {p: B.MGRIT(probs[p], **opts, pmg=dict(precision=0, tol=1e-10)) for p in orders}
@@ -890,6 +907,7 @@ def main():
 
     # end to end through the C ABI with host buffers: H2D of u0, fhat (pinned),
     # solve, D2H of the final time level, every step
+    log("heat_c2: end to end")
     hu0 = {p: u0s[p].cpu().pin_memory() for p in orders}
     hfh = {p: fhats[p].cpu().pin_memory() for p in orders}
     hout = {p: torch.empty(probs[p].N, dtype=torch.float64).pin_memory() for p in orders}
@@ -925,6 +943,7 @@ def main():
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     # roofline of the dominant kernel (k_mgrit_sweep), one profiled solve per order
+    log("heat_c2: profiled solves for the roofline")
     roof = None
     prof_tot_ms, prof_bytes, prof_launches = 0.0, 0.0, 0
     for p in orders:
@@ -962,15 +981,18 @@ def main():
     # the curved-map workload, where the iterate exceeds L2
     annulus, U_annulus = None, None
     if not args.skip_annulus and rank == 0:
+        log("annulus_c3")
         annulus, U_annulus = annulus_measure(2, 1)
 
-    # the learned coarse propagator (learned_c4, without its plain FP64 arm) and the
-    # uneven batch in one persistent launch (batch_c5, device scheduling only):
-    # one timed run each
+    # (--extra) the learned coarse propagator (learned_c4, without its plain FP64
+    # arm) and the uneven batch in one persistent launch (batch_c5, device
+    # scheduling only): one timed run each
     learned_c4, batch_c5 = None, None
-    if not args.skip_extra and rank == 0:
+    if args.extra and rank == 0:
+        log("learned_c4")
         learned_c4 = learned_measure(1, plain_arm=False)
         torch.cuda.empty_cache()
+        log("batch_c5")
         batch_c5 = batch_measure(1, 1, host_arm=False)
         torch.cuda.empty_cache()
 
@@ -978,6 +1000,7 @@ def main():
     if refs:
         # errors against the oracle's sequential backward Euler (Sec. 3: the
         # fixed point of MGRIT), every timed form and order
+        log("oracle references and CPU baseline")
         seq = {job: f.result() for job, f in refs.items()}
         refs_ex.shutdown()
         errors = {}
