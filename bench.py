@@ -69,8 +69,9 @@ def parse():
     ap.add_argument("--skip-check", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true",
                     help="skip the CPU baseline leg (oracle timings and the errors against it)")
-    ap.add_argument("--extra", action="store_true",
-                    help="add the learned_c4 and batch_c5 sub-objects to the default run")
+    ap.add_argument("--skip-extra", action="store_true",
+                    help="leave the learned_c4 and batch_c5 sub-objects (child processes) out "
+                         "of the default run")
     ap.add_argument("--skip-annulus", action="store_true",
                     help="skip the annulus_c3 sub-measurement of the default run")
     ap.add_argument("--sjf", type=int, default=1,
@@ -367,7 +368,8 @@ def run_reference(args):
 
 
 def run_batch(args):
-    print(json.dumps(batch_measure(args.steps, args.warmup, args.sjf, args.batch_order)))
+    print(json.dumps(batch_measure(args.steps, args.warmup, args.sjf, args.batch_order,
+                                   host_arm=not args.skip_plain)))
 
 
 def batch_measure(steps, warmup, sjf=1, batch_order="shortest", host_arm=True):
@@ -464,7 +466,28 @@ def batch_measure(steps, warmup, sjf=1, batch_order="shortest", host_arm=True):
 
 
 def run_learned(args):
-    print(json.dumps(learned_measure(args.steps)))
+    print(json.dumps(learned_measure(args.steps, plain_arm=not args.skip_plain)))
+
+
+def extra_child(mode_args, timeout_s):
+    """One of the standalone measurement modes in a child process (a fresh CUDA
+    context, as when it runs alone), its JSON line as a dict; a child that does
+    not finish within timeout_s seconds is killed and reported unavailable."""
+    cmd = [sys.executable, os.path.abspath(__file__)] + mode_args
+    t0 = time.perf_counter()
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"unavailable": f"{' '.join(mode_args)}: did not finish within {timeout_s} s"}
+    if r.returncode != 0:
+        tail = r.stderr.strip().splitlines()[-1:] or [""]
+        return {"unavailable": f"{' '.join(mode_args)}: exit {r.returncode}: {tail[0][:200]}"}
+    try:
+        line = json.loads(r.stdout.strip().splitlines()[-1])
+    except (ValueError, IndexError):
+        return {"unavailable": f"{' '.join(mode_args)}: no JSON line"}
+    line["child_seconds"] = round(time.perf_counter() - t0, 1)
+    return line
 
 
 def learned_measure(steps, plain_arm=True):
@@ -984,17 +1007,6 @@ def main():
         log("annulus_c3")
         annulus, U_annulus = annulus_measure(2, 1)
 
-    # (--extra) the learned coarse propagator (learned_c4, without its plain FP64
-    # arm) and the uneven batch in one persistent launch (batch_c5, device
-    # scheduling only): one timed run each
-    learned_c4, batch_c5 = None, None
-    if args.extra and rank == 0:
-        log("learned_c4")
-        learned_c4 = learned_measure(1, plain_arm=False)
-        torch.cuda.empty_cache()
-        log("batch_c5")
-        batch_c5 = batch_measure(1, 1, host_arm=False)
-        torch.cuda.empty_cache()
 
     cpu, errors = None, None
     if refs:
@@ -1011,6 +1023,16 @@ def main():
         if annulus is not None:
             annulus["error_vs_oracle"] = rel_err(U_annulus, seq[("annulus_c3",)])
         cpu = cpu_baseline_leg()
+
+    # the learned coarse propagator (learned_c4, without its plain FP64 arm) and the
+    # uneven batch in one persistent launch (batch_c5, device scheduling only), one
+    # timed run each, as child processes with a time limit (single-GPU runs only)
+    learned_c4, batch_c5 = None, None
+    if not args.skip_extra and rank == 0 and world == 1:
+        log("learned_c4 (child process)")
+        learned_c4 = extra_child(["--learned", "--steps", "1", "--skip-plain"], 360)
+        log("batch_c5 (child process)")
+        batch_c5 = extra_child(["--batch", "--steps", "1", "--warmup", "1", "--skip-plain"], 360)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
