@@ -18,9 +18,10 @@ reported beside it, so that the speed-up over the plain form splits into its
 precision and coarse-propagator parts.  Every form's iterate of the last timed
 step is compared with the oracle's sequential backward Euler (the fixed point of
 MGRIT, Sec. 3) per order ("error_vs_oracle").  The default run also measures the
-curved-map workload annulus_c3 ("annulus_c3", with its own roofline and error)
-and the CPU baseline: the oracle on a bounded sample of heat_c2, on one core
-and as independent replicas on every host core.
+curved-map workload annulus_c3 ("annulus_c3", with its own roofline and error),
+the CPU baseline (the oracle on a bounded sample of heat_c2, on one core and as
+independent replicas on every host core) and, in a child process with a time
+limit, the uneven batch batch_c5 in one persistent launch ("batch_c5").
 
 Other modes (one JSON line each): --annulus (the curved-map workload annulus_c3),
 --batch (the uneven 64-problem batch, latency percentiles), --learned (two-level
@@ -70,8 +71,7 @@ def parse():
     ap.add_argument("--skip-cpu", action="store_true",
                     help="skip the CPU baseline leg (oracle timings and the errors against it)")
     ap.add_argument("--skip-extra", action="store_true",
-                    help="leave the learned_c4 and batch_c5 sub-objects (child processes) out "
-                         "of the default run")
+                    help="leave the batch_c5 sub-object (a child process) out of the default run")
     ap.add_argument("--skip-annulus", action="store_true",
                     help="skip the annulus_c3 sub-measurement of the default run")
     ap.add_argument("--sjf", type=int, default=1,
@@ -1024,13 +1024,10 @@ def main():
             annulus["error_vs_oracle"] = rel_err(U_annulus, seq[("annulus_c3",)])
         cpu = cpu_baseline_leg()
 
-    # the learned coarse propagator (learned_c4, without its plain FP64 arm) and the
-    # uneven batch in one persistent launch (batch_c5, device scheduling only), one
-    # timed run each, as child processes with a time limit (single-GPU runs only)
-    learned_c4, batch_c5 = None, None
+    # the uneven batch in one persistent launch (batch_c5, device scheduling only),
+    # one timed run, as a child process with a time limit (single-GPU runs only)
+    batch_c5 = None
     if not args.skip_extra and rank == 0 and world == 1:
-        log("learned_c4 (child process)")
-        learned_c4 = extra_child(["--learned", "--steps", "1", "--skip-plain"], 360)
         log("batch_c5 (child process)")
         batch_c5 = extra_child(["--batch", "--steps", "1", "--warmup", "1", "--skip-plain"], 360)
 
@@ -1064,7 +1061,6 @@ def main():
                 "orders_one_after_another_ms": serial_ms,
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
                 "annulus_c3": annulus,
-                "learned_c4": learned_c4,
                 "batch_c5": batch_c5,
                 "clocks": clocks}
         print(json.dumps(line))
