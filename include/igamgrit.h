@@ -163,6 +163,17 @@ igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const floa
  * only (needs no device).  IGM_ERR_ARG for p outside [2, 8] or n < 1. */
 igm_status iga_apply_f32_layout(int n, int p, long smem_max, int* out);
 
+/* The launch plan of iga_apply_f32's other two forms for an n x n grid at
+ * order p, nrhs columns, a device with sms SMs and smem_max bytes of opt-in
+ * shared memory per block (HOST out; needs no device).  form 1, the row-strip
+ * form (out[5]): rows per strip (0 when not even one row fits), threads per
+ * CTA, dynamic shared bytes, strips (grid x), column groups (grid y).  form 2,
+ * the curved form (out[6]): tile rows and columns, staged rows and columns
+ * (the tile plus p halo lines on each side; two stages of float4 of them in
+ * shared memory), tiles (grid x), column groups (grid y).  IGM_ERR_ARG for
+ * invalid input. */
+igm_status iga_apply_f32_plan(int form, int n, int p, int nrhs, int sms, long smem_max, int* out);
+
 /* ---------------------------------------------------------------------------
  * p-multigrid (Sec. 4) for A = M + c K, c = kappa*dt.
  * ------------------------------------------------------------------------ */

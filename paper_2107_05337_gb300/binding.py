@@ -65,6 +65,7 @@ EXPORTS = {
     "iga_transfer_host": (c_int, [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                   POINTER(c_double)]),
     "iga_apply_f32_layout": (c_int, [c_int, c_int, c_long, POINTER(c_int)]),
+    "iga_apply_f32_plan": (c_int, [c_int, c_int, c_int, c_int, c_int, c_long, POINTER(c_int)]),
     "pmg_block_tri_host": (c_int, [c_int, c_int, POINTER(c_int), POINTER(c_int), POINTER(c_double),
                                    POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                    POINTER(c_double), POINTER(c_double)]),
@@ -350,6 +351,15 @@ def apply_f32_layout(n, p, smem_max=232448):
     out = (c_int * 7)()
     _check(lib().iga_apply_f32_layout(n, p, smem_max, out))
     return dict(zip(("cap", "ring", "J", "xs", "ns", "rows", "smem"), list(out)))
+
+
+def apply_f32_plan(form, n, p, nrhs, sms=152, smem_max=232448):
+    """iga_apply_f32_plan as a dict: form "strip" or "curved"."""
+    k = {"strip": (1, ("SR", "threads", "smem", "strips", "groups")),
+         "curved": (2, ("TR", "TC", "HR", "HC", "tiles", "groups"))}[form]
+    out = (c_int * len(k[1]))()
+    _check(lib().iga_apply_f32_plan(k[0], n, p, nrhs, sms, smem_max, out))
+    return dict(zip(k[1], list(out)))
 
 
 class Problem:

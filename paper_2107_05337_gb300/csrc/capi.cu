@@ -1235,6 +1235,17 @@ extern "C" igm_status iga_apply_f32_layout(int n, int p, long smem_max, int* out
   return IGM_OK;
 }
 
+extern "C" igm_status iga_apply_f32_plan(int form, int n, int p, int nrhs, int sms, long smem_max,
+                                         int* out) {
+  if (!out || (form != 1 && form != 2) || n < 1 || p < 2 || p > 8 || nrhs < 0 || sms < 1 ||
+      smem_max <= 0)
+    return fail(IGM_ERR_ARG,
+                "iga_apply_f32_plan: form 1 or 2, n >= 1, p in [2, 8], nrhs >= 0, sms >= 1, smem_max > 0, out");
+  if (form == 1) spmm32_strip_plan(n, p, nrhs, sms, (size_t)smem_max, out);
+  else spmm32_curved_plan(n, p, nrhs, sms, out);
+  return IGM_OK;
+}
+
 extern "C" igm_status iga_apply_f32(iga_ops* ops, int which, double c, int nrhs, const float* x,
                                     float* y, long ld, igm_stream s) {
   if (!ops || (nrhs > 0 && (!x || !y))) return fail(IGM_ERR_ARG, "null argument");

@@ -369,16 +369,13 @@ template <int W>
 cudaError_t launch_strip_w(int n, int nrhs, const float* M1, const float* K1, SpmmCoef cf,
                            const float* x, float* y, long ld, int sms, size_t smem_max,
                            cudaStream_t st) {
-  size_t bytes = 0;
-  int threads = 0;
-  const int SR = strip_plan(n, (W - 1) / 2, smem_max, &bytes, &threads);
+  int pl[5];
+  spmm32_strip_plan(n, (W - 1) / 2, nrhs, sms, smem_max, pl);
+  const int SR = pl[0], threads = pl[1], bytes = pl[2], strips = pl[3], cg = pl[4];
   if (!SR) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_spmm32_strip<W>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   if (e != cudaSuccess) return e;
-  const int strips = (n + SR - 1) / SR;
-  // about four CTAs per SM over the launch
-  const int cg = std::max(1, std::min(nrhs, (4 * sms + strips - 1) / strips));
   k_spmm32_strip<W><<<dim3(strips, cg), threads, bytes, st>>>(n, nrhs, SR, M1, K1, cf, x, y, ld);
   return cudaGetLastError();
 }
@@ -499,10 +496,9 @@ cudaError_t launch_curved_w(int n, int nrhs, const float* Mq, const float* Kq, f
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
   }
-  const int tiles = ((n + kCurvTC - 1) / kCurvTC) * ((n + kCurvTR - 1) / kCurvTR);
-  const int ngroups = (nrhs + 3) / 4;
-  // about four CTAs per SM over the launch; each loads its coefficients once
-  const int cg = std::max(1, std::min(ngroups, (4 * sms + tiles - 1) / tiles));
+  int pl[6];
+  spmm32_curved_plan(n, p, nrhs, sms, pl);
+  const int tiles = pl[4], cg = pl[5];
   k_spmm32_curved<W><<<dim3(tiles, cg), kCurvThreads, bytes, st>>>(n, nrhs, Mq, Kq, cm, ck, x, y,
                                                                    ld);
   return cudaGetLastError();
@@ -624,6 +620,31 @@ int spmm32_strip_rows(int n, int p, size_t smem_max) {
   size_t bytes = 0;
   int threads = 0;
   return (p >= 2 && p <= 8 && n >= 1) ? strip_plan(n, p, smem_max, &bytes, &threads) : 0;
+}
+
+void spmm32_strip_plan(int n, int p, int nrhs, int sms, size_t smem_max, int* out) {
+  size_t bytes = 0;
+  int threads = 0;
+  const int SR = (p >= 2 && p <= 8 && n >= 1) ? strip_plan(n, p, smem_max, &bytes, &threads) : 0;
+  const int strips = SR ? (n + SR - 1) / SR : 0;
+  out[0] = SR;
+  out[1] = SR ? threads : 0;
+  out[2] = (int)bytes;
+  out[3] = strips;
+  // about four CTAs per SM over the launch
+  out[4] = SR ? std::max(1, std::min(nrhs, (4 * sms + strips - 1) / strips)) : 0;
+}
+
+void spmm32_curved_plan(int n, int p, int nrhs, int sms, int* out) {
+  const int tiles = ((n + kCurvTC - 1) / kCurvTC) * ((n + kCurvTR - 1) / kCurvTR);
+  const int ngroups = (nrhs + 3) / 4;
+  out[0] = kCurvTR;
+  out[1] = kCurvTC;
+  out[2] = kCurvTR + 2 * p;
+  out[3] = kCurvTC + 2 * p;
+  out[4] = tiles;
+  // about four CTAs per SM over the launch; each loads its coefficients once
+  out[5] = std::max(1, std::min(ngroups, (4 * sms + tiles - 1) / tiles));
 }
 
 cudaError_t launch_spmm32_curved(int n, int p, int nrhs, const float* Mq, const float* Kq,

@@ -28,6 +28,14 @@ cudaError_t launch_spmm32_strip(int n, int p, int nrhs, const float* M1, const f
                                 SpmmCoef cf, const float* x, float* y, long ld, int sms,
                                 size_t smem_max, cudaStream_t st);
 int spmm32_strip_rows(int n, int p, size_t smem_max);
+// The launch plan of the row-strip form for nrhs columns on a device with sms
+// SMs: out[5] = {strip rows SR (0: does not fit), threads per CTA, dynamic
+// shared bytes, strips (grid x), column groups (grid y)}.  Host code only.
+void spmm32_strip_plan(int n, int p, int nrhs, int sms, size_t smem_max, int* out);
+// The launch plan of the curved form: out[6] = {tile rows, tile columns,
+// staged rows, staged columns, tiles (grid x), column groups (grid y)}; its
+// dynamic shared memory is two stages of staged rows x columns float4.
+void spmm32_curved_plan(int n, int p, int nrhs, int sms, int* out);
 // The curved map: assembled stencils in FP32, coefficient q of point i at
 // Mq[q N + i] (q = (dy + p)(2p + 1) + dx + p, N = n*n; the [N][(2p+1)^2]
 // stencil transposed), y_b = (cm M + ck K) x_b; Mq or Kq may be null (that
