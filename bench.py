@@ -548,13 +548,18 @@ def learned_measure(steps, plain_arm=True):
     Uref = Uref.clone()
     units = prob.N * Nt
 
-    def timed(h):
-        h.run(u0, check=False)
+    def timed(make):
+        """A warm-up run, then each timed run on a handle of its own (made before
+        its timing starts): a second run on one handle of the learned form
+        stalled on the GPU (open), a handle's first run converges."""
+        make().run(u0, check=False)
         torch.cuda.synchronize()
         ms = []
         st = None
         status = 0
         for _ in range(max(1, steps)):
+            h = make()
+            torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record()
@@ -562,19 +567,25 @@ def learned_measure(steps, plain_arm=True):
             e1.record()
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
+            del h
         err = float(torch.linalg.norm(U - Uref) / torch.linalg.norm(Uref))
         return float(np.mean(ms)), st, err, status
 
     common = dict(T=T, Nt=Nt, m=m, max_levels=2, tol=1e-10, max_iter=100)
-    learned = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
-    learned.set_coarse_propagator(phic, 0.5)
-    be = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
-    arms = [("learned", learned), ("backward_euler", be)]
+
+    def make_learned():
+        h = B.MGRIT(prob, **common, coarse_cycles=1, pmg=dict(precision=1, tol=1e-10))
+        h.set_coarse_propagator(phic, 0.5)
+        return h
+
+    arms = [("learned", make_learned),
+            ("backward_euler", lambda: B.MGRIT(prob, **common, coarse_cycles=1,
+                                               pmg=dict(precision=1, tol=1e-10)))]
     if plain_arm:
-        arms.append(("plain_fp64", B.MGRIT(prob, **common, pmg=dict(precision=0, tol=1e-10))))
+        arms.append(("plain_fp64", lambda: B.MGRIT(prob, **common, pmg=dict(precision=0, tol=1e-10))))
     res = {}
-    for name, h in arms:
-        ms, st, err, status = timed(h)
+    for name, make in arms:
+        ms, st, err, status = timed(make)
         log(f"learned_c4: {name} {ms:.0f} ms, {st['iters']} iterations")
         hist = st["res_hist"]
         res[name] = {"value": units / (ms * 1e-3), "ms": ms, "iters": st["iters"],
@@ -595,7 +606,7 @@ def learned_measure(steps, plain_arm=True):
                          "seconds": round(train_s, 2), "data_seconds": round(gen_s, 2),
                          "loss_first": float(np.mean(loss[:20])), "loss_last": float(np.mean(loss[-20:]))},
             "steps": max(1, steps)}
-    del learned, be, arms, phic, seq, stepper, X, X0, Uref
+    del arms, phic, seq, stepper, X, X0, Uref
     return line
 
 
